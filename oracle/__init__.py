@@ -1,0 +1,245 @@
+"""CPU oracle for numerical entanglement -- TEST INFRASTRUCTURE ONLY.
+
+Only the test-suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` use this package.  The product library never imports it and
+shares no code with it.  The arithmetic lives in ``ne_oracle.c`` (plain C,
+every intermediate in ``__int128`` with overflow checks); this module only
+marshals numpy arrays and composes the paper's steps:
+
+  entangle (Eq. 7 / Eq. 16)  ->  op on each entangled stream (Eq. 10)
+  ->  extract + check with an unused stream r (Eq. 17-20, Eq. 24)
+
+and the checksum-ABFT comparator (Eq. 3-6).  All functions take and return
+C-contiguous numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ne_oracle.c")
+_LIB = os.path.join(_HERE, "libne_oracle.so")
+
+POLICY_PAPER = 0        # maximise (M-2)l+k under Eq. 13 with k <= l (Table II rule)
+POLICY_SMALLEST = 1     # smallest l whose Eq. 14 range covers the output bound
+POLICY_BYTE = 2         # smallest multiple-of-8 l whose Eq. 14 range covers the bound
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def build(force: bool = False) -> str:
+    """Compile ne_oracle.c into libne_oracle.so next to it (gcc, OpenMP)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-o", tmp, _SRC])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def _L():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        i32, i64, p = ctypes.c_int, ctypes.c_int64, ctypes.c_void_p
+        lib.or_threads.restype = i32
+        lib.or_range_eq14.argtypes = [i32, i32, i32]
+        lib.or_range_eq14.restype = i64
+        lib.or_choose_l.argtypes = [i32, i32, i64, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+        lib.or_entangle.argtypes = [i32, i32, p, p, i64]
+        lib.or_gemm.argtypes = [p, p, p, i32, i32, i32]
+        lib.or_cconv.argtypes = [p, p, p, i64, i64, i64]
+        lib.or_elementwise.argtypes = [i32, p, p, p, i64]
+        lib.or_entangle_kernel_self.argtypes = [i32, p, p, i64]
+        lib.or_extract.argtypes = [i32, i32, p, i64, i32, p, p]
+        lib.or_abft_encode.argtypes = [i32, p, i64, p]
+        lib.or_abft_check.argtypes = [i32, p, i64, p]
+        lib.or_abft_recover.argtypes = [i32, p, i64, i32]
+        for f in ("or_entangle", "or_gemm", "or_cconv", "or_elementwise", "or_entangle_kernel_self",
+                  "or_extract", "or_abft_encode", "or_abft_check", "or_abft_recover", "or_choose_l"):
+            getattr(lib, f).restype = i32
+        _lib = lib
+    return _lib
+
+
+_ERR = {1: "overflow: an intermediate left the int64 word (checked in __int128)",
+        2: "invalid argument", 3: "no feasible (l, k)"}
+
+
+def _chk(code: int, what: str):
+    if code != 0:
+        raise OracleError(f"{what}: {_ERR.get(code, code)}")
+
+
+def _arr(a, dtype):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a, a.ctypes.data
+
+
+def threads() -> int:
+    """OpenMP threads the oracle uses."""
+    return int(_L().or_threads())
+
+
+# ---- parameters (Eq. 13, Eq. 14, Table II) --------------------------------
+
+def range_eq14(M: int, l: int, k: int) -> int:
+    """Eq. 14 output range bound 2^((M-3)l+k) (2^(l-1)-1); -1 if >= 2^63."""
+    return int(_L().or_range_eq14(M, l, k))
+
+
+def choose_l(M: int, w: int = 64, out_bound: int = 0, policy: int = POLICY_PAPER):
+    l, k = ctypes.c_int(), ctypes.c_int()
+    _chk(_L().or_choose_l(M, w, int(out_bound), policy, ctypes.byref(l), ctypes.byref(k)), "choose_l")
+    return l.value, k.value
+
+
+# ---- entanglement ----------------------------------------------------------
+
+def entangle(c, l: int):
+    """c: int32 [M, n] (or [..., M, n]); returns int64 eps of the same shape (Eq. 16)."""
+    c, pc = _arr(c, np.int32)
+    M, n = c.shape[-2], c.shape[-1]
+    out = np.empty(c.shape, np.int64)
+    batch = int(np.prod(c.shape[:-2], dtype=np.int64)) if c.ndim > 2 else 1
+    for b in range(batch):
+        _chk(_L().or_entangle(M, l, pc + b * M * n * 4, out.ctypes.data + b * M * n * 8, n), "entangle")
+    return out
+
+
+# ---- LSB operations (Eq. 2 / Eq. 10) ---------------------------------------
+
+def gemm(A, G):
+    """D = A @ G exactly; A int64 [m, k], G int8 [k, n]."""
+    A, pa = _arr(A, np.int64)
+    G, pg = _arr(G, np.int8)
+    m, k = A.shape
+    k2, n = G.shape
+    assert k == k2
+    D = np.empty((m, n), np.int64)
+    _chk(_L().or_gemm(pa, pg, D.ctypes.data, m, n, k), "gemm")
+    return D
+
+
+def cconv(x, g):
+    """Circular convolution y[.., n] = sum_j x[.., j] g[(n - j) mod N].
+
+    x: int64 [B, S, N]; g: int8 [B, N] (kernel b serves the S signals of group b).
+    """
+    x, px = _arr(x, np.int64)
+    g, pg = _arr(g, np.int8)
+    B, S, N = x.shape
+    assert g.shape == (B, N)
+    y = np.empty_like(x)
+    _chk(_L().or_cconv(px, pg, y.ctypes.data, B, S, N), "cconv")
+    return y
+
+
+OP_ADD, OP_SUB, OP_MUL = 0, 1, 2
+
+
+def elementwise(op: int, x, g):
+    x, px = _arr(x, np.int64)
+    g, pg = _arr(g, np.int64)
+    assert x.shape == g.shape
+    y = np.empty_like(x)
+    _chk(_L().or_elementwise(op, px, pg, y.ctypes.data, x.size), "elementwise")
+    return y
+
+
+def entangle_kernel_self(g, l: int):
+    """Footnote to Eq. 10: g <- S_l{g} + g (for op in {+, -})."""
+    g, pg = _arr(g, np.int64)
+    out = np.empty_like(g)
+    _chk(_L().or_entangle_kernel_self(l, pg, out.ctypes.data, g.size), "entangle_kernel_self")
+    return out
+
+
+# ---- extraction / check / recovery (Eq. 17-20, Eq. 24) ---------------------
+
+def extract(delta, l: int, r: int = 0, check: bool = True):
+    """delta: int64 [M, n] (or [..., M, n]).  Returns (dhat, flags) where flags
+    is a uint8 array of the positions (None when check is False, in which case
+    delta[r] is not read: this is the fail-stop recovery of Prop. 3)."""
+    delta, pd = _arr(delta, np.int64)
+    M, n = delta.shape[-2], delta.shape[-1]
+    batch = int(np.prod(delta.shape[:-2], dtype=np.int64)) if delta.ndim > 2 else 1
+    dhat = np.empty(delta.shape, np.int64)
+    flags = np.zeros(delta.shape[:-2] + (n,), np.uint8) if check else None
+    for b in range(batch):
+        fp = flags.ctypes.data + b * n if check else None
+        _chk(_L().or_extract(M, l, pd + b * M * n * 8, n, r, dhat.ctypes.data + b * M * n * 8, fp), "extract")
+    return dhat, flags
+
+
+def recover(delta, l: int, r_lost: int):
+    """Prop. 3: all M outputs from the M-1 planes other than r_lost."""
+    return extract(delta, l, r_lost, check=False)[0]
+
+
+# ---- checksum ABFT (Eq. 3-6) ----------------------------------------------
+
+def abft_encode(c):
+    """Eq. 4: r = sum_m c_m; c int32 [M, n] -> int64 [n]."""
+    c, pc = _arr(c, np.int32)
+    M, n = c.shape
+    r = np.empty(n, np.int64)
+    _chk(_L().or_abft_encode(M, pc, n, r.ctypes.data), "abft_encode")
+    return r
+
+
+def abft_check(d):
+    """Eq. 6 per position; d int64 [M+1, n] (last plane is e)."""
+    d, pd = _arr(d, np.int64)
+    M = d.shape[0] - 1
+    n = d.shape[1]
+    f = np.zeros(n, np.uint8)
+    _chk(_L().or_abft_check(M, pd, n, f.ctypes.data), "abft_check")
+    return f
+
+
+def abft_recover(d, j: int):
+    """Sec. II-A: rebuild plane j of d [M+1, n] from e and the others."""
+    d = np.array(d, dtype=np.int64, order="C", copy=True)
+    M = d.shape[0] - 1
+    _chk(_L().or_abft_recover(M, d.ctypes.data, d.shape[1], j), "abft_recover")
+    return d
+
+
+# ---- the pipelines composed from the steps ---------------------------------
+
+def gemm_direct(c, G):
+    """d_m = c_m G for every stream (Eq. 2, inner products); c int32 [M, m, k]."""
+    return np.stack([gemm(np.asarray(cm, np.int64), G) for cm in c])
+
+
+def gemm_entangled(c, G, l: int, r: int = 0):
+    """entangle -> delta_m = eps_m G -> extract/check.  Returns (dhat, flags, delta)."""
+    M, m, k = c.shape
+    eps = entangle(c.reshape(M, m * k), l).reshape(M, m, k)
+    delta = np.stack([gemm(eps[i], G) for i in range(M)])
+    n = G.shape[1]
+    dhat, flags = extract(delta.reshape(M, m * n), l, r)
+    return dhat.reshape(M, m, n), flags.reshape(m, n), delta
+
+
+def cconv_direct(c, g):
+    """c int32 [B, M, N], g int8 [B, N] -> int64 [B, M, N]."""
+    return cconv(np.asarray(c, np.int64), g)
+
+
+def cconv_entangled(c, g, l: int, r: int = 0):
+    """entangle each group -> circular convolution per stream -> extract/check.
+    Returns (dhat [B, M, N], flags [B, N], delta [B, M, N])."""
+    eps = entangle(c, l)
+    delta = cconv(eps, g)
+    dhat, flags = extract(delta, l, r)
+    return dhat, flags, delta

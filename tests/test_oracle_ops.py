@@ -1,0 +1,136 @@
+"""Pins for the oracle's LSB operations, the ABFT comparator and the composed
+pipelines: textbook/library routines (numpy matmul, an explicit circulant
+matrix, numpy FFT), Python big-integer brute force and the invariant that
+disentangled outputs equal the direct outputs (Prop. 3-4)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1604_04740_gb300 import inputs
+
+
+def test_gemm_matches_numpy_matmul():
+    rng = np.random.default_rng(0)
+    for m, n, k in [(1, 1, 1), (7, 5, 3), (33, 17, 65), (64, 64, 64)]:
+        A = rng.integers(-(2 ** 20), 2 ** 20, (m, k), dtype=np.int64)
+        G = rng.integers(-128, 128, (k, n)).astype(np.int8)
+        assert (oracle.gemm(A, G) == A @ G.astype(np.int64)).all()
+
+
+def test_gemm_big_int_brute_force_and_overflow():
+    A = np.array([[2 ** 55, -(2 ** 55)], [3, 4]], np.int64)
+    G = np.array([[127, -128], [127, 127]], np.int8)
+    want = [[sum(int(A[i, t]) * int(G[t, j]) for t in range(2)) for j in range(2)] for i in range(2)]
+    assert oracle.gemm(A, G).tolist() == want
+    # a partial sum beyond int64 is reported even if the final sum would fit
+    A2 = np.array([[2 ** 62, -(2 ** 62)]], np.int64)
+    G2 = np.array([[2], [2]], np.int8)
+    with pytest.raises(oracle.OracleError):
+        oracle.gemm(A2, G2)
+
+
+def test_cconv_matches_circulant_matrix_and_fft():
+    rng = np.random.default_rng(1)
+    for N in (1, 2, 5, 16, 100, 256):
+        x = rng.integers(-(2 ** 20), 2 ** 20, (2, 3, N), dtype=np.int64)
+        g = rng.integers(-128, 128, (2, N)).astype(np.int8)
+        y = oracle.cconv(x, g)
+        for b in range(2):
+            C = np.array([[int(g[b, (i - j) % N]) for j in range(N)] for i in range(N)], np.int64)
+            for s in range(3):
+                assert (y[b, s] == C @ x[b, s]).all()
+        # FFT route on small-magnitude data (exact after rounding)
+        xs = rng.integers(-100, 100, (1, 1, N), dtype=np.int64)
+        ys = oracle.cconv(xs, g[:1])
+        f = np.fft.ifft(np.fft.fft(xs[0, 0].astype(float)) * np.fft.fft(g[0].astype(float))).real
+        assert (ys[0, 0] == np.rint(f).astype(np.int64)).all()
+
+
+def test_cconv_tiny_brute_force():
+    x = np.array([[[1, 2, 3]]], np.int64)
+    g = np.array([[1, 0, -1]], np.int8)
+    # y[n] = sum_j x[j] g[(n-j) mod 3]:  y0 = 1*1 + 2*g[2] + 3*g[1] = 1 - 2 = -1
+    #                                     y1 = 1*g[1] + 2*g[0] + 3*g[2] = 2 - 3 = -1
+    #                                     y2 = 1*g[2] + 2*g[1] + 3*g[0] = -1 + 3 = 2
+    assert oracle.cconv(x, g)[0, 0].tolist() == [-1, -1, 2]
+
+
+def test_elementwise_and_self_entangled_kernel():
+    rng = np.random.default_rng(2)
+    x = rng.integers(-(2 ** 30), 2 ** 30, 50, dtype=np.int64)
+    g = rng.integers(-(2 ** 20), 2 ** 20, 50, dtype=np.int64)
+    assert (oracle.elementwise(oracle.OP_ADD, x, g) == x + g).all()
+    assert (oracle.elementwise(oracle.OP_SUB, x, g) == x - g).all()
+    assert (oracle.elementwise(oracle.OP_MUL, x, g) == x * g).all()
+    assert (oracle.entangle_kernel_self(g, 9) == g * 513).all()
+
+
+def test_elementwise_add_pipeline_uses_self_entangled_kernel():
+    # Footnote to Eq. 10: with g <- S_l{g} + g the entangled sum decodes to c + g.
+    M, l, n = 3, 12, 64
+    rng = np.random.default_rng(5)
+    c = rng.integers(-500, 500, (M, n)).astype(np.int32)
+    g = rng.integers(-500, 500, n, dtype=np.int64)
+    eps = oracle.entangle(c, l)
+    ge = oracle.entangle_kernel_self(g, l)
+    for op, want in ((oracle.OP_ADD, c + g), (oracle.OP_SUB, c - g)):
+        delta = np.stack([oracle.elementwise(op, eps[m], ge) for m in range(M)])
+        dh, fl = oracle.extract(delta, l, 0)
+        assert (dh == want).all() and not fl.any()
+    delta = np.stack([oracle.elementwise(oracle.OP_MUL, eps[m], g) for m in range(M)])
+    dh, fl = oracle.extract(delta, l, 1)
+    assert (dh == c * g).all() and not fl.any()
+
+
+def test_abft_encode_check_recover():
+    rng = np.random.default_rng(3)
+    M, n = 4, 100
+    c = rng.integers(-(2 ** 31), 2 ** 31 - 1, (M, n)).astype(np.int32)
+    r = oracle.abft_encode(c)
+    assert (r == c.astype(np.int64).sum(axis=0)).all()
+    # op = elementwise x g on M+1 streams (Eq. 5)
+    g = rng.integers(-128, 128, n, dtype=np.int64)
+    d = np.concatenate([c.astype(np.int64) * g, (r * g)[None]])
+    assert not oracle.abft_check(d).any()
+    bad = d.copy()
+    bad[2, 17] ^= 1 << 40
+    f = oracle.abft_check(bad)
+    assert f[17] and f.sum() == 1
+    lost = d.copy()
+    lost[1] = 999
+    assert (oracle.abft_recover(lost, 1) == d).all()
+
+
+@pytest.mark.parametrize("M,l", [(3, 11), (3, 22), (4, 10), (4, 16), (5, 8)])
+def test_gemm_pipeline_equals_direct(M, l):
+    c = inputs.streams(0, (M, 24, 40))
+    G = inputs.operator_int8(0, (40, 19))
+    direct = oracle.gemm_direct(c, G)
+    for r in range(M):
+        dh, fl, delta = oracle.gemm_entangled(c, G, l, r)
+        assert (dh == direct).all() and not fl.any()
+        assert (oracle.recover(delta.reshape(M, -1), l, r).reshape(dh.shape) == direct).all()
+
+
+@pytest.mark.parametrize("M,l,N", [(3, 13, 64), (3, 16, 100), (4, 16, 33), (5, 8, 50)])
+def test_cconv_pipeline_equals_direct(M, l, N):
+    c = inputs.streams(1, (3, M, N))
+    g = inputs.operator_int8(1, (3, N))
+    direct = oracle.cconv_direct(c, g)
+    dh, fl, delta = oracle.cconv_entangled(c, g, l, 0)
+    assert (dh == direct).all() and not fl.any()
+
+
+def test_inputs_generator_is_stable():
+    # The generator is the published SplitMix64 output function on a counter;
+    # the first value for key 0 + GAMMA is the well-known SplitMix64 first
+    # output for seed 0.
+    z = inputs._fin(np.array([0x9E3779B97F4A7C15], np.uint64))[0]
+    assert int(z) == 0xE220A8397B1DCDAF
+    a = inputs.int8_uniform(0, inputs.TAG_C, (1000,))
+    assert a.min() >= -128 and a.max() <= 127 and a.dtype == np.int8
+    assert (a == inputs.int8_uniform(0, inputs.TAG_C, (1000,))).all()
+    assert (a[500:] == inputs.int8_uniform(0, inputs.TAG_C, (500,), start=500)).all()
+    gi, pos, j, b = inputs.fault_list(1, 10, 100, 3, 50)
+    assert len(set(zip(gi.tolist(), pos.tolist()))) == 50
+    assert j.max() < 3 and b.max() < 64
