@@ -1,0 +1,233 @@
+/*
+ * ne.h -- C ABI of the GB300 (sm_103a) numerical-entanglement library.
+ *
+ * Numerical entanglement (Anam & Andreopoulos, "Reliable Linear, Sesquilinear
+ * and Bijective Operations on Integer Data Streams via Numerical
+ * Entanglement") makes a linear/sesquilinear integer operation on M >= 3
+ * streams fault tolerant without extra streams:
+ *
+ *   entangle   eps_m = c_m + 2^l c_{(m-1) mod M}                (Eq. 7, Eq. 16)
+ *   operate    delta_m = eps_m op g, on every stream unchanged    (Eq. 10)
+ *   extract    all M outputs from any M-1 of the delta_m        (Eq. 17-20)
+ *   check      recreate the unused delta_r and compare           (Eq. 24)
+ *   recover    a lost stream r is simply the unused one          (Prop. 3)
+ *
+ * All arithmetic is exact integer arithmetic on w = 64-bit words.
+ *
+ * Conventions for every entry point
+ *  - Pointers named with a device type are DEVICE pointers; the caller owns
+ *    all memory.  Only ne_*_host entry points take host pointers.
+ *  - Calls are asynchronous on the CUDA stream `s` (0 = legacy default
+ *    stream) and return a host-side status: NE_EINVAL / NE_ERANGE for
+ *    arguments rejected before any launch, NE_ECUDA if a launch failed.
+ *    Conditions found on the device are written to the caller's `status`
+ *    word (device int32, nullable) and are visible after the stream syncs.
+ *  - Stream planes are stored as [batch][M][n] (row-major): group b,
+ *    stream m, position i is at index (b*M + m)*n + i.
+ *  - Check results are bitmaps of uint32 words: position i of group b is bit
+ *    (i % 32) of word b*ceil(n/32) + i/32 (bits past n in the last word are
+ *    0).  When a count pointer `nflag` (device uint64) is given, the call
+ *    first sets it to 0 and then adds the number of flagged positions.
+ *  - No entry point allocates device memory.  ne_last_error() returns a
+ *    message for the last failed call on the calling host thread.
+ */
+#ifndef NE_H
+#define NE_H
+
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    NE_OK = 0,
+    NE_EINVAL = 1,    /* invalid argument (null pointer, size, alignment, M < 3, ...)       */
+    NE_ERANGE = 2,    /* parameters violate Eq. 13, or data outside the planned digit range */
+    NE_ECUDA = 3,     /* a CUDA runtime call or launch failed                               */
+    NE_ETIMEOUT = 4,  /* a bounded device-side wait gave up                                 */
+    NE_ENOMEM = 5     /* a caller-provided workspace is too small                           */
+} ne_status;
+
+/* The method's parameters: M streams (3 <= M <= 32), shift l, word width w
+ * (always 64 here).  Valid when (M-1) l < w, i.e. Eq. 13 holds with k >= 1. */
+typedef struct {
+    int32_t M;
+    int32_t l;
+    int32_t w;
+} ne_params;
+
+/* Balanced base-256 digit planes of entangled words.  A word x is stored as
+ * the S planes sigma_0..sigma_{S-1} (int8) with
+ *     x = sum_s sigma_s * 2^shift[s],   shift[s] a multiple of 8, ascending,
+ * where the digits not listed are identically zero for the inputs the plan
+ * was made for (see ne_plan_digits).  Plane layout: [batch][M][S][n]. */
+#define NE_MAX_DIGITS 8
+typedef struct {
+    int32_t S;
+    int32_t shift[NE_MAX_DIGITS];
+} ne_digits;
+
+/* l-selection policies for ne_choose_l */
+#define NE_L_PAPER    0  /* max (M-2)l+k s.t. (M-1)l+k <= w, k <= l; ties -> larger (M-1)l+k */
+#define NE_L_SMALLEST 1  /* smallest l with an admissible k whose Eq. 14 range covers the bound */
+#define NE_L_BYTE     2  /* as NE_L_SMALLEST, l restricted to multiples of 8 */
+
+/* fused epilogues of the digit-plane operations */
+#define NE_FUSE_NONE          0  /* write delta_m (int64) for every computed stream            */
+#define NE_FUSE_EXTRACT_CHECK 1  /* write d_hat (Eq. 17-20) and the Eq. 24 check flags        */
+#define NE_FUSE_RECOVER       2  /* stream r is lost: skip it, write d_hat from the other M-1 */
+
+/* ------------------------------------------------------------------------ */
+/* Planning (host only, no device work)                                      */
+/* ------------------------------------------------------------------------ */
+
+/* Choose the shift l and the bookkeeping k of Sec. III-C: Eq. 13
+ * ((M-1)l + k <= w) with k <= l, and the Eq. 14 output range
+ * 2^((M-3)l+k) (2^(l-1)-1) >= out_bound for the bound-driven policies.
+ * Returns NE_ERANGE if no (l, k) exists.  l, k: host out-pointers. */
+ne_status ne_choose_l(int32_t M, int32_t w, int64_t out_bound, int32_t policy,
+                      int32_t* l, int32_t* k);
+
+/* Which balanced base-256 digits of eps = a + 2^l b can be non-zero when the
+ * stream values a, b lie in [cmin, cmax] (the entanglement of Eq. 16).
+ * Fills *dg with the digit positions that occur.  A range of at most 4096
+ * values is enumerated exactly; a wider range lists every digit up to the
+ * width of |eps| <= max|c| (2^l + 1).  NE_ERANGE if more than NE_MAX_DIGITS
+ * digits would be needed. */
+ne_status ne_plan_digits(int32_t l, int32_t cmin, int32_t cmax, ne_digits* dg);
+
+/* ------------------------------------------------------------------------ */
+/* Entanglement (Eq. 7 for M = 3; Eq. 15-16 for general M)                   */
+/* ------------------------------------------------------------------------ */
+
+/* eps[b][m][i] = c[b][m][i] + 2^l c[b][(m-1) mod M][i].
+ * c: int32 [batch][M][n], eps: int64 [batch][M][n] (may not alias c). */
+ne_status ne_entangle(ne_params p, const int32_t* c, int64_t* eps,
+                      int64_t batch, int64_t n, cudaStream_t s);
+
+/* Same entangled words, stored as digit planes: planes is int8
+ * [batch][M][dg.S][n].  A word with a non-zero digit outside dg, or a
+ * residue beyond the top digit, sets *status = NE_ERANGE (status nullable;
+ * the call does not reset it). */
+ne_status ne_entangle_digits(ne_params p, ne_digits dg, const int32_t* c, int8_t* planes,
+                             int64_t batch, int64_t n, int32_t* status, cudaStream_t s);
+
+/* ------------------------------------------------------------------------ */
+/* The LSB operation on each stream (Eq. 10), unaware of the entanglement    */
+/* ------------------------------------------------------------------------ */
+
+/* Matrix product per stream on CUDA cores in int64 (exact while every partial
+ * sum fits 64 bits): out[m] = x[m] * G for streams m = 0..P-1 whose bit in
+ * skip_mask is clear (skipped planes are not written: a fail-stopped core).
+ * x: int64 [P][rows][k] (entangled words, or raw streams widened to int64),
+ * G: int8 [k][cols], out: int64 [P][rows][cols].  P is the number of planes
+ * (M for entangled streams, M+1 for the checksum comparator). */
+ne_status ne_gemm(int32_t P, const int64_t* x, const int8_t* G, int64_t* out,
+                  int32_t rows, int32_t cols, int32_t k, uint32_t skip_mask, cudaStream_t s);
+
+/* The same product on the int8 tensor path: every digit plane is multiplied
+ * by G with int32 accumulation over K chunks of at most 2^31 / 2^14 terms
+ * (no int32 overflow for int8 x int8), and the digits are recombined exactly
+ * in int64.  planes: int8 [M][dg.S][rows][k]; G: int8 [k][cols].
+ *  fuse = NE_FUSE_NONE:          out = delta, int64 [M][rows][cols].
+ *  fuse = NE_FUSE_EXTRACT_CHECK: out = d_hat of Eq. 17-20 using every stream
+ *        but r, and flags/nflag receive the Eq. 24 check of stream r
+ *        (positions flattened as i*cols + j; flags nullable).
+ *  fuse = NE_FUSE_RECOVER:       stream r is not computed at all; out = d_hat
+ *        from the other M-1 streams (Prop. 3); flags ignored.
+ * rows, cols >= 1; k >= 1 and a multiple of 16; cols a multiple of 8. */
+ne_status ne_gemm_digits(ne_params p, ne_digits dg, const int8_t* planes, const int8_t* G,
+                         int64_t* out, uint32_t* flags, uint64_t* nflag,
+                         int32_t rows, int32_t cols, int32_t k,
+                         int32_t fuse, int32_t r, cudaStream_t s);
+
+/* Batched circular convolution on CUDA cores in int64 (the direct form):
+ * out[b][m][i] = sum_j x[b][m][j] g[b][(i - j) mod N] for the P planes of
+ * each group.  x, out: int64 [batch][P][N]; g: int8 [batch][N]. */
+ne_status ne_cconv(int32_t P, const int64_t* x, const int8_t* g, int64_t* out,
+                   int64_t batch, int64_t N, uint32_t skip_mask, cudaStream_t s);
+
+/* The same convolution on the int8 tensor path: the circulant of g is tiled
+ * into Toeplitz blocks built in shared memory and multiplied with the digit
+ * planes (int32 accumulation, exact int64 recombination), with the same
+ * fused epilogues as ne_gemm_digits.  planes: int8 [batch][M][dg.S][N];
+ * g: int8 [batch][N]; out: int64 [batch][M][N]; flags: [batch][N/32].
+ * N a multiple of 64 with 64 <= N <= 4096. */
+ne_status ne_cconv_digits(ne_params p, ne_digits dg, const int8_t* planes, const int8_t* g,
+                          int64_t* out, uint32_t* flags, uint64_t* nflag,
+                          int64_t batch, int64_t N, int32_t fuse, int32_t r, cudaStream_t s);
+
+/* ------------------------------------------------------------------------ */
+/* Extraction, check and recovery (Eq. 17-20, Eq. 24, Prop. 3)               */
+/* ------------------------------------------------------------------------ */
+
+/* All M outputs from the streams other than r:
+ *   T = (-1)^M sum_{m=0}^{M-2} (-1)^m 2^((M-2-m)l) delta_{(r+1+m) mod M}   (Eq. 17)
+ *   d_{r-1} = low (M-1)l bits of T, sign-extended                          (Eq. 18)
+ *   d_r = floor((-1)^M (T - d_{r-1}) / 2^((M-1)l))                         (Eq. 19)
+ *   d_{r+m} = delta_{r+m} - 2^l d_{r+m-1},  m = 1..M-2                     (Eq. 20)
+ * in 128-bit arithmetic (Remark 1); outputs are the low 64 bits.  The sign
+ * (-1)^M and the index r-1 in Eq. 19 are the readings under which Eq. 17-19
+ * reduce to Eq. 11 at M = 3.  delta, d_hat: int64 [batch][M][n].
+ * If flags or nflag is non-null, also performs the check of ne_check. */
+ne_status ne_extract(ne_params p, const int64_t* delta, int64_t* d_hat,
+                     int64_t batch, int64_t n, int32_t r,
+                     uint32_t* flags, uint64_t* nflag, cudaStream_t s);
+
+/* Eq. 24: flag a position when delta_r != d_r + 2^l d_{r-1}, with d_r and
+ * d_{r-1} of Eq. 18-19 computed exactly from the other streams.  Any fault
+ * confined to one stream of a position is flagged (Prop. 4). */
+ne_status ne_check(ne_params p, const int64_t* delta, int64_t batch, int64_t n, int32_t r,
+                   uint32_t* flags, uint64_t* nflag, cudaStream_t s);
+
+/* Prop. 3: stream r_lost is unavailable (never read, may hold anything);
+ * all M outputs are rebuilt from the other M-1. */
+ne_status ne_recover(ne_params p, const int64_t* delta, int64_t* d_hat,
+                     int64_t batch, int64_t n, int32_t r_lost, cudaStream_t s);
+
+/* ------------------------------------------------------------------------ */
+/* Transient-fault injection (test harness for the fault model of Sec. I)    */
+/* ------------------------------------------------------------------------ */
+
+/* XOR one bit into entangled outputs: for f < count, flips bit bit[f] of
+ * delta[(group[f]*P + stream[f])*n + pos[f]].  All four lists are device
+ * int64 arrays; entries are validated on the device and out-of-range
+ * entries are skipped and reported in *status (NE_EINVAL, nullable). */
+ne_status ne_inject(int64_t* delta, int32_t P, int64_t batch, int64_t n,
+                    const int64_t* group, const int64_t* pos, const int64_t* stream,
+                    const int64_t* bit, int64_t count, int32_t* status, cudaStream_t s);
+
+/* ------------------------------------------------------------------------ */
+/* Checksum ABFT comparator (Eq. 3-6, Sec. II-A)                             */
+/* ------------------------------------------------------------------------ */
+
+/* Eq. 4: x[b][m][i] = c[b][m][i] for m < M and x[b][M][i] = sum_m c[b][m][i]
+ * (the checksum stream), widened to int64.  c: int32 [batch][M][n];
+ * x: int64 [batch][M+1][n]. */
+ne_status ne_abft_encode(int32_t M, const int32_t* c, int64_t* x,
+                         int64_t batch, int64_t n, cudaStream_t s);
+
+/* Eq. 6 per position: flag when sum_{m<M} d[b][m][i] != d[b][M][i].
+ * d: int64 [batch][M+1][n]; flags/nflag as for ne_check. */
+ne_status ne_abft_check(int32_t M, const int64_t* d, int64_t batch, int64_t n,
+                        uint32_t* flags, uint64_t* nflag, cudaStream_t s);
+
+/* Sec. II-A: rebuild the lost plane j of d in place as d[M] - sum_{m != j} d[m]. */
+ne_status ne_abft_recover(int32_t M, int64_t* d, int64_t batch, int64_t n, int32_t j,
+                          cudaStream_t s);
+
+/* ------------------------------------------------------------------------ */
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char* ne_last_error(void);
+
+/* Library version string. */
+const char* ne_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NE_H */

@@ -1,0 +1,54 @@
+// Shared device/host helpers of the numerical-entanglement library (sm_103a).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "ne.h"
+
+namespace ne {
+
+// ---- host-side error reporting (ne_host.cu) --------------------------------
+ne_status fail(ne_status st, const char* fmt, ...);
+ne_status check_launch(const char* what);
+int sm_count();                      // SMs of the current device (cached per device)
+ne_status validate_params(const ne_params& p);
+ne_status validate_digits(const ne_digits& dg);
+
+// grid of roughly `waves` full waves of `threads`-thread blocks on this GPU
+inline int wave_blocks(int threads, int waves = 4) {
+    int per_sm = 2048 / threads;
+    if (per_sm < 1) per_sm = 1;
+    return sm_count() * per_sm * waves;
+}
+
+inline bool aligned(const void* p, int bytes) {
+    return (reinterpret_cast<uintptr_t>(p) % bytes) == 0;
+}
+
+// ---- 128-bit helpers (Remark 1: the 2w-bit temporaries) ---------------------
+typedef __int128 i128;
+typedef unsigned __int128 u128;
+
+__device__ __forceinline__ i128 shl128(i128 x, int s) { return (i128)((u128)x << s); }
+// arithmetic (floor) shift; nvcc implements >> on signed 128-bit as arithmetic
+__device__ __forceinline__ i128 sar128(i128 x, int s) { return x >> s; }
+
+// sign extension of the low L bits of a word, 1 <= L <= 63 (Eq. 18)
+__device__ __forceinline__ int64_t sext_low(uint64_t lo, int L) {
+    return (int64_t)(lo << (64 - L)) >> (64 - L);
+}
+
+// ---- flag bitmaps -----------------------------------------------------------
+// The extraction kernels give each lane two consecutive positions; lanes 0-15
+// cover bits 0..31 of one bitmap word and lanes 16-31 the next.  OR-reduce the
+// 2-bit contributions over each half-warp.
+__device__ __forceinline__ uint32_t halfwarp_or(uint32_t v) {
+    v |= __shfl_xor_sync(0xffffffffu, v, 1);
+    v |= __shfl_xor_sync(0xffffffffu, v, 2);
+    v |= __shfl_xor_sync(0xffffffffu, v, 4);
+    v |= __shfl_xor_sync(0xffffffffu, v, 8);
+    return v;
+}
+
+}  // namespace ne

@@ -1,0 +1,224 @@
+// Entanglement (Eq. 7 for M = 3, Eq. 15-16 for general M) and the checksum
+// encoder of the ABFT comparator (Eq. 4).  All three are streaming,
+// HBM-bound kernels: one pass over the int32 input planes, 16-byte loads,
+// every output written once.
+//
+// Traversal: blockIdx.y walks the groups (batch rows) and blockIdx.x/threads
+// walk the positions of a row in chunks of VEC, so no division is needed to
+// split a flat index into (group, position).
+#include "ne_common.cuh"
+
+namespace {
+
+using namespace ne;
+
+// ---- int64 words -------------------------------------------------------------
+
+// eps_m = c_m + 2^l c_{m-1} (mod M); the product is formed in unsigned
+// arithmetic so that it is the exact two's-complement value (|c| < 2^31 and
+// l <= 31 under Eq. 13 keep it far from 2^63).
+__device__ __forceinline__ int64_t entangle_word(int32_t cm, int32_t cprev, int l) {
+    return (int64_t)((uint64_t)(int64_t)cm + ((uint64_t)(int64_t)cprev << l));
+}
+
+template <int VEC>
+__global__ void __launch_bounds__(256) k_entangle(const int32_t* __restrict__ c, int64_t* __restrict__ eps,
+                                                  int M, int l, int64_t batch, int64_t n) {
+    const int64_t nchunk = n / VEC;
+    for (int64_t b = blockIdx.y; b < batch; b += gridDim.y) {
+        const int32_t* cb = c + b * M * n;
+        int64_t* eb = eps + b * M * n;
+        for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nchunk;
+             q += (int64_t)gridDim.x * blockDim.x) {
+            if constexpr (VEC == 4) {
+                // the previous stream's chunk stays in registers: M + 1 loads per chunk
+                int4 prev = __ldcs(reinterpret_cast<const int4*>(cb + (int64_t)(M - 1) * n + q * 4));
+                for (int m = 0; m < M; m++) {
+                    int4 cur = __ldcs(reinterpret_cast<const int4*>(cb + (int64_t)m * n + q * 4));
+                    longlong2 lo, hi;
+                    lo.x = entangle_word(cur.x, prev.x, l);
+                    lo.y = entangle_word(cur.y, prev.y, l);
+                    hi.x = entangle_word(cur.z, prev.z, l);
+                    hi.y = entangle_word(cur.w, prev.w, l);
+                    longlong2* dst = reinterpret_cast<longlong2*>(eb + (int64_t)m * n + q * 4);
+                    __stcs(dst, lo);
+                    __stcs(dst + 1, hi);
+                    prev = cur;
+                }
+            } else {
+                int32_t prev = cb[(int64_t)(M - 1) * n + q];
+                for (int m = 0; m < M; m++) {
+                    int32_t cur = cb[(int64_t)m * n + q];
+                    eb[(int64_t)m * n + q] = entangle_word(cur, prev, l);
+                    prev = cur;
+                }
+            }
+        }
+    }
+}
+
+// ---- digit planes --------------------------------------------------------------
+
+struct DigitPlan {
+    int S;
+    int top;           // index of the highest digit that is computed (shift/8)
+    uint32_t stored;   // bit t set: digit t is stored
+    int slot[8];       // plane index of digit t (valid where stored)
+};
+
+// Balanced base-256 digits: digit t of a word is the signed low byte of the
+// running remainder, and the remainder becomes (x - digit) / 256, exactly.
+// Each thread takes VEC consecutive positions of a group (two 16-byte loads
+// per input stream when VEC = 8) and writes one VEC-byte word per stored
+// digit plane.  A non-zero digit that the plan does not store, or a
+// remainder left after the top planned digit, reports NE_ERANGE.
+template <int VEC>
+__global__ void __launch_bounds__(256) k_entangle_digits(const int32_t* __restrict__ c, int8_t* __restrict__ planes,
+                                                         int M, int l, DigitPlan P, int64_t batch, int64_t n,
+                                                         int32_t* status) {
+    const int64_t nchunk = n / VEC;
+    bool ok = true;
+    for (int64_t b = blockIdx.y; b < batch; b += gridDim.y) {
+        const int32_t* cb = c + b * M * n;
+        int8_t* pb = planes + b * M * P.S * n;
+        for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nchunk;
+             q += (int64_t)gridDim.x * blockDim.x) {
+            int32_t prev[VEC], cur[VEC];
+            if constexpr (VEC == 8) {
+                const int4* src = reinterpret_cast<const int4*>(cb + (int64_t)(M - 1) * n + q * 8);
+                int4 a = __ldcs(src), bb = __ldcs(src + 1);
+                prev[0] = a.x; prev[1] = a.y; prev[2] = a.z; prev[3] = a.w;
+                prev[4] = bb.x; prev[5] = bb.y; prev[6] = bb.z; prev[7] = bb.w;
+            } else {
+                prev[0] = cb[(int64_t)(M - 1) * n + q];
+            }
+            for (int m = 0; m < M; m++) {
+                if constexpr (VEC == 8) {
+                    const int4* src = reinterpret_cast<const int4*>(cb + (int64_t)m * n + q * 8);
+                    int4 a = __ldcs(src), bb = __ldcs(src + 1);
+                    cur[0] = a.x; cur[1] = a.y; cur[2] = a.z; cur[3] = a.w;
+                    cur[4] = bb.x; cur[5] = bb.y; cur[6] = bb.z; cur[7] = bb.w;
+                } else {
+                    cur[0] = cb[(int64_t)m * n + q];
+                }
+                int64_t x[VEC];
+#pragma unroll
+                for (int v = 0; v < VEC; v++) x[v] = entangle_word(cur[v], prev[v], l);
+                int8_t* mp = pb + (int64_t)m * P.S * n + q * VEC;
+#pragma unroll
+                for (int t = 0; t < 8; t++) {
+                    if (t > P.top) break;
+                    uint32_t w0 = 0, w1 = 0;
+                    bool nz = false;
+#pragma unroll
+                    for (int v = 0; v < VEC; v++) {
+                        const int8_t d = (int8_t)(x[v] & 0xff);
+                        nz |= (d != 0);
+                        if (v < 4) w0 |= (uint32_t)(uint8_t)d << (8 * v);
+                        else w1 |= (uint32_t)(uint8_t)d << (8 * (v - 4));
+                        x[v] = (x[v] - d) >> 8;
+                    }
+                    if (P.stored & (1u << t)) {
+                        int8_t* dst = mp + (int64_t)P.slot[t] * n;
+                        if constexpr (VEC == 8) __stcs(reinterpret_cast<uint2*>(dst), make_uint2(w0, w1));
+                        else dst[0] = (int8_t)w0;
+                    } else {
+                        ok = ok && !nz;
+                    }
+                }
+#pragma unroll
+                for (int v = 0; v < VEC; v++) {
+                    ok = ok && (x[v] == 0);
+                    prev[v] = cur[v];
+                }
+            }
+        }
+    }
+    if (!ok && status) atomicExch(status, (int32_t)NE_ERANGE);
+}
+
+// ---- checksum encoder (Eq. 4) -------------------------------------------------
+
+__global__ void __launch_bounds__(256) k_abft_encode(const int32_t* __restrict__ c, int64_t* __restrict__ x,
+                                                     int M, int64_t batch, int64_t n) {
+    for (int64_t b = blockIdx.y; b < batch; b += gridDim.y) {
+        const int32_t* cb = c + b * M * n;
+        int64_t* xb = x + b * (M + 1) * n;
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+            int64_t sum = 0;
+            for (int m = 0; m < M; m++) {
+                int64_t v = cb[(int64_t)m * n + i];
+                xb[(int64_t)m * n + i] = v;
+                sum += v;
+            }
+            xb[(int64_t)M * n + i] = sum;
+        }
+    }
+}
+
+dim3 grid_rows(int64_t batch, int64_t chunks, int threads) {
+    int64_t gy = batch < 65535 ? batch : 65535;
+    int64_t want = (int64_t)wave_blocks(threads, 4);
+    int64_t gx = (chunks + threads - 1) / threads;
+    int64_t cap = want / gy;
+    if (cap < 1) cap = 1;
+    if (gx > cap) gx = cap;
+    if (gx < 1) gx = 1;
+    return dim3((unsigned)gx, (unsigned)gy, 1);
+}
+
+}  // namespace
+
+extern "C" ne_status ne_entangle(ne_params p, const int32_t* c, int64_t* eps, int64_t batch, int64_t n,
+                                 cudaStream_t s) {
+    ne_status st = validate_params(p);
+    if (st) return st;
+    if (batch < 0 || n < 0) return fail(NE_EINVAL, "ne_entangle: batch=%lld n=%lld", (long long)batch, (long long)n);
+    if (batch == 0 || n == 0) return NE_OK;
+    if (!c || !eps) return fail(NE_EINVAL, "ne_entangle: null pointer");
+    const int T = 256;
+    if (n % 4 == 0 && aligned(c, 16) && aligned(eps, 16)) {
+        k_entangle<4><<<grid_rows(batch, n / 4, T), T, 0, s>>>(c, eps, p.M, p.l, batch, n);
+    } else {
+        k_entangle<1><<<grid_rows(batch, n, T), T, 0, s>>>(c, eps, p.M, p.l, batch, n);
+    }
+    return check_launch("ne_entangle");
+}
+
+extern "C" ne_status ne_entangle_digits(ne_params p, ne_digits dg, const int32_t* c, int8_t* planes,
+                                        int64_t batch, int64_t n, int32_t* status, cudaStream_t s) {
+    ne_status st = validate_params(p);
+    if (st) return st;
+    if ((st = validate_digits(dg))) return st;
+    if (batch < 0 || n < 0) return fail(NE_EINVAL, "ne_entangle_digits: batch=%lld n=%lld", (long long)batch, (long long)n);
+    if (batch == 0 || n == 0) return NE_OK;
+    if (!c || !planes) return fail(NE_EINVAL, "ne_entangle_digits: null pointer");
+    DigitPlan P;
+    P.S = dg.S;
+    P.stored = 0;
+    P.top = 0;
+    for (int t = 0; t < 8; t++) P.slot[t] = 0;
+    for (int s2 = 0; s2 < dg.S; s2++) {
+        int t = dg.shift[s2] / 8;
+        P.stored |= 1u << t;
+        P.slot[t] = s2;
+    }
+    P.top = dg.shift[dg.S - 1] / 8;   // digits above the top planned one must be 0
+    const int T = 256;
+    if (n % 8 == 0 && aligned(c, 16) && aligned(planes, 8)) {
+        k_entangle_digits<8><<<grid_rows(batch, n / 8, T), T, 0, s>>>(c, planes, p.M, p.l, P, batch, n, status);
+    } else {
+        k_entangle_digits<1><<<grid_rows(batch, n, T), T, 0, s>>>(c, planes, p.M, p.l, P, batch, n, status);
+    }
+    return check_launch("ne_entangle_digits");
+}
+
+extern "C" ne_status ne_abft_encode(int32_t M, const int32_t* c, int64_t* x, int64_t batch, int64_t n,
+                                    cudaStream_t s) {
+    if (M < 1 || M > 64 || batch < 0 || n < 0) return fail(NE_EINVAL, "ne_abft_encode: M=%d", M);
+    if (batch == 0 || n == 0) return NE_OK;
+    if (!c || !x) return fail(NE_EINVAL, "ne_abft_encode: null pointer");
+    const int T = 256;
+    k_abft_encode<<<grid_rows(batch, n, T), T, 0, s>>>(c, x, M, batch, n);
+    return check_launch("ne_abft_encode");
+}

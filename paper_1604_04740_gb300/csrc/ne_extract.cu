@@ -1,0 +1,312 @@
+// Disentanglement (Eq. 17-20), the reliability check (Eq. 24), fail-stop
+// recovery (Prop. 3), transient-fault injection and the ABFT check/recovery
+// (Eq. 6, Sec. II-A).  HBM-bound streaming kernels.
+//
+// Work split: a warp owns a segment of 32*VEC consecutive positions of one
+// group (VEC = 2 with 16-byte loads when possible), so each segment maps to
+// whole uint32 words of the flag bitmap and the flags are assembled with
+// warp shuffles, not atomics.
+#include "ne_common.cuh"
+
+namespace {
+
+using namespace ne;
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+
+// ---- per-position extraction ---------------------------------------------------
+//
+// rot[j] holds delta_{(r+j) mod M}; rot[0] (= delta_r) is only read when the
+// check is requested.  Outputs out[j] = low 64 bits of d_{(r+j) mod M}.
+template <int MT>
+__device__ __forceinline__ bool extract_rot(const int64_t* rot, int M, int l, bool check, int64_t* out) {
+    const int Mv = MT ? MT : M;
+    // Eq. 17 by Horner's rule, times (-1)^M
+    i128 acc = 0;
+#pragma unroll
+    for (int m = 0; m < (MT ? MT - 1 : 31); m++) {
+        if (!MT && m >= Mv - 1) break;
+        i128 v = (i128)rot[1 + m];
+        acc = shl128(acc, l) + ((m & 1) ? -v : v);
+    }
+    const i128 T = (Mv & 1) ? -acc : acc;
+    const int L = (Mv - 1) * l;
+    // Eq. 18: d_{r-1} = low L bits of T, sign-extended
+    const int64_t d_last = sext_low((uint64_t)T, L);
+    // Eq. 19: d_r = floor((-1)^M (T - d_{r-1}) / 2^L)
+    i128 diff = T - (i128)d_last;
+    if (Mv & 1) diff = -diff;
+    const i128 d_r = sar128(diff, L);
+    out[0] = (int64_t)(uint64_t)d_r;
+    out[Mv - 1] = d_last;
+    // Eq. 20: d_{r+m} = delta_{r+m} - 2^l d_{r+m-1}.  Only the low 64 bits are
+    // kept, and the low 64 bits of a difference/product depend only on the low
+    // 64 bits of its operands, so wrapping 64-bit arithmetic is exact here.
+    uint64_t prev = (uint64_t)d_r;
+#pragma unroll
+    for (int j = 1; j < (MT ? MT - 1 : 31); j++) {
+        if (!MT && j >= Mv - 1) break;
+        uint64_t cur = (uint64_t)rot[j] - (prev << l);
+        out[j] = (int64_t)cur;
+        prev = cur;
+    }
+    // Eq. 24 on the exact values: delta_r versus d_r + 2^l d_{r-1}
+    bool flag = false;
+    if (check) flag = ((i128)rot[0] != d_r + shl128((i128)d_last, l));
+    return flag;
+}
+
+// flags of one segment: VEC bits per lane -> bitmap words (see file comment)
+template <int VEC>
+__device__ __forceinline__ void emit_flags(uint32_t f, int lane, int64_t seg, int64_t wpr,
+                                           uint32_t* flags_row, unsigned long long* nflag) {
+    if constexpr (VEC == 2) {
+        uint32_t v = halfwarp_or(f << (2 * (lane & 15)));
+        if ((lane & 15) == 0) {
+            int64_t w = 2 * seg + (lane >> 4);
+            if (w < wpr) {
+                if (flags_row) flags_row[w] = v;
+                if (nflag && v) atomicAdd(nflag, (unsigned long long)__popc(v));
+            }
+        }
+    } else {
+        uint32_t v = __ballot_sync(0xffffffffu, f != 0);
+        if (lane == 0 && seg < wpr) {
+            if (flags_row) flags_row[seg] = v;
+            if (nflag && v) atomicAdd(nflag, (unsigned long long)__popc(v));
+        }
+    }
+}
+
+template <int MT, int VEC, bool WRITE_D, bool CHECK>
+__global__ void __launch_bounds__(kThreads) k_extract(const int64_t* __restrict__ delta, int64_t* __restrict__ dhat,
+                                                      int M, int l, int r, int64_t batch, int64_t n,
+                                                      uint32_t* __restrict__ flags, unsigned long long* nflag) {
+    const int Mv = MT ? MT : M;
+    const int lane = threadIdx.x & 31;
+    const int64_t seg_len = 32 * VEC;
+    const int64_t nseg = (n + seg_len - 1) / seg_len;
+    const int64_t wpr = (n + 31) / 32;
+    for (int64_t b = blockIdx.y; b < batch; b += gridDim.y) {
+        const int64_t* db = delta + b * Mv * n;
+        int64_t* ob = dhat + b * Mv * n;
+        uint32_t* fb = flags ? flags + b * wpr : nullptr;
+        for (int64_t seg = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5); seg < nseg;
+             seg += (int64_t)gridDim.x * kWarps) {
+            const int64_t i = seg * seg_len + lane * VEC;
+            uint32_t f = 0;
+            if (i < n) {
+                int64_t rot[VEC][MT ? MT : 32];
+                // rotate while loading: register index j is static, address is not
+#pragma unroll
+                for (int j = 0; j < (MT ? MT : 32); j++) {
+                    if (!MT && j >= Mv) break;
+                    if (j == 0 && !CHECK) continue;
+                    int m = r + j;
+                    if (m >= Mv) m -= Mv;
+                    const int64_t* src = db + (int64_t)m * n + i;
+                    if constexpr (VEC == 2) {
+                        longlong2 v = __ldcs(reinterpret_cast<const longlong2*>(src));
+                        rot[0][j] = v.x;
+                        rot[1][j] = v.y;
+                    } else {
+                        rot[0][j] = __ldcs(src);
+                    }
+                }
+#pragma unroll
+                for (int v = 0; v < VEC; v++) {
+                    int64_t out[MT ? MT : 32];
+                    if (extract_rot<MT>(rot[v], Mv, l, CHECK, out)) f |= 1u << v;
+                    if constexpr (WRITE_D) {
+#pragma unroll
+                        for (int j = 0; j < (MT ? MT : 32); j++) {
+                            if (!MT && j >= Mv) break;
+                            rot[v][j] = out[j];
+                        }
+                    }
+                }
+                if constexpr (WRITE_D) {
+#pragma unroll
+                    for (int j = 0; j < (MT ? MT : 32); j++) {
+                        if (!MT && j >= Mv) break;
+                        int m = r + j;
+                        if (m >= Mv) m -= Mv;
+                        int64_t* dst = ob + (int64_t)m * n + i;
+                        if constexpr (VEC == 2) __stcs(reinterpret_cast<longlong2*>(dst), make_longlong2(rot[0][j], rot[1][j]));
+                        else __stcs(dst, rot[0][j]);
+                    }
+                }
+            }
+            if constexpr (CHECK) emit_flags<VEC>(f, lane, seg, wpr, fb, nflag);
+        }
+    }
+}
+
+dim3 grid_segments(int64_t batch, int64_t nseg) {
+    int64_t gy = batch < 65535 ? batch : 65535;
+    int64_t want = (int64_t)wave_blocks(kThreads, 4);
+    int64_t gx = (nseg + kWarps - 1) / kWarps;
+    int64_t cap = want / gy;
+    if (cap < 1) cap = 1;
+    if (gx > cap) gx = cap;
+    if (gx < 1) gx = 1;
+    return dim3((unsigned)gx, (unsigned)gy, 1);
+}
+
+template <int MT, bool WRITE_D, bool CHECK>
+void launch_extract_vec(const int64_t* delta, int64_t* dhat, int M, int l, int r, int64_t batch, int64_t n,
+                        uint32_t* flags, unsigned long long* nflag, cudaStream_t s) {
+    const bool vec2 = (n % 2 == 0) && aligned(delta, 16) && (!WRITE_D || aligned(dhat, 16));
+    if (vec2) {
+        dim3 g = grid_segments(batch, (n + 63) / 64);
+        k_extract<MT, 2, WRITE_D, CHECK><<<g, kThreads, 0, s>>>(delta, dhat, M, l, r, batch, n, flags, nflag);
+    } else {
+        dim3 g = grid_segments(batch, (n + 31) / 32);
+        k_extract<MT, 1, WRITE_D, CHECK><<<g, kThreads, 0, s>>>(delta, dhat, M, l, r, batch, n, flags, nflag);
+    }
+}
+
+template <bool WRITE_D, bool CHECK>
+void launch_extract(const int64_t* delta, int64_t* dhat, int M, int l, int r, int64_t batch, int64_t n,
+                    uint32_t* flags, unsigned long long* nflag, cudaStream_t s) {
+    switch (M) {
+        case 3: launch_extract_vec<3, WRITE_D, CHECK>(delta, dhat, M, l, r, batch, n, flags, nflag, s); break;
+        case 4: launch_extract_vec<4, WRITE_D, CHECK>(delta, dhat, M, l, r, batch, n, flags, nflag, s); break;
+        case 5: launch_extract_vec<5, WRITE_D, CHECK>(delta, dhat, M, l, r, batch, n, flags, nflag, s); break;
+        case 6: launch_extract_vec<6, WRITE_D, CHECK>(delta, dhat, M, l, r, batch, n, flags, nflag, s); break;
+        case 8: launch_extract_vec<8, WRITE_D, CHECK>(delta, dhat, M, l, r, batch, n, flags, nflag, s); break;
+        default: launch_extract_vec<0, WRITE_D, CHECK>(delta, dhat, M, l, r, batch, n, flags, nflag, s); break;
+    }
+}
+
+ne_status common_args(const ne_params& p, int64_t batch, int64_t n, int32_t r, const char* who) {
+    ne_status st = validate_params(p);
+    if (st) return st;
+    if (batch < 0 || n < 0) return fail(NE_EINVAL, "%s: batch=%lld n=%lld", who, (long long)batch, (long long)n);
+    if (r < 0 || r >= p.M) return fail(NE_EINVAL, "%s: r=%d not in [0, M)", who, r);
+    return NE_OK;
+}
+
+// ---- fault injection ---------------------------------------------------------
+
+__global__ void k_inject(int64_t* delta, int P, int64_t batch, int64_t n, const int64_t* group, const int64_t* pos,
+                         const int64_t* stream, const int64_t* bit, int64_t count, int32_t* status) {
+    for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < count; f += (int64_t)gridDim.x * blockDim.x) {
+        int64_t g = group[f], i = pos[f], j = stream[f], b = bit[f];
+        if (g < 0 || g >= batch || i < 0 || i >= n || j < 0 || j >= P || b < 0 || b > 63) {
+            if (status) atomicExch(status, (int32_t)NE_EINVAL);
+            continue;
+        }
+        atomicXor(reinterpret_cast<unsigned long long*>(delta + (g * P + j) * n + i), 1ull << b);
+    }
+}
+
+// ---- checksum ABFT check / recovery -----------------------------------------------
+
+__global__ void __launch_bounds__(kThreads) k_abft_check(const int64_t* __restrict__ d, int M, int64_t batch, int64_t n,
+                                                         uint32_t* __restrict__ flags, unsigned long long* nflag) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nseg = (n + 31) / 32;
+    const int64_t wpr = nseg;
+    for (int64_t b = blockIdx.y; b < batch; b += gridDim.y) {
+        const int64_t* db = d + b * (M + 1) * n;
+        uint32_t* fb = flags ? flags + b * wpr : nullptr;
+        for (int64_t seg = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5); seg < nseg;
+             seg += (int64_t)gridDim.x * kWarps) {
+            const int64_t i = seg * 32 + lane;
+            uint32_t f = 0;
+            if (i < n) {
+                i128 sum = 0;
+                for (int m = 0; m < M; m++) sum += (i128)__ldcs(db + (int64_t)m * n + i);
+                f = (sum != (i128)__ldcs(db + (int64_t)M * n + i));
+            }
+            emit_flags<1>(f, lane, seg, wpr, fb, nflag);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_abft_recover(int64_t* d, int M, int64_t batch, int64_t n, int j) {
+    for (int64_t b = blockIdx.y; b < batch; b += gridDim.y) {
+        int64_t* db = d + b * (M + 1) * n;
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+            uint64_t v = (uint64_t)db[(int64_t)M * n + i];
+            for (int m = 0; m < M; m++)
+                if (m != j) v -= (uint64_t)db[(int64_t)m * n + i];
+            db[(int64_t)j * n + i] = (int64_t)v;
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" ne_status ne_extract(ne_params p, const int64_t* delta, int64_t* d_hat, int64_t batch, int64_t n,
+                                int32_t r, uint32_t* flags, uint64_t* nflag, cudaStream_t s) {
+    ne_status st = common_args(p, batch, n, r, "ne_extract");
+    if (st) return st;
+    if (!delta || !d_hat) return fail(NE_EINVAL, "ne_extract: null pointer");
+    unsigned long long* nf = reinterpret_cast<unsigned long long*>(nflag);
+    if (nf && cudaMemsetAsync(nf, 0, sizeof(*nf), s) != cudaSuccess) return check_launch("ne_extract: reset count");
+    if (batch == 0 || n == 0) return NE_OK;
+    if (flags || nflag) launch_extract<true, true>(delta, d_hat, p.M, p.l, r, batch, n, flags, nf, s);
+    else launch_extract<true, false>(delta, d_hat, p.M, p.l, r, batch, n, nullptr, nullptr, s);
+    return check_launch("ne_extract");
+}
+
+extern "C" ne_status ne_check(ne_params p, const int64_t* delta, int64_t batch, int64_t n, int32_t r,
+                              uint32_t* flags, uint64_t* nflag, cudaStream_t s) {
+    ne_status st = common_args(p, batch, n, r, "ne_check");
+    if (st) return st;
+    if (!delta || (!flags && !nflag)) return fail(NE_EINVAL, "ne_check: null pointer");
+    unsigned long long* nf = reinterpret_cast<unsigned long long*>(nflag);
+    if (nf && cudaMemsetAsync(nf, 0, sizeof(*nf), s) != cudaSuccess) return check_launch("ne_check: reset count");
+    if (batch == 0 || n == 0) return NE_OK;
+    launch_extract<false, true>(delta, nullptr, p.M, p.l, r, batch, n, flags, nf, s);
+    return check_launch("ne_check");
+}
+
+extern "C" ne_status ne_recover(ne_params p, const int64_t* delta, int64_t* d_hat, int64_t batch, int64_t n,
+                                int32_t r_lost, cudaStream_t s) {
+    ne_status st = common_args(p, batch, n, r_lost, "ne_recover");
+    if (st) return st;
+    if (!delta || !d_hat) return fail(NE_EINVAL, "ne_recover: null pointer");
+    if (batch == 0 || n == 0) return NE_OK;
+    launch_extract<true, false>(delta, d_hat, p.M, p.l, r_lost, batch, n, nullptr, nullptr, s);
+    return check_launch("ne_recover");
+}
+
+extern "C" ne_status ne_inject(int64_t* delta, int32_t P, int64_t batch, int64_t n, const int64_t* group,
+                               const int64_t* pos, const int64_t* stream, const int64_t* bit, int64_t count,
+                               int32_t* status, cudaStream_t s) {
+    if (P < 1 || batch < 0 || n < 0 || count < 0) return fail(NE_EINVAL, "ne_inject: bad sizes");
+    if (count == 0) return NE_OK;
+    if (!delta || !group || !pos || !stream || !bit) return fail(NE_EINVAL, "ne_inject: null pointer");
+    int blocks = (int)((count + 255) / 256);
+    if (blocks > 4096) blocks = 4096;
+    k_inject<<<blocks, 256, 0, s>>>(delta, P, batch, n, group, pos, stream, bit, count, status);
+    return check_launch("ne_inject");
+}
+
+extern "C" ne_status ne_abft_check(int32_t M, const int64_t* d, int64_t batch, int64_t n, uint32_t* flags,
+                                   uint64_t* nflag, cudaStream_t s) {
+    if (M < 1 || M > 64 || batch < 0 || n < 0) return fail(NE_EINVAL, "ne_abft_check: bad sizes");
+    if (!d || (!flags && !nflag)) return fail(NE_EINVAL, "ne_abft_check: null pointer");
+    unsigned long long* nf = reinterpret_cast<unsigned long long*>(nflag);
+    if (nf && cudaMemsetAsync(nf, 0, sizeof(*nf), s) != cudaSuccess) return check_launch("ne_abft_check: reset");
+    if (batch == 0 || n == 0) return NE_OK;
+    k_abft_check<<<grid_segments(batch, (n + 31) / 32), kThreads, 0, s>>>(d, M, batch, n, flags, nf);
+    return check_launch("ne_abft_check");
+}
+
+extern "C" ne_status ne_abft_recover(int32_t M, int64_t* d, int64_t batch, int64_t n, int32_t j, cudaStream_t s) {
+    if (M < 1 || M > 64 || batch < 0 || n < 0 || j < 0 || j >= M) return fail(NE_EINVAL, "ne_abft_recover: bad args");
+    if (!d) return fail(NE_EINVAL, "ne_abft_recover: null pointer");
+    if (batch == 0 || n == 0) return NE_OK;
+    int64_t gy = batch < 65535 ? batch : 65535;
+    int64_t gx = (n + 255) / 256;
+    int64_t cap = wave_blocks(256, 4) / gy;
+    if (cap < 1) cap = 1;
+    if (gx > cap) gx = cap;
+    k_abft_recover<<<dim3((unsigned)gx, (unsigned)gy), 256, 0, s>>>(d, M, batch, n, j);
+    return check_launch("ne_abft_recover");
+}

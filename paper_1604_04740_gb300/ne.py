@@ -1,0 +1,304 @@
+"""Thin Python binding of the C ABI in include/ne.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls, takes torch
+tensors that already live on the GPU, checks dtype/device/contiguity/shape,
+passes raw device pointers and the current CUDA stream, and raises NEError
+on a non-zero status.  No computation happens in Python: if libne.so cannot
+be built or loaded, importing this module fails.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+NE_OK, NE_EINVAL, NE_ERANGE, NE_ECUDA, NE_ETIMEOUT, NE_ENOMEM = range(6)
+NE_L_PAPER, NE_L_SMALLEST, NE_L_BYTE = 0, 1, 2
+NE_FUSE_NONE, NE_FUSE_EXTRACT_CHECK, NE_FUSE_RECOVER = 0, 1, 2
+NE_MAX_DIGITS = 8
+
+
+class NEError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"status {status}: {msg}")
+        self.status = status
+
+
+class ne_params(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int32), ("l", ctypes.c_int32), ("w", ctypes.c_int32)]
+
+
+class ne_digits(ctypes.Structure):
+    _fields_ = [("S", ctypes.c_int32), ("shift", ctypes.c_int32 * NE_MAX_DIGITS)]
+
+    @property
+    def shifts(self):
+        return tuple(self.shift[i] for i in range(self.S))
+
+    def __repr__(self):
+        return f"ne_digits(S={self.S}, shift={self.shifts})"
+
+
+def params(M: int, l: int, w: int = 64) -> ne_params:
+    return ne_params(M, l, w)
+
+
+def digits(shifts) -> ne_digits:
+    d = ne_digits()
+    d.S = len(shifts)
+    for i, s in enumerate(shifts):
+        d.shift[i] = s
+    return d
+
+
+def _load():
+    path = _build.LIB
+    if not os.path.exists(path) or os.environ.get("NE_REBUILD") == "1":
+        _build.build()
+    lib = ctypes.CDLL(path)
+    P, i32, i64, u32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
+    sig = {
+        "ne_choose_l": [i32, i32, i64, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)],
+        "ne_plan_digits": [i32, i32, i32, ctypes.POINTER(ne_digits)],
+        "ne_entangle": [ne_params, P, P, i64, i64, P],
+        "ne_entangle_digits": [ne_params, ne_digits, P, P, i64, i64, P, P],
+        "ne_gemm": [i32, P, P, P, i32, i32, i32, u32, P],
+        "ne_gemm_digits": [ne_params, ne_digits, P, P, P, P, P, i32, i32, i32, i32, i32, P],
+        "ne_cconv": [i32, P, P, P, i64, i64, u32, P],
+        "ne_cconv_digits": [ne_params, ne_digits, P, P, P, P, P, i64, i64, i32, i32, P],
+        "ne_extract": [ne_params, P, P, i64, i64, i32, P, P, P],
+        "ne_check": [ne_params, P, i64, i64, i32, P, P, P],
+        "ne_recover": [ne_params, P, P, i64, i64, i32, P],
+        "ne_inject": [P, i32, i64, i64, P, P, P, P, i64, P, P],
+        "ne_abft_encode": [i32, P, P, i64, i64, P],
+        "ne_abft_check": [i32, P, i64, i64, P, P, P],
+        "ne_abft_recover": [i32, P, i64, i64, i32, P],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    lib.ne_last_error.restype = ctypes.c_char_p
+    lib.ne_version.restype = ctypes.c_char_p
+    return lib
+
+
+_lib = _load()
+LIB_PATH = _build.LIB
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _call(name: str, *args):
+    st = getattr(_lib, name)(*args)
+    if st != NE_OK:
+        raise NEError(st, _lib.ne_last_error().decode())
+
+
+def _ptr(t, dtype, name, allow_none=False):
+    if t is None:
+        if allow_none:
+            return None
+        raise ValueError(f"{name} is required")
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def ne_version() -> str:
+    return _lib.ne_version().decode()
+
+
+# ---- planning ----------------------------------------------------------------
+
+def ne_choose_l(M: int, w: int = 64, out_bound: int = 0, policy: int = NE_L_PAPER):
+    l, k = ctypes.c_int32(), ctypes.c_int32()
+    _call("ne_choose_l", M, w, int(out_bound), policy, ctypes.byref(l), ctypes.byref(k))
+    return l.value, k.value
+
+
+def ne_plan_digits(l: int, cmin: int = -128, cmax: int = 127) -> ne_digits:
+    d = ne_digits()
+    _call("ne_plan_digits", l, cmin, cmax, ctypes.byref(d))
+    return d
+
+
+# ---- entanglement --------------------------------------------------------------
+
+def _bmn(t, M):
+    """(batch, n) of a [.., M, n] plane tensor."""
+    if t.dim() < 2 or t.shape[-2] != M:
+        raise ValueError(f"expected [..., {M}, n] planes, got {tuple(t.shape)}")
+    n = t.shape[-1]
+    batch = t.numel() // (M * n) if n else 0
+    return batch, n
+
+
+def ne_entangle(p: ne_params, c: torch.Tensor, eps: torch.Tensor | None = None) -> torch.Tensor:
+    batch, n = _bmn(c, p.M)
+    if eps is None:
+        eps = torch.empty(c.shape, dtype=torch.int64, device=c.device)
+    if eps.shape != c.shape:
+        raise ValueError("eps must have the shape of c")
+    _call("ne_entangle", p, _ptr(c, torch.int32, "c"), _ptr(eps, torch.int64, "eps"), batch, n, _stream())
+    return eps
+
+
+def ne_entangle_digits(p: ne_params, dg: ne_digits, c: torch.Tensor, planes: torch.Tensor | None = None,
+                       status: torch.Tensor | None = None) -> torch.Tensor:
+    """planes: int8 [..., M, S, n] (the shape of c with S inserted)."""
+    batch, n = _bmn(c, p.M)
+    shape = tuple(c.shape[:-1]) + (dg.S, n)
+    if planes is None:
+        planes = torch.empty(shape, dtype=torch.int8, device=c.device)
+    if tuple(planes.shape) != shape:
+        raise ValueError(f"planes must be {shape}")
+    _call("ne_entangle_digits", p, dg, _ptr(c, torch.int32, "c"), _ptr(planes, torch.int8, "planes"), batch, n,
+          _ptr(status, torch.int32, "status", True), _stream())
+    return planes
+
+
+# ---- operations ----------------------------------------------------------------
+
+def ne_gemm(x: torch.Tensor, G: torch.Tensor, out: torch.Tensor | None = None, skip_mask: int = 0) -> torch.Tensor:
+    """x int64 [P, rows, k] @ G int8 [k, cols] -> int64 [P, rows, cols]."""
+    P, rows, k = x.shape
+    k2, cols = G.shape
+    if k != k2:
+        raise ValueError("inner dimensions differ")
+    if out is None:
+        out = torch.empty((P, rows, cols), dtype=torch.int64, device=x.device)
+    if tuple(out.shape) != (P, rows, cols):
+        raise ValueError("out shape")
+    _call("ne_gemm", P, _ptr(x, torch.int64, "x"), _ptr(G, torch.int8, "G"), _ptr(out, torch.int64, "out"),
+          rows, cols, k, skip_mask, _stream())
+    return out
+
+
+def ne_gemm_digits(p: ne_params, dg: ne_digits, planes: torch.Tensor, G: torch.Tensor,
+                   out: torch.Tensor | None = None, flags: torch.Tensor | None = None,
+                   nflag: torch.Tensor | None = None, fuse: int = NE_FUSE_EXTRACT_CHECK, r: int = 0) -> torch.Tensor:
+    """planes int8 [M, S, rows, k]; G int8 [k, cols] -> int64 [M, rows, cols]."""
+    M, S, rows, k = planes.shape
+    if M != p.M or S != dg.S:
+        raise ValueError("planes shape does not match (M, S)")
+    k2, cols = G.shape
+    if k != k2:
+        raise ValueError("inner dimensions differ")
+    if out is None:
+        out = torch.empty((M, rows, cols), dtype=torch.int64, device=planes.device)
+    _call("ne_gemm_digits", p, dg, _ptr(planes, torch.int8, "planes"), _ptr(G, torch.int8, "G"),
+          _ptr(out, torch.int64, "out"), _ptr(flags, torch.int32, "flags", True),
+          _ptr(nflag, torch.int64, "nflag", True), rows, cols, k, fuse, r, _stream())
+    return out
+
+
+def ne_cconv(x: torch.Tensor, g: torch.Tensor, out: torch.Tensor | None = None, skip_mask: int = 0) -> torch.Tensor:
+    """x int64 [batch, P, N], g int8 [batch, N] -> int64 [batch, P, N]."""
+    batch, P, N = x.shape
+    if tuple(g.shape) != (batch, N):
+        raise ValueError("g must be [batch, N]")
+    if out is None:
+        out = torch.empty_like(x)
+    _call("ne_cconv", P, _ptr(x, torch.int64, "x"), _ptr(g, torch.int8, "g"), _ptr(out, torch.int64, "out"),
+          batch, N, skip_mask, _stream())
+    return out
+
+
+def ne_cconv_digits(p: ne_params, dg: ne_digits, planes: torch.Tensor, g: torch.Tensor,
+                    out: torch.Tensor | None = None, flags: torch.Tensor | None = None,
+                    nflag: torch.Tensor | None = None, fuse: int = NE_FUSE_EXTRACT_CHECK, r: int = 0) -> torch.Tensor:
+    """planes int8 [batch, M, S, N]; g int8 [batch, N] -> int64 [batch, M, N]."""
+    batch, M, S, N = planes.shape
+    if M != p.M or S != dg.S or tuple(g.shape) != (batch, N):
+        raise ValueError("planes / g shapes")
+    if out is None:
+        out = torch.empty((batch, M, N), dtype=torch.int64, device=planes.device)
+    _call("ne_cconv_digits", p, dg, _ptr(planes, torch.int8, "planes"), _ptr(g, torch.int8, "g"),
+          _ptr(out, torch.int64, "out"), _ptr(flags, torch.int32, "flags", True),
+          _ptr(nflag, torch.int64, "nflag", True), batch, N, fuse, r, _stream())
+    return out
+
+
+# ---- extraction / check / recovery ---------------------------------------------
+
+def flag_words(batch: int, n: int) -> int:
+    return batch * ((n + 31) // 32)
+
+
+def ne_extract(p: ne_params, delta: torch.Tensor, d_hat: torch.Tensor | None = None, r: int = 0,
+               flags: torch.Tensor | None = None, nflag: torch.Tensor | None = None) -> torch.Tensor:
+    batch, n = _bmn(delta, p.M)
+    if d_hat is None:
+        d_hat = torch.empty_like(delta)
+    _call("ne_extract", p, _ptr(delta, torch.int64, "delta"), _ptr(d_hat, torch.int64, "d_hat"), batch, n, r,
+          _ptr(flags, torch.int32, "flags", True), _ptr(nflag, torch.int64, "nflag", True), _stream())
+    return d_hat
+
+
+def ne_check(p: ne_params, delta: torch.Tensor, r: int = 0, flags: torch.Tensor | None = None,
+             nflag: torch.Tensor | None = None):
+    batch, n = _bmn(delta, p.M)
+    if flags is None:
+        flags = torch.empty(flag_words(batch, n), dtype=torch.int32, device=delta.device)
+    _call("ne_check", p, _ptr(delta, torch.int64, "delta"), batch, n, r, _ptr(flags, torch.int32, "flags", True),
+          _ptr(nflag, torch.int64, "nflag", True), _stream())
+    return flags
+
+
+def ne_recover(p: ne_params, delta: torch.Tensor, r_lost: int, d_hat: torch.Tensor | None = None) -> torch.Tensor:
+    batch, n = _bmn(delta, p.M)
+    if d_hat is None:
+        d_hat = torch.empty_like(delta)
+    _call("ne_recover", p, _ptr(delta, torch.int64, "delta"), _ptr(d_hat, torch.int64, "d_hat"), batch, n, r_lost,
+          _stream())
+    return d_hat
+
+
+def ne_inject(delta: torch.Tensor, P: int, group, pos, stream, bit, status: torch.Tensor | None = None):
+    """delta int64 [batch, P, n]; fault lists int64 device tensors of equal length."""
+    batch, n = _bmn(delta, P)
+    count = group.numel()
+    for t in (pos, stream, bit):
+        if t.numel() != count:
+            raise ValueError("fault lists differ in length")
+    _call("ne_inject", _ptr(delta, torch.int64, "delta"), P, batch, n, _ptr(group, torch.int64, "group"),
+          _ptr(pos, torch.int64, "pos"), _ptr(stream, torch.int64, "stream"), _ptr(bit, torch.int64, "bit"),
+          count, _ptr(status, torch.int32, "status", True), _stream())
+
+
+# ---- checksum ABFT ---------------------------------------------------------------
+
+def ne_abft_encode(M: int, c: torch.Tensor, x: torch.Tensor | None = None) -> torch.Tensor:
+    batch, n = _bmn(c, M)
+    shape = tuple(c.shape[:-2]) + (M + 1, n)
+    if x is None:
+        x = torch.empty(shape, dtype=torch.int64, device=c.device)
+    _call("ne_abft_encode", M, _ptr(c, torch.int32, "c"), _ptr(x, torch.int64, "x"), batch, n, _stream())
+    return x
+
+
+def ne_abft_check(M: int, d: torch.Tensor, flags: torch.Tensor | None = None, nflag: torch.Tensor | None = None):
+    batch, n = _bmn(d, M + 1)
+    if flags is None:
+        flags = torch.empty(flag_words(batch, n), dtype=torch.int32, device=d.device)
+    _call("ne_abft_check", M, _ptr(d, torch.int64, "d"), batch, n, _ptr(flags, torch.int32, "flags", True),
+          _ptr(nflag, torch.int64, "nflag", True), _stream())
+    return flags
+
+
+def ne_abft_recover(M: int, d: torch.Tensor, j: int) -> torch.Tensor:
+    batch, n = _bmn(d, M + 1)
+    _call("ne_abft_recover", M, _ptr(d, torch.int64, "d"), batch, n, j, _stream())
+    return d
