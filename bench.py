@@ -1,0 +1,599 @@
+#!/usr/bin/env python
+"""Benchmark of the numerical-entanglement hot path on GB300.
+
+A step is one pass of the whole path over one batch of synthetic input:
+entangle the M streams (stored as int8 digit planes), run the operation on
+every entangled stream on the int8 tensor path, and extract + check every
+output position (fused into the operation's epilogue).
+
+Workloads (--workload):
+  cconv   batched circular convolution: 4096 groups x M = 3 streams of
+          length-1024 int32 signals in [-128, 127], one int8 filter per group
+          (the default; the configuration the headline metric is quoted on)
+  gemm    M = 4 streams of 4096 x 4096 int32 matrices times one shared
+          4096 x 4096 int8 matrix
+  gemm64  M = 3 streams of 64 x 64 times a shared 64 x 64 int8 matrix on the
+          int64 CUDA-core form (latency-bound)
+
+metric: useful integer operations per second, 2 * (multiply-adds of the
+operation on the raw streams) / time, in Gop/s.  All results are exact; the
+extracted outputs of sampled groups are compared with the CPU oracle in the
+cpu_baseline leg.
+
+--impl reference times the CPU oracle (the plain C reference of the method)
+on a bounded sample per step and prints the same JSON line with
+"impl": "reference".
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "entangled int GEMM/conv Gop/s & overhead % vs plain, same GB300, bit-exact"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=None)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cconv", choices=["cconv", "gemm", "gemm64"])
+    ap.add_argument("--no-extras", action="store_true", help="skip overhead, ABFT and CPU-baseline legs")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target length of the CPU-baseline sample")
+    a = ap.parse_args()
+    if a.steps is None:
+        a.steps = {"cconv": 400, "gemm": 20, "gemm64": 2000}[a.workload]
+    return a
+
+
+# ---- workload definitions ---------------------------------------------------------
+
+class Workload:
+    def __init__(self, name):
+        from paper_1604_04740_gb300 import inputs
+        self.name = name
+        if name == "cconv":
+            self.G, self.M, self.N = 4096, 3, 1024
+            self.c = inputs.streams(0, (self.G, self.M, self.N))
+            self.g = inputs.operator_int8(0, (self.G, self.N))
+            self.bound = self.N * 2 ** 14
+            self.useful_ops = 2 * self.G * self.M * self.N ** 2
+            self.desc = f"batched circular convolution: {self.G} groups x M={self.M} x N={self.N}, int8 filter per group"
+        elif name == "gemm":
+            self.M, self.n = 4, 4096
+            self.c = inputs.streams(0, (self.M, self.n, self.n))
+            self.Gm = inputs.operator_int8(0, (self.n, self.n))
+            self.bound = self.n * 2 ** 14
+            self.useful_ops = 2 * self.M * self.n ** 3
+            self.desc = f"GEMM: M={self.M} streams of {self.n}x{self.n} int32 times a shared {self.n}x{self.n} int8"
+        else:
+            self.M, self.n = 3, 64
+            self.c = inputs.streams(0, (self.M, self.n, self.n))
+            self.Gm = inputs.operator_int8(0, (self.n, self.n))
+            self.bound = self.n * 2 ** 14
+            self.useful_ops = 2 * self.M * self.n ** 3
+            self.desc = f"GEMM: M={self.M} streams of {self.n}x{self.n} times a shared {self.n}x{self.n} int8, int64 CUDA-core form"
+
+
+# ---- clock sampling ------------------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "50"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---- timing helpers ---------------------------------------------------------------------
+
+def timed_steps(torch, step, K, W, flush, inner=None):
+    """Run W warm-up steps, then K timed steps with an L2 flush before each
+    (outside the events).  Returns (total ms of the K steps, list of inner
+    kernel ms if `inner` events are produced by step)."""
+    for _ in range(W):
+        step(None)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    inner_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    for k in range(K):
+        flush.add_(1)
+        ev[k][0].record(stream)
+        step(inner_ev[k])
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    total = sum(a.elapsed_time(b) for a, b in ev)
+    inner_ms = [a.elapsed_time(b) for a, b in inner_ev] if inner else None
+    return total, inner_ms
+
+
+def source_hash(*names):
+    h = hashlib.sha256()
+    for n in names:
+        with open(os.path.join(ROOT, "paper_1604_04740_gb300", "csrc", n), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(kernel, src_files):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current source of the kernel; else None."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    try:
+        rec = json.load(open(path)).get(kernel)
+    except Exception:
+        return None
+    if not rec or rec.get("source_hash") != source_hash(*src_files):
+        return None
+    return rec.get("bytes_per_launch")
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# ---- the CPU oracle (cpu_baseline leg and the reference arm) ---------------------------
+
+def oracle_sample(wl, seconds, compare=None):
+    """Time the oracle's entangled pipeline on a bounded sample of the
+    workload.  Returns (Gop/s, threads, sample description, parity)."""
+    import oracle
+    from paper_1604_04740_gb300 import inputs  # noqa: F401
+    if wl.name == "cconv":
+        l, _ = oracle.choose_l(wl.M, 64, wl.bound, oracle.POLICY_BYTE)
+        t0 = time.perf_counter()
+        oracle.cconv_entangled(wl.c[:1], wl.g[:1], l, 0)
+        one = time.perf_counter() - t0
+        ng = int(max(1, min(wl.G, seconds / max(one, 1e-3))))
+        t0 = time.perf_counter()
+        dh, fl, _ = oracle.cconv_entangled(wl.c[:ng], wl.g[:ng], l, 0)
+        dt = time.perf_counter() - t0
+        ops = 2 * ng * wl.M * wl.N ** 2
+        parity = None
+        if compare is not None:
+            parity = bool((compare[:ng] == dh).all() and not fl.any())
+        return ops / dt / 1e9, oracle.threads(), f"{ng} of {wl.G} groups (entangle + convolution + extract/check)", parity
+    # GEMM: a band of rows of every stream
+    M, n = wl.M, wl.c.shape[1]
+    l, _ = oracle.choose_l(M, 64, wl.bound, oracle.POLICY_BYTE if wl.name == "gemm" else oracle.POLICY_SMALLEST)
+    t0 = time.perf_counter()
+    oracle.gemm_entangled(wl.c[:, :1, :], wl.Gm, l, 0)
+    one = time.perf_counter() - t0
+    nr = int(max(1, min(n, seconds / max(one, 1e-3))))
+    t0 = time.perf_counter()
+    dh, fl, _ = oracle.gemm_entangled(np.ascontiguousarray(wl.c[:, :nr, :]), wl.Gm, l, 0)
+    dt = time.perf_counter() - t0
+    ops = 2 * M * nr * n * wl.Gm.shape[1]
+    parity = None
+    if compare is not None:
+        parity = bool((compare[:, :nr, :] == dh).all() and not fl.any())
+    return ops / dt / 1e9, oracle.threads(), f"{nr} of {n} rows of every stream (entangle + product + extract/check)", parity
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    wl = Workload(args.workload)
+    per_step = max(0.5, min(10.0, 150.0 / max(1, args.steps + args.warmup)))
+    vals = []
+    desc = threads = None
+    for k in range(args.warmup + args.steps):
+        v, threads, desc, _ = oracle_sample(wl, per_step)
+        if k >= args.warmup:
+            vals.append(v)
+    value = statistics.mean(vals)
+    line = {"metric": METRIC, "impl": "reference", "value": value, "unit": "Gop/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": wl.useful_ops / (value * 1e9) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic", "config": {"workload": wl.desc},
+            "cpu_baseline": {"value": value, "unit": "Gop/s", "cores": threads, "kind": "oracle",
+                             "sample": f"per step: {desc}"},
+            "e2e": {"value": value, "unit": "Gop/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---- our path ---------------------------------------------------------------------------
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_1604_04740_gb300 import ne
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    wl = Workload(args.workload)
+    K, W = args.steps, args.warmup
+    flush = torch.zeros(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    extras = {}
+
+    if wl.name == "cconv":
+        M, G, N = wl.M, wl.G, wl.N
+        l, k = ne.ne_choose_l(M, 64, wl.bound, ne.NE_L_BYTE)
+        p = ne.params(M, l)
+        dg = ne.ne_plan_digits(l, -128, 127)
+        c = torch.from_numpy(wl.c).to(dev)
+        g = torch.from_numpy(wl.g).to(dev)
+        planes = torch.empty((G, M, dg.S, N), dtype=torch.int8, device=dev)
+        out = torch.empty((G, M, N), dtype=torch.int64, device=dev)
+        flags = torch.empty(G * N // 32, dtype=torch.int32, device=dev)
+        nflag = torch.zeros(1, dtype=torch.int64, device=dev)
+        status = torch.zeros(1, dtype=torch.int32, device=dev)
+        stream = torch.cuda.current_stream()
+
+        def step(ev):
+            ne.ne_entangle_digits(p, dg, c, planes, status)
+            if ev is not None:
+                ev[0].record(stream)
+            ne.ne_cconv_digits(p, dg, planes, g, out, flags, nflag, ne.NE_FUSE_EXTRACT_CHECK, 0)
+            if ev is not None:
+                ev[1].record(stream)
+
+        launches_per_step = 2
+        mma_ops_per_launch = 2 * G * M * dg.S * N * N
+        dominant = "ne_cconv_digits"
+        dom_src = ("ne_cconv_digits.cu", "ne_extract.cuh", "ne_mma.cuh")
+        h2d = wl.c.nbytes + wl.g.nbytes
+        d2h = out.numel() * 8 + flags.numel() * 4 + 8
+        cfg = {"workload": wl.desc, "l": l, "k": k, "digits": list(dg.shifts), "global_batch": G,
+               "l2": "flushed (256 MiB write) before every timed step", "parallelism": f"replicas x{world}"}
+    elif wl.name == "gemm":
+        M, n = wl.M, wl.n
+        l, k = ne.ne_choose_l(M, 64, wl.bound, ne.NE_L_BYTE)
+        p = ne.params(M, l)
+        dg = ne.ne_plan_digits(l, -128, 127)
+        c = torch.from_numpy(wl.c).to(dev).reshape(M, n * n)
+        Gm = torch.from_numpy(wl.Gm).to(dev)
+        planes = torch.empty((M, dg.S, n * n), dtype=torch.int8, device=dev)
+        out = torch.empty((M, n, n), dtype=torch.int64, device=dev)
+        flags = torch.empty(n * n // 32, dtype=torch.int32, device=dev)
+        nflag = torch.zeros(1, dtype=torch.int64, device=dev)
+        status = torch.zeros(1, dtype=torch.int32, device=dev)
+        stream = torch.cuda.current_stream()
+        pl4 = planes.view(M, dg.S, n, n)
+
+        def step(ev):
+            ne.ne_entangle_digits(p, dg, c, planes, status)
+            if ev is not None:
+                ev[0].record(stream)
+            ne.ne_gemm_digits(p, dg, pl4, Gm, out, flags, nflag, ne.NE_FUSE_EXTRACT_CHECK, 0)
+            if ev is not None:
+                ev[1].record(stream)
+
+        launches_per_step = 2
+        mma_ops_per_launch = 2 * M * dg.S * n ** 3
+        dominant = "ne_gemm_digits"
+        dom_src = ("ne_gemm_digits.cu", "ne_extract.cuh", "ne_mma.cuh")
+        h2d = wl.c.nbytes + wl.Gm.nbytes
+        d2h = out.numel() * 8 + flags.numel() * 4 + 8
+        cfg = {"workload": wl.desc, "l": l, "k": k, "digits": list(dg.shifts),
+               "l2": "flushed (256 MiB write) before every timed step", "parallelism": f"replicas x{world}"}
+    else:
+        M, n = wl.M, wl.n
+        l, k = ne.ne_choose_l(M, 64, wl.bound, ne.NE_L_SMALLEST)
+        p = ne.params(M, l)
+        c = torch.from_numpy(wl.c).to(dev).reshape(M, n * n)
+        Gm = torch.from_numpy(wl.Gm).to(dev)
+        eps = torch.empty((M, n * n), dtype=torch.int64, device=dev)
+        delta = torch.empty((M, n, n), dtype=torch.int64, device=dev)
+        out = torch.empty((1, M, n * n), dtype=torch.int64, device=dev)
+        flags = torch.empty(n * n // 32, dtype=torch.int32, device=dev)
+        nflag = torch.zeros(1, dtype=torch.int64, device=dev)
+        stream = torch.cuda.current_stream()
+
+        def step(ev):
+            ne.ne_entangle(p, c, eps)
+            if ev is not None:
+                ev[0].record(stream)
+            ne.ne_gemm(eps.view(M, n, n), Gm, delta)
+            if ev is not None:
+                ev[1].record(stream)
+            ne.ne_extract(p, delta.view(1, M, n * n), out, 0, flags, nflag)
+
+        launches_per_step = 3
+        mma_ops_per_launch = None
+        dominant = "ne_gemm (int64)"
+        dom_src = ("ne_ops_i64.cu",)
+        h2d = wl.c.nbytes + wl.Gm.nbytes
+        d2h = out.numel() * 8 + flags.numel() * 4 + 8
+        cfg = {"workload": wl.desc, "l": l, "k": k, "l2": "flushed (256 MiB write) before every timed step",
+               "parallelism": f"replicas x{world}"}
+
+    # --- main timed region ---------------------------------------------------------------
+    import torch.distributed as dist
+    try:
+        smi_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        smi_id = str(local_rank)
+    sampler = ClockSampler(smi_id)
+    for _ in range(W):
+        step(None)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.15)
+    total_ms, inner = timed_steps(torch, step, K, 0, flush, inner=True)
+    clocks = sampler.stop()
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / K
+    value = wl.useful_ops * world / (ms_per_step * 1e-3) / 1e9
+    assert int(nflag.item()) == 0, "clean data flagged"
+    if wl.name != "gemm64":
+        assert int(status.item()) == 0, "digit plan violated"
+
+    # --- roofline of the dominant kernel ---------------------------------------------------
+    inner_avg = statistics.mean(inner)
+    peaks = measured_peaks()
+    if mma_ops_per_launch is not None:
+        # live ceiling of the int8 tensor instruction (register-resident probe)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ne.ne_probe_mma_peak(64)
+        e0.record(stream)
+        ops = ne.ne_probe_mma_peak(4096)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        peak = ops / (e0.elapsed_time(e1) * 1e-3) / 1e12
+        achieved = mma_ops_per_launch / (inner_avg * 1e-3) / 1e12
+        roof = {"bound": "tensor", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "TOP/s",
+                "frac": achieved / peak, "traffic": traffic_for(dominant, dom_src),
+                "peak_source": "measured in this run: mma.sync.m16n8k32 s8 register-resident probe (ne_probe_mma_peak); "
+                               "MEASURED_PEAKS.json has no int8 figure and sm_103a has no tcgen05 integer MMA",
+                "algorithmic": f"{mma_ops_per_launch} int8 ops per launch (2 x M x S x units)",
+                "ms_per_launch": inner_avg}
+    else:
+        roof = {"bound": "alu", "kernel": dominant, "achieved": wl.useful_ops / (inner_avg * 1e-3) / 1e12,
+                "peak": None, "unit": "TOP/s", "frac": None, "traffic": None, "ms_per_launch": inner_avg}
+    hbm_peak = peaks.get("hbm_gbs")
+
+    # --- end to end through host buffers -----------------------------------------------------
+    c_host = torch.from_numpy(wl.c).pin_memory()
+    op_host = torch.from_numpy(wl.g if wl.name == "cconv" else wl.Gm).pin_memory()
+    out_host = torch.empty(out.shape, dtype=torch.int64).pin_memory()
+    flags_host = torch.empty(flags.shape, dtype=torch.int32).pin_memory()
+    nflag_host = torch.empty(1, dtype=torch.int64).pin_memory()
+    c_dev_view = c.view(wl.c.shape)
+    op_dev = g if wl.name == "cconv" else Gm
+
+    def e2e_step(ev):
+        c_dev_view.copy_(c_host, non_blocking=True)
+        op_dev.copy_(op_host, non_blocking=True)
+        step(None)
+        out_host.copy_(out, non_blocking=True)
+        flags_host.copy_(flags, non_blocking=True)
+        nflag_host.copy_(nflag, non_blocking=True)
+
+    Ke = max(3, min(K, 50))
+    e2e_ms, _ = timed_steps(torch, e2e_step, Ke, 2, flush)
+    e2e = {"value": wl.useful_ops * world / (e2e_ms / Ke * 1e-3) / 1e9, "unit": "Gop/s",
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms / Ke}
+
+    # --- overheads, ABFT comparator, recovery, CPU baseline -------------------------------------
+    cpu = None
+    if not args.no_extras and wl.name == "cconv":
+        extras = cconv_extras(torch, ne, wl, dev, flush, step, p, dg, planes, g, out, ms_per_step, hbm_peak)
+    elif not args.no_extras and wl.name == "gemm":
+        extras = gemm_extras(torch, ne, wl, dev, flush, p, dg, pl4, Gm, out, ms_per_step)
+    if not args.no_extras and rank == 0:
+        host_out = out.cpu().numpy()
+        if wl.name == "gemm64":
+            host_out = host_out.reshape(wl.M, wl.n, wl.n)
+        v, threads, desc, parity = oracle_sample(wl, args.cpu_seconds, compare=host_out)
+        cpu = {"value": v, "unit": "Gop/s", "cores": threads, "kind": "oracle", "sample": desc,
+               "outputs_match_gpu": parity}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "Gop/s", "n_gpus": world, "steps": K, "warmup": W,
+                "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "s8" if mma_ops_per_launch is not None else "int64", "data": "synthetic",
+                "config": cfg, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "gpu_launches": launches_per_step * K}
+        line.update(extras)
+        print(json.dumps(line), flush=True)
+
+
+def cconv_extras(torch, ne, wl, dev, flush, step, p, dg, planes, g, out, ms_step, hbm_peak):
+    """Overhead of entanglement against the plain operation, the checksum
+    ABFT comparator and fail-stop recovery, all on this GPU."""
+    M, G, N = wl.M, wl.G, wl.N
+    K, W = 20, 3
+    stream = torch.cuda.current_stream()
+    res = {}
+    x64 = torch.from_numpy(wl.c.astype(np.int64)).to(dev)       # raw streams as int64 words
+    c = torch.from_numpy(wl.c).to(dev)
+    # (1) plain, same tensor kernel and digit count as the entangled words
+    raw_planes = torch.empty_like(planes)
+    dg_same = ne.digits(dg.shifts)
+    out2 = torch.empty_like(out)
+
+    def plain_same(ev):
+        ne.ne_split_digits(dg_same, x64, M, raw_planes)
+        ne.ne_cconv_digits(p, dg_same, raw_planes, g, out2, None, None, ne.NE_FUSE_NONE, 0)
+
+    t_same, _ = timed_steps(torch, plain_same, K, W, flush)
+    # (2) plain, fewest digits the raw int8-valued streams need (one)
+    dg1 = ne.digits((0,))
+    raw1 = torch.empty((G, M, 1, N), dtype=torch.int8, device=dev)
+
+    def plain_min(ev):
+        ne.ne_split_digits(dg1, x64, M, raw1)
+        ne.ne_cconv_digits(p, dg1, raw1, g, out2, None, None, ne.NE_FUSE_NONE, 0)
+
+    t_min, _ = timed_steps(torch, plain_min, K, W, flush)
+    ent_ms = ms_step
+    # (3) int64 CUDA-core family: the same direct kernel on raw and entangled words
+    pl = ne.params(M, ne.ne_choose_l(M, 64, wl.bound, ne.NE_L_SMALLEST)[0])
+    eps = torch.empty((G, M, N), dtype=torch.int64, device=dev)
+    d64 = torch.empty_like(eps)
+    o64 = torch.empty_like(eps)
+    fl = torch.empty(G * N // 32, dtype=torch.int32, device=dev)
+    Ki = 4
+
+    def plain_i64(ev):
+        ne.ne_cconv(x64, g, d64)
+
+    def ent_i64(ev):
+        ne.ne_entangle(pl, c, eps)
+        ne.ne_cconv(eps, g, d64)
+        ne.ne_extract(pl, d64, o64, 0, fl, None)
+
+    t_pi, _ = timed_steps(torch, plain_i64, Ki, 1, flush)
+    t_ei, _ = timed_steps(torch, ent_i64, Ki, 1, flush)
+    # (4) checksum ABFT on the tensor path: M+1 streams, two digits (the checksum needs 9 bits)
+    x5 = torch.empty((G, M + 1, N), dtype=torch.int64, device=dev)
+    dgA = ne.digits((0, 8))
+    aplanes = torch.empty((G, M + 1, 2, N), dtype=torch.int8, device=dev)
+    aout = torch.empty((G, M + 1, N), dtype=torch.int64, device=dev)
+    pA = ne.params(M + 1, 1)
+    nfa = torch.zeros(1, dtype=torch.int64, device=dev)
+
+    def abft_tensor(ev):
+        ne.ne_abft_encode(M, c, x5)
+        ne.ne_split_digits(dgA, x5, M + 1, aplanes)
+        ne.ne_cconv_digits(pA, dgA, aplanes, g, aout, None, None, ne.NE_FUSE_NONE, 0)
+        ne.ne_abft_check(M, aout, fl, nfa)
+
+    t_abft, _ = timed_steps(torch, abft_tensor, K, W, flush)
+    # (5) checksum ABFT, int64 family
+    a64 = torch.empty((G, M + 1, N), dtype=torch.int64, device=dev)
+
+    def abft_i64(ev):
+        ne.ne_abft_encode(M, c, x5)
+        ne.ne_cconv(x5, g, a64)
+        ne.ne_abft_check(M, a64, fl, nfa)
+
+    t_ai, _ = timed_steps(torch, abft_i64, Ki, 1, flush)
+    # (6) fail-stop: stream 1 lost, all outputs from the other two
+    def recover(ev):
+        ne.ne_entangle_digits(p, dg, c, planes)
+        ne.ne_cconv_digits(p, dg, planes, g, out2, None, None, ne.NE_FUSE_RECOVER, 1)
+
+    t_rec, _ = timed_steps(torch, recover, K, W, flush)
+    # (7) the entangle pass alone: HBM roofline of the streaming kernel
+    def ent_only(ev):
+        ne.ne_entangle_digits(p, dg, c, planes)
+
+    t_e, _ = timed_steps(torch, ent_only, K, W, flush)
+    ent_bytes = wl.c.nbytes + planes.numel()
+    torch.cuda.synchronize()
+    ms = lambda t, k: t / k  # noqa: E731
+    res["overhead_pct"] = {
+        "vs_plain_same_kernel_same_digits": 100 * (ent_ms / ms(t_same, K) - 1),
+        "vs_plain_fewest_digits": 100 * (ent_ms / ms(t_min, K) - 1),
+        "int64_family": 100 * (ms(t_ei, Ki) / ms(t_pi, Ki) - 1),
+        "abft_tensor_vs_plain_same_kernel": 100 * (ms(t_abft, K) / ms(t_same, K) - 1),
+        "abft_int64_vs_plain_int64": 100 * (ms(t_ai, Ki) / ms(t_pi, Ki) - 1),
+    }
+    res["ms"] = {"entangled_step": ent_ms, "plain_same_digits": ms(t_same, K), "plain_one_digit": ms(t_min, K),
+                 "plain_int64": ms(t_pi, Ki), "entangled_int64": ms(t_ei, Ki), "abft_tensor": ms(t_abft, K),
+                 "abft_int64": ms(t_ai, Ki), "fail_stop_recovery_step": ms(t_rec, K),
+                 "entangle_digits_pass": ms(t_e, K)}
+    res["entangle_pass_hbm"] = {"bytes": ent_bytes, "GB/s": ent_bytes / (ms(t_e, K) * 1e-3) / 1e9,
+                                "peak_GB/s": hbm_peak, "frac": (ent_bytes / (ms(t_e, K) * 1e-3) / 1e9 / hbm_peak)
+                                if hbm_peak else None}
+    return res
+
+
+def gemm_extras(torch, ne, wl, dev, flush, p, dg, planes, Gm, out, ms_step):
+    M, n = wl.M, wl.n
+    K, W = 5, 2
+    x64 = torch.from_numpy(wl.c.astype(np.int64)).to(dev).reshape(M, n * n)
+    raw = torch.empty_like(planes)
+    out2 = torch.empty_like(out)
+    dg_same = ne.digits(dg.shifts)
+
+    def plain_same(ev):
+        ne.ne_split_digits(dg_same, x64, M, raw.view(M, dg.S, n * n))
+        ne.ne_gemm_digits(p, dg_same, raw, Gm, out2, None, None, ne.NE_FUSE_NONE, 0)
+
+    t_same, _ = timed_steps(torch, plain_same, K, W, flush)
+    dg1 = ne.digits((0,))
+    raw1 = torch.empty((M, 1, n, n), dtype=torch.int8, device=dev)
+
+    def plain_min(ev):
+        ne.ne_split_digits(dg1, x64, M, raw1.view(M, 1, n * n))
+        ne.ne_gemm_digits(p, dg1, raw1, Gm, out2, None, None, ne.NE_FUSE_NONE, 0)
+
+    t_min, _ = timed_steps(torch, plain_min, K, W, flush)
+    return {"overhead_pct": {"vs_plain_same_kernel_same_digits": 100 * (ms_step / (t_same / K) - 1),
+                             "vs_plain_fewest_digits": 100 * (ms_step / (t_min / K) - 1)},
+            "ms": {"entangled_step": ms_step, "plain_same_digits": t_same / K, "plain_one_digit": t_min / K}}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

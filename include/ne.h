@@ -114,6 +114,13 @@ ne_status ne_entangle(ne_params p, const int32_t* c, int64_t* eps,
 ne_status ne_entangle_digits(ne_params p, ne_digits dg, const int32_t* c, int8_t* planes,
                              int64_t batch, int64_t n, int32_t* status, cudaStream_t s);
 
+/* Digit planes of arbitrary int64 words (entangled words produced elsewhere,
+ * or the raw and checksum streams of the ABFT comparator): x is int64
+ * [batch][P][n], planes is int8 [batch][P][dg.S][n].  Out-of-plan words set
+ * *status = NE_ERANGE as for ne_entangle_digits. */
+ne_status ne_split_digits(ne_digits dg, const int64_t* x, int8_t* planes, int64_t batch, int32_t P,
+                          int64_t n, int32_t* status, cudaStream_t s);
+
 /* ------------------------------------------------------------------------ */
 /* The LSB operation on each stream (Eq. 10), unaware of the entanglement    */
 /* ------------------------------------------------------------------------ */
@@ -219,6 +226,13 @@ ne_status ne_abft_recover(int32_t M, int64_t* d, int64_t batch, int64_t n, int32
                           cudaStream_t s);
 
 /* ------------------------------------------------------------------------ */
+
+/* Measurement support (no counterpart in the paper): runs a register-resident
+ * loop of mma.sync.m16n8k32 s8 instructions on every SM -- the throughput
+ * ceiling of the int8 tensor path on sm_103a -- and writes the number of
+ * int8 operations (2 per multiply-add) it issued to *ops (host pointer).
+ * The caller times the launch on stream s. */
+ne_status ne_probe_mma_peak(int32_t iters, int64_t* ops, cudaStream_t s);
 
 /* Message of the last failed call on this host thread ("" if none). */
 const char* ne_last_error(void);

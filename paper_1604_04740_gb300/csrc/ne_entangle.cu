@@ -222,3 +222,52 @@ extern "C" ne_status ne_abft_encode(int32_t M, const int32_t* c, int64_t* x, int
     k_abft_encode<<<grid_rows(batch, n, T), T, 0, s>>>(c, x, M, batch, n);
     return check_launch("ne_abft_encode");
 }
+
+// ---- digit planes of existing int64 words -------------------------------------
+
+namespace {
+
+__global__ void __launch_bounds__(256) k_split_digits(const int64_t* __restrict__ x, int8_t* __restrict__ planes,
+                                                      DigitPlan P, int64_t batch, int Pl, int64_t n, int32_t* status) {
+    bool ok = true;
+    const int64_t rows = batch * Pl;
+    for (int64_t row = blockIdx.y; row < rows; row += gridDim.y) {
+        const int64_t* xr = x + row * n;
+        int8_t* pr = planes + row * P.S * n;
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+            int64_t v = xr[i];
+#pragma unroll
+            for (int t = 0; t < 8; t++) {
+                if (t > P.top) break;
+                const int8_t d = (int8_t)(v & 0xff);
+                if (P.stored & (1u << t)) pr[(int64_t)P.slot[t] * n + i] = d;
+                else ok = ok && (d == 0);
+                v = (v - d) >> 8;
+            }
+            ok = ok && (v == 0);
+        }
+    }
+    if (!ok && status) atomicExch(status, (int32_t)NE_ERANGE);
+}
+
+}  // namespace
+
+extern "C" ne_status ne_split_digits(ne_digits dg, const int64_t* x, int8_t* planes, int64_t batch, int32_t Pl,
+                                     int64_t n, int32_t* status, cudaStream_t s) {
+    ne_status st = validate_digits(dg);
+    if (st) return st;
+    if (batch < 0 || n < 0 || Pl < 1) return fail(NE_EINVAL, "ne_split_digits: bad sizes");
+    if (batch == 0 || n == 0) return NE_OK;
+    if (!x || !planes) return fail(NE_EINVAL, "ne_split_digits: null pointer");
+    DigitPlan P;
+    P.S = dg.S;
+    P.stored = 0;
+    for (int t = 0; t < 8; t++) P.slot[t] = 0;
+    for (int s2 = 0; s2 < dg.S; s2++) {
+        P.stored |= 1u << (dg.shift[s2] / 8);
+        P.slot[dg.shift[s2] / 8] = s2;
+    }
+    P.top = dg.shift[dg.S - 1] / 8;
+    k_split_digits<<<grid_rows(batch * Pl, n, 256), 256, 0, s>>>(x, planes, P, batch, Pl, n, status);
+    return check_launch("ne_split_digits");
+}

@@ -1,0 +1,56 @@
+// Inline-PTX building blocks of the int8 tensor path on sm_103a.
+//
+// The 5th-generation tcgen05 MMA has no integer kind on sm_103a (ptxas
+// rejects .kind::i8 for this target), so exact int8 x int8 -> int32
+// products use the warp-level mma.sync.m16n8k32 s8 instruction with register
+// accumulators.  Operands are staged in shared memory with cp.async and read
+// with ldmatrix.
+//
+// Fragment layouts of mma.m16n8k32 (s8), lane = 4*g + t (g = lane>>2, t = lane&3):
+//   A (16x32, row-major): a0 = A[g][4t..4t+3],   a1 = A[g+8][4t..4t+3],
+//                         a2 = A[g][16+4t..],    a3 = A[g+8][16+4t..]
+//   B (32x8, column-major): b0 = B[4t..4t+3][g], b1 = B[16+4t..16+4t+3][g]
+//   C/D (16x8, s32): c0 = D[g][2t], c1 = D[g][2t+1], c2 = D[g+8][2t], c3 = D[g+8][2t+1]
+#pragma once
+
+#include <cstdint>
+
+namespace ne {
+
+__device__ __forceinline__ void mma_s8(int (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k32.row.col.s32.s8.s8.s32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+        : "+r"(d[0]), "+r"(d[1]), "+r"(d[2]), "+r"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], uint32_t saddr) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(saddr));
+}
+
+__device__ __forceinline__ uint32_t lds32(uint32_t saddr) {
+    uint32_t v;
+    asm volatile("ld.shared.b32 %0, [%1];\n" : "=r"(v) : "r"(saddr));
+    return v;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// 16-byte asynchronous global->shared copy; src_bytes = 0 writes zeros.
+__device__ __forceinline__ void cp_async16(uint32_t saddr, const void* gptr, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(saddr), "l"(gptr), "r"(src_bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+}  // namespace ne

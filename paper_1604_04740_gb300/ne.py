@@ -76,6 +76,8 @@ def _load():
         "ne_abft_encode": [i32, P, P, i64, i64, P],
         "ne_abft_check": [i32, P, i64, i64, P, P, P],
         "ne_abft_recover": [i32, P, i64, i64, i32, P],
+        "ne_split_digits": [ne_digits, P, P, i64, i32, i64, P, P],
+        "ne_probe_mma_peak": [i32, ctypes.POINTER(i64), P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -167,6 +169,28 @@ def ne_entangle_digits(p: ne_params, dg: ne_digits, c: torch.Tensor, planes: tor
     _call("ne_entangle_digits", p, dg, _ptr(c, torch.int32, "c"), _ptr(planes, torch.int8, "planes"), batch, n,
           _ptr(status, torch.int32, "status", True), _stream())
     return planes
+
+
+def ne_split_digits(dg: ne_digits, x: torch.Tensor, P: int, planes: torch.Tensor | None = None,
+                    status: torch.Tensor | None = None) -> torch.Tensor:
+    """x int64 [..., P, n] -> planes int8 [..., P, S, n]."""
+    batch, n = _bmn(x, P)
+    shape = tuple(x.shape[:-1]) + (dg.S, n)
+    if planes is None:
+        planes = torch.empty(shape, dtype=torch.int8, device=x.device)
+    if tuple(planes.shape) != shape:
+        raise ValueError(f"planes must be {shape}")
+    _call("ne_split_digits", dg, _ptr(x, torch.int64, "x"), _ptr(planes, torch.int8, "planes"), batch, P, n,
+          _ptr(status, torch.int32, "status", True), _stream())
+    return planes
+
+
+def ne_probe_mma_peak(iters: int) -> int:
+    """Launch the int8 tensor-path throughput probe on the current stream;
+    returns the number of int8 operations it issues (time it with events)."""
+    ops = ctypes.c_int64()
+    _call("ne_probe_mma_peak", iters, ctypes.byref(ops), _stream())
+    return ops.value
 
 
 # ---- operations ----------------------------------------------------------------
