@@ -137,6 +137,79 @@ __global__ void __launch_bounds__(256) k_entangle_digits(const int32_t* __restri
     if (!ok && status) atomicExch(status, (int32_t)NE_ERANGE);
 }
 
+// Walks the flat space of (group, chunk) pairs with a grid stride, keeping
+// the pair up to date by constant increments instead of a division per step.
+struct FlatWalk {
+    int64_t b, q, db, dq, nchunk;
+    __device__ FlatWalk(int64_t start, int64_t stride, int64_t nchunk_) : nchunk(nchunk_) {
+        b = start / nchunk;
+        q = start - b * nchunk;
+        db = stride / nchunk;
+        dq = stride - db * nchunk;
+    }
+    __device__ void next() {
+        q += dq;
+        b += db;
+        if (q >= nchunk) {
+            q -= nchunk;
+            b++;
+        }
+    }
+};
+
+// The common case (compile-time M, n a multiple of 8, aligned planes): every
+// thread owns 8 positions of one group, issues the 2 x 16-byte loads of all
+// M streams before any arithmetic, and writes one 8-byte word per stored
+// digit plane and stream.
+template <int MT>
+__global__ void __launch_bounds__(256, 3) k_entangle_digits8(const int32_t* __restrict__ c, int8_t* __restrict__ planes,
+                                                          int l, DigitPlan P, int64_t batch, int64_t n,
+                                                          int32_t* status) {
+    const int64_t nchunk = n / 8;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    bool ok = true;
+    for (FlatWalk w((int64_t)blockIdx.x * blockDim.x + threadIdx.x, stride, nchunk); w.b < batch; w.next()) {
+        const int32_t* cb = c + w.b * MT * n + w.q * 8;
+        int32_t v[MT][8];
+#pragma unroll
+        for (int m = 0; m < MT; m++) {
+            const int4* src = reinterpret_cast<const int4*>(cb + (int64_t)m * n);
+            const int4 a = __ldcs(src), bb = __ldcs(src + 1);
+            v[m][0] = a.x; v[m][1] = a.y; v[m][2] = a.z; v[m][3] = a.w;
+            v[m][4] = bb.x; v[m][5] = bb.y; v[m][6] = bb.z; v[m][7] = bb.w;
+        }
+        int8_t* pb = planes + w.b * MT * P.S * n + w.q * 8;
+#pragma unroll
+        for (int m = 0; m < MT; m++) {
+            const int pm = (m + MT - 1) % MT;
+            int64_t x[8];
+#pragma unroll
+            for (int e = 0; e < 8; e++) x[e] = entangle_word(v[m][e], v[pm][e], l);
+#pragma unroll
+            for (int t = 0; t < 8; t++) {
+                if (t > P.top) break;
+                uint32_t w0 = 0, w1 = 0;
+                bool nz = false;
+#pragma unroll
+                for (int e = 0; e < 8; e++) {
+                    const int8_t d = (int8_t)(x[e] & 0xff);
+                    nz |= (d != 0);
+                    if (e < 4) w0 |= (uint32_t)(uint8_t)d << (8 * e);
+                    else w1 |= (uint32_t)(uint8_t)d << (8 * (e - 4));
+                    x[e] = (x[e] - d) >> 8;
+                }
+                if (P.stored & (1u << t))
+                    __stcs(reinterpret_cast<uint2*>(pb + ((int64_t)m * P.S + P.slot[t]) * n), make_uint2(w0, w1));
+                else
+                    ok = ok && !nz;
+            }
+#pragma unroll
+            for (int e = 0; e < 8; e++) ok = ok && (x[e] == 0);
+        }
+    }
+    if (!ok && status) atomicExch(status, (int32_t)NE_ERANGE);
+}
+
 // ---- checksum encoder (Eq. 4) -------------------------------------------------
 
 __global__ void __launch_bounds__(256) k_abft_encode(const int32_t* __restrict__ c, int64_t* __restrict__ x,
@@ -205,7 +278,17 @@ extern "C" ne_status ne_entangle_digits(ne_params p, ne_digits dg, const int32_t
     }
     P.top = dg.shift[dg.S - 1] / 8;   // digits above the top planned one must be 0
     const int T = 256;
-    if (n % 8 == 0 && aligned(c, 16) && aligned(planes, 8)) {
+    if (n % 8 == 0 && aligned(c, 16) && aligned(planes, 8) && p.M >= 3 && p.M <= 5) {
+        const int64_t chunks = batch * (n / 8);
+        int64_t blocks = (chunks + T - 1) / T;
+        const int64_t cap = (int64_t)wave_blocks(T, 8);
+        if (blocks > cap) blocks = cap;
+        switch (p.M) {
+            case 3: k_entangle_digits8<3><<<(unsigned)blocks, T, 0, s>>>(c, planes, p.l, P, batch, n, status); break;
+            case 4: k_entangle_digits8<4><<<(unsigned)blocks, T, 0, s>>>(c, planes, p.l, P, batch, n, status); break;
+            default: k_entangle_digits8<5><<<(unsigned)blocks, T, 0, s>>>(c, planes, p.l, P, batch, n, status); break;
+        }
+    } else if (n % 8 == 0 && aligned(c, 16) && aligned(planes, 8)) {
         k_entangle_digits<8><<<grid_rows(batch, n / 8, T), T, 0, s>>>(c, planes, p.M, p.l, P, batch, n, status);
     } else {
         k_entangle_digits<1><<<grid_rows(batch, n, T), T, 0, s>>>(c, planes, p.M, p.l, P, batch, n, status);
