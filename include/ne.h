@@ -62,11 +62,17 @@ typedef struct {
  * the S planes sigma_0..sigma_{S-1} (int8) with
  *     x = sum_s sigma_s * 2^shift[s],   shift[s] a multiple of 8, ascending,
  * where the digits not listed are identically zero for the inputs the plan
- * was made for (see ne_plan_digits).  Plane layout: [batch][M][S][n]. */
+ * was made for (see ne_plan_digits).  Plane layout: [batch][M][S][n].
+ * l, lo, hi record the shift and the stream-value range [lo, hi] the plan
+ * was derived for (lo > hi: unknown); ne_entangle_digits uses them to check
+ * its inputs instead of every digit. */
 #define NE_MAX_DIGITS 8
 typedef struct {
     int32_t S;
     int32_t shift[NE_MAX_DIGITS];
+    int32_t l;
+    int32_t lo;
+    int32_t hi;
 } ne_digits;
 
 /* l-selection policies for ne_choose_l */

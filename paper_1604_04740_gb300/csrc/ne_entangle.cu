@@ -210,6 +210,99 @@ __global__ void __launch_bounds__(256, 3) k_entangle_digits8(const int32_t* __re
     if (!ok && status) atomicExch(status, (int32_t)NE_ERANGE);
 }
 
+// Digit planes when the plan knows the stream-value range [lo, hi] it was
+// derived for and its top digit is at most 3.  Every input is checked to lie
+// in [lo, hi]; then every entangled word fits 32 bits, so it is formed in
+// 32-bit arithmetic, and its balanced digits are the bytes of y = x + OFF
+// with OFF = 0x80 in every digit position (digit t = byte t of y minus 128,
+// i.e. the byte XOR 0x80 read as int8).  Digits the plan does not store must
+// be exactly 0x80 in y, and y must stay below 256^(top+1).  Eight positions
+// per thread: the digit bytes of four words are gathered with byte permutes.
+struct FastPlan {
+    uint32_t off;        // 0x80 in digits 0..top
+    uint32_t ns_mask;    // bytes of digits <= top that are not stored
+    uint32_t ns_want;    // 0x80 in those bytes
+    uint32_t lim;        // 256^(top+1), 0 when top = 3 (no limit in 32 bits)
+    int S;
+    int byte_of[NE_MAX_DIGITS];   // stored plane s -> digit index
+};
+
+template <int MT>
+__global__ void __launch_bounds__(256) k_entangle_digits_fast(const int32_t* __restrict__ c, int8_t* __restrict__ planes,
+                                                              int l, FastPlan F, int32_t lo, int32_t hi, int64_t batch,
+                                                              int64_t n, int32_t* status) {
+    const int64_t nchunk = n / 8;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const uint32_t span = (uint32_t)hi - (uint32_t)lo;
+    bool ok = true;
+    for (FlatWalk w((int64_t)blockIdx.x * blockDim.x + threadIdx.x, stride, nchunk); w.b < batch; w.next()) {
+        const int32_t* cb = c + w.b * MT * n + w.q * 8;
+        int32_t v[MT][8];
+#pragma unroll
+        for (int m = 0; m < MT; m++) {
+            const int4* src = reinterpret_cast<const int4*>(cb + (int64_t)m * n);
+            const int4 a = __ldcs(src), bb = __ldcs(src + 1);
+            v[m][0] = a.x; v[m][1] = a.y; v[m][2] = a.z; v[m][3] = a.w;
+            v[m][4] = bb.x; v[m][5] = bb.y; v[m][6] = bb.z; v[m][7] = bb.w;
+#pragma unroll
+            for (int e = 0; e < 8; e++) ok &= ((uint32_t)v[m][e] - (uint32_t)lo <= span);
+        }
+        int8_t* pb = planes + w.b * MT * F.S * n + w.q * 8;
+#pragma unroll
+        for (int m = 0; m < MT; m++) {
+            const int pm = (m + MT - 1) % MT;
+            uint32_t y[8];
+#pragma unroll
+            for (int e = 0; e < 8; e++) {
+                y[e] = (uint32_t)v[m][e] + ((uint32_t)v[pm][e] << l) + F.off;
+                ok &= ((y[e] & F.ns_mask) == F.ns_want) && (F.lim == 0 || y[e] < F.lim);
+            }
+#pragma unroll
+            for (int s = 0; s < 4; s++) {
+                if (s >= F.S) break;
+                const uint32_t t = (uint32_t)F.byte_of[s];
+                const uint32_t sel = t | ((t + 4) << 4);
+                const uint32_t w0 = __byte_perm(__byte_perm(y[0], y[1], sel), __byte_perm(y[2], y[3], sel), 0x5410);
+                const uint32_t w1 = __byte_perm(__byte_perm(y[4], y[5], sel), __byte_perm(y[6], y[7], sel), 0x5410);
+                __stcs(reinterpret_cast<uint2*>(pb + ((int64_t)m * F.S + s) * n),
+                       make_uint2(w0 ^ 0x80808080u, w1 ^ 0x80808080u));
+            }
+        }
+    }
+    if (!ok && status) atomicExch(status, (int32_t)NE_ERANGE);
+}
+
+// int64 words with the same flat traversal: four positions per thread, the
+// M 16-byte loads issued before the arithmetic.
+template <int MT>
+__global__ void __launch_bounds__(256) k_entangle_words4(const int32_t* __restrict__ c, int64_t* __restrict__ eps, int l,
+                                                         int64_t batch, int64_t n) {
+    const int64_t nchunk = n / 4;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (FlatWalk w((int64_t)blockIdx.x * blockDim.x + threadIdx.x, stride, nchunk); w.b < batch; w.next()) {
+        const int32_t* cb = c + w.b * MT * n + w.q * 4;
+        int4 v[MT];
+#pragma unroll
+        for (int m = 0; m < MT; m++) v[m] = __ldcs(reinterpret_cast<const int4*>(cb + (int64_t)m * n));
+        int64_t* eb = eps + w.b * MT * n + w.q * 4;
+#pragma unroll
+        for (int m = 0; m < MT; m++) {
+            const int4 cur = v[m], prev = v[(m + MT - 1) % MT];
+            longlong2* dst = reinterpret_cast<longlong2*>(eb + (int64_t)m * n);
+            __stcs(dst, make_longlong2(entangle_word(cur.x, prev.x, l), entangle_word(cur.y, prev.y, l)));
+            __stcs(dst + 1, make_longlong2(entangle_word(cur.z, prev.z, l), entangle_word(cur.w, prev.w, l)));
+        }
+    }
+}
+
+int flat_blocks(int64_t chunks, int threads) {
+    int64_t blocks = (chunks + threads - 1) / threads;
+    const int64_t cap = (int64_t)wave_blocks(threads, 8);
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    return (int)blocks;
+}
+
 // ---- checksum encoder (Eq. 4) -------------------------------------------------
 
 __global__ void __launch_bounds__(256) k_abft_encode(const int32_t* __restrict__ c, int64_t* __restrict__ x,
@@ -250,7 +343,14 @@ extern "C" ne_status ne_entangle(ne_params p, const int32_t* c, int64_t* eps, in
     if (batch == 0 || n == 0) return NE_OK;
     if (!c || !eps) return fail(NE_EINVAL, "ne_entangle: null pointer");
     const int T = 256;
-    if (n % 4 == 0 && aligned(c, 16) && aligned(eps, 16)) {
+    if (n % 4 == 0 && aligned(c, 16) && aligned(eps, 16) && p.M <= 5) {
+        const int blocks = flat_blocks(batch * (n / 4), T);
+        switch (p.M) {
+            case 3: k_entangle_words4<3><<<blocks, T, 0, s>>>(c, eps, p.l, batch, n); break;
+            case 4: k_entangle_words4<4><<<blocks, T, 0, s>>>(c, eps, p.l, batch, n); break;
+            default: k_entangle_words4<5><<<blocks, T, 0, s>>>(c, eps, p.l, batch, n); break;
+        }
+    } else if (n % 4 == 0 && aligned(c, 16) && aligned(eps, 16)) {
         k_entangle<4><<<grid_rows(batch, n / 4, T), T, 0, s>>>(c, eps, p.M, p.l, batch, n);
     } else {
         k_entangle<1><<<grid_rows(batch, n, T), T, 0, s>>>(c, eps, p.M, p.l, batch, n);
@@ -278,7 +378,29 @@ extern "C" ne_status ne_entangle_digits(ne_params p, ne_digits dg, const int32_t
     }
     P.top = dg.shift[dg.S - 1] / 8;   // digits above the top planned one must be 0
     const int T = 256;
-    if (n % 8 == 0 && aligned(c, 16) && aligned(planes, 8) && p.M >= 3 && p.M <= 5) {
+    const bool vec8 = n % 8 == 0 && aligned(c, 16) && aligned(planes, 8);
+    if (vec8 && p.M <= 5 && dg.lo <= dg.hi && dg.l == p.l && P.top <= 3) {
+        FastPlan F;
+        F.off = 0;
+        F.ns_mask = 0;
+        F.ns_want = 0;
+        for (int t = 0; t <= P.top; t++) {
+            F.off |= 0x80u << (8 * t);
+            if (!(P.stored & (1u << t))) {
+                F.ns_mask |= 0xffu << (8 * t);
+                F.ns_want |= 0x80u << (8 * t);
+            }
+        }
+        F.lim = P.top < 3 ? (1u << (8 * (P.top + 1))) : 0u;
+        F.S = dg.S;
+        for (int s2 = 0; s2 < NE_MAX_DIGITS; s2++) F.byte_of[s2] = s2 < dg.S ? dg.shift[s2] / 8 : 0;
+        const int blocks = flat_blocks(batch * (n / 8), T);
+        switch (p.M) {
+            case 3: k_entangle_digits_fast<3><<<blocks, T, 0, s>>>(c, planes, p.l, F, dg.lo, dg.hi, batch, n, status); break;
+            case 4: k_entangle_digits_fast<4><<<blocks, T, 0, s>>>(c, planes, p.l, F, dg.lo, dg.hi, batch, n, status); break;
+            default: k_entangle_digits_fast<5><<<blocks, T, 0, s>>>(c, planes, p.l, F, dg.lo, dg.hi, batch, n, status); break;
+        }
+    } else if (vec8 && p.M >= 3 && p.M <= 5) {
         const int64_t chunks = batch * (n / 8);
         int64_t blocks = (chunks + T - 1) / T;
         const int64_t cap = (int64_t)wave_blocks(T, 8);

@@ -138,6 +138,9 @@ extern "C" ne_status ne_plan_digits(int32_t l, int32_t cmin, int32_t cmax, ne_di
         }
     for (int s = S; s < NE_MAX_DIGITS; s++) dg->shift[s] = 0;
     dg->S = S;
+    dg->l = l;
+    dg->lo = cmin;
+    dg->hi = cmax;
     return NE_OK;
 }
 

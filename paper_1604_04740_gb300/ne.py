@@ -32,7 +32,8 @@ class ne_params(ctypes.Structure):
 
 
 class ne_digits(ctypes.Structure):
-    _fields_ = [("S", ctypes.c_int32), ("shift", ctypes.c_int32 * NE_MAX_DIGITS)]
+    _fields_ = [("S", ctypes.c_int32), ("shift", ctypes.c_int32 * NE_MAX_DIGITS),
+                ("l", ctypes.c_int32), ("lo", ctypes.c_int32), ("hi", ctypes.c_int32)]
 
     @property
     def shifts(self):
@@ -47,10 +48,12 @@ def params(M: int, l: int, w: int = 64) -> ne_params:
 
 
 def digits(shifts) -> ne_digits:
+    """A digit set without a known input range (every word is checked)."""
     d = ne_digits()
     d.S = len(shifts)
     for i, s in enumerate(shifts):
         d.shift[i] = s
+    d.l, d.lo, d.hi = 0, 1, 0
     return d
 
 

@@ -57,7 +57,8 @@ def test_choose_l_agrees_with_oracle(lib, M, w):
 
 
 class Digits(ctypes.Structure):
-    _fields_ = [("S", ctypes.c_int32), ("shift", ctypes.c_int32 * 8)]
+    _fields_ = [("S", ctypes.c_int32), ("shift", ctypes.c_int32 * 8), ("l", ctypes.c_int32),
+                ("lo", ctypes.c_int32), ("hi", ctypes.c_int32)]
 
 
 def _brute_digits(l, lo, hi):
@@ -81,6 +82,7 @@ def test_plan_digits_matches_brute_force(lib, l, lo, hi):
     d = Digits()
     assert lib.ne_plan_digits(l, lo, hi, ctypes.byref(d)) == 0
     assert [d.shift[i] for i in range(d.S)] == _brute_digits(l, lo, hi)
+    assert (d.l, d.lo, d.hi) == (l, lo, hi)
 
 
 def test_byte_aligned_l_gives_two_digits_for_int8_streams(lib):

@@ -86,6 +86,25 @@ def test_entangle_digits_recombine_to_words(ne, M, l, lo, hi, shape):
     assert (rec == eps).all()
 
 
+@pytest.mark.parametrize("M,l,lo,hi", [(3, 16, -128, 127), (4, 13, -128, 127), (5, 8, -100, 100), (3, 24, -128, 127)])
+def test_entangle_digits_range_checked_path_equals_generic_path(ne, M, l, lo, hi):
+    # a plan from ne_plan_digits carries its input range (checked per input,
+    # 32-bit word arithmetic); the same digit set without a range checks
+    # every word on the generic path.  Both must write the same planes.
+    c = inputs.int32_uniform(l, inputs.TAG_C, (8, M, 1024), lo, hi)
+    dg = ne.ne_plan_digits(l, lo, hi)
+    dg_generic = ne.digits(dg.shifts)
+    st1 = torch.zeros(1, dtype=torch.int32, device=DEV)
+    st2 = torch.zeros(1, dtype=torch.int32, device=DEV)
+    a = ne.ne_entangle_digits(ne.params(M, l), dg, dev(c), status=st1)
+    b = ne.ne_entangle_digits(ne.params(M, l), dg_generic, dev(c), status=st2)
+    assert (host(a) == host(b)).all() and int(st1.item()) == 0 and int(st2.item()) == 0
+    bad = c.copy()
+    bad[3, 1, 77] = hi + 1
+    ne.ne_entangle_digits(ne.params(M, l), dg, dev(bad), status=st1)
+    assert int(st1.item()) == ne.NE_ERANGE
+
+
 def test_entangle_digits_reports_out_of_plan_words(ne):
     M, l = 3, 16
     dg = ne.ne_plan_digits(l, -128, 127)            # digits 0 and 2 only
