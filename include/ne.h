@@ -232,6 +232,81 @@ ne_status ne_abft_recover(int32_t M, int64_t* d, int64_t batch, int64_t n, int32
                           cudaStream_t s);
 
 /* ------------------------------------------------------------------------ */
+/* Ragged batches: many independent jobs in one persistent launch            */
+/* ------------------------------------------------------------------------ */
+/*
+ * Sec. IV notes that long streams and large products are processed as many
+ * independent blocks; the entanglement of every block is independent.  A
+ * batch runs any mix of such jobs -- products and circular convolutions,
+ * with their own M, l and sizes -- through the same digit-plane tensor path:
+ * one launch entangles every job into digit planes, then ONE persistent
+ * launch walks a tile list covering all jobs (an atomic tile counter), each
+ * tile running the operation with the fused extract/check (or fused
+ * recovery) of its job.  Both launches read only device memory prepared by
+ * ne_batch_plan, so ne_batch_run can be captured in a CUDA graph and
+ * replayed.
+ */
+#define NE_JOB_GEMM  0
+#define NE_JOB_CCONV 1
+
+#define NE_ORDER_JOB 0   /* tiles in job order                         */
+#define NE_ORDER_LPT 1   /* costliest tiles first (longest-processing-time) */
+
+typedef struct {
+    int32_t kind;              /* NE_JOB_GEMM or NE_JOB_CCONV                                 */
+    int32_t M;                 /* streams, 3..5                                               */
+    int32_t l;                 /* shift; 0: chosen by the plan's l_policy from the job's bound */
+    int32_t rows, cols, k;     /* GEMM: (rows x k) streams times a (k x cols) operator;
+                                  k a multiple of 16, cols a multiple of 8                    */
+    int32_t N;                 /* CCONV: signal length, a multiple of 64 in [64, 65536]       */
+    int32_t r;                 /* checked stream (EXTRACT_CHECK) or lost stream (RECOVER)     */
+    int32_t fuse;              /* NE_FUSE_EXTRACT_CHECK or NE_FUSE_RECOVER                    */
+    int32_t cmin, cmax;        /* range of the stream values (bound and digit plan)           */
+    int64_t c_off;             /* int32 element offset of the job's streams [M][positions]    */
+    int64_t op_off;            /* byte offset of the job's operator: G [k][cols] or g [N]     */
+    int64_t out_off;           /* int64 element offset of the job's outputs [M][positions]    */
+    int64_t flag_off;          /* uint32 word offset of the job's check bitmap                */
+    int64_t fault_begin;       /* the job's range [begin, end) in the fault lists             */
+    int64_t fault_end;
+} ne_job;
+
+typedef struct {
+    int32_t ctas_per_sm;       /* resident blocks per SM of the persistent launch (1..4)      */
+    int32_t order;             /* NE_ORDER_JOB or NE_ORDER_LPT                                */
+    int32_t cconv_blocks;      /* outputs per convolution tile, in blocks of 64: 4, 8 or 16   */
+    int32_t l_policy;          /* NE_L_BYTE or NE_L_SMALLEST for jobs with l = 0              */
+} ne_batch_config;
+
+typedef struct {               /* what ne_batch_run needs to know on the host                 */
+    int32_t njobs, ntiles, nsegs, grid;
+    int64_t flag_words;        /* total check-bitmap words (for clearing)                     */
+    int64_t workspace_bytes;   /* device workspace the plan occupies                          */
+    int64_t mma_ops;           /* int8 operations the tiles issue (2 x multiply-adds)         */
+    int64_t useful_ops;        /* 2 x multiply-adds of the operations on the raw streams      */
+} ne_batch_info;
+
+/* Plan a batch: choose l and the digit plan of every job, lay out the digit
+ * planes, cut entangle segments and operation tiles, order the tiles, and
+ * write the tables to the device workspace (synchronous copy; workspace may
+ * be null to only size it: info->workspace_bytes).  jobs is a host array.
+ * Jobs are validated here (NE_EINVAL / NE_ERANGE with the job index in the
+ * message).  The fault lists are sorted by position within each job's
+ * range. */
+ne_status ne_batch_plan(const ne_job* jobs, int32_t njobs, ne_batch_config cfg, void* workspace,
+                        int64_t workspace_bytes, ne_batch_info* info, cudaStream_t s);
+
+/* Run a planned batch.  c: int32 stream arena, ops: int8 operator arena,
+ * out: int64 output arena (d_hat of every job), flags: check bitmaps (all
+ * info.flag_words are cleared first), nflag: total flagged positions
+ * (nullable), faults: optional transient-fault lists (positions within the
+ * job, stream, bit; all null when unused) applied to delta before the
+ * extraction, status: NE_ERANGE if an input lies outside its job's range
+ * (nullable, not reset).  No allocation, no host synchronisation. */
+ne_status ne_batch_run(ne_batch_info info, const int32_t* c, const int8_t* ops, int64_t* out, uint32_t* flags,
+                       uint64_t* nflag, const int64_t* fault_pos, const int32_t* fault_stream,
+                       const int32_t* fault_bit, void* workspace, int32_t* status, cudaStream_t s);
+
+/* ------------------------------------------------------------------------ */
 
 /* Measurement support (no counterpart in the paper): runs a register-resident
  * loop of mma.sync.m16n8k32 s8 instructions on every SM -- the throughput

@@ -1,0 +1,584 @@
+// Ragged batches of independent jobs (products and circular convolutions of
+// entangled streams, each with its own M, l and sizes) in one persistent
+// launch.  Sec. IV of the paper processes long streams and large products as
+// many independent blocks; every block is entangled, operated on (Eq. 10),
+// extracted and checked (Eq. 17-20, Eq. 24) on its own, so a batch is a
+// list of such blocks of different shapes.
+//
+//   ne_batch_plan (host): per job l (Eq. 13/14 from the job's bound) and the
+//     digit plan; digit-plane arena layout; entangle segments; operation
+//     tiles (ordered by cost when asked); tables copied to the workspace.
+//   ne_batch_run (device, graph-capturable): clear the tile counter and the
+//     flag bitmaps; one launch entangles every segment into digit planes;
+//     ONE persistent launch: each CTA takes the next tile from an atomic
+//     counter and runs a product tile (16 x 64 outputs, all M*S planes) or
+//     a convolution tile (up to 1024 outputs, all planes, ne_cconv_tile.cuh)
+//     with the fused extract/check or fused recovery of its job.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "ne_cconv_tile.cuh"
+#include "ne_entangle.cuh"
+#include "ne_extract.cuh"
+#include "ne_mma.cuh"
+
+namespace {
+
+using namespace ne;
+
+constexpr int THREADS = 256;
+constexpr int SEG = 8192;        // positions per entangle segment
+constexpr int MS_MAX = 10;       // M <= 5 streams x S <= 2 digits
+
+struct DevJob {
+    int32_t kind, M, l, S, MS, rows, cols, k, N, r, fuse, pad;
+    int32_t shift[NE_MAX_DIGITS];
+    FastPlan fp;
+    int64_t c_off, op_off, out_off, flag_off, plane_off, npos, nout, fault_begin, fault_end;
+};
+
+struct DevTile {
+    int32_t job, kind, a, b;     // product: row tile, column tile; convolution: output chunk, blocks
+};
+
+struct DevSeg {
+    int32_t job, pad;
+    int64_t start, count;        // positions of every stream of the job
+};
+
+struct Layout {
+    int64_t jobs, tiles, segs, planes, total;
+};
+
+int64_t align256(int64_t x) { return (x + 255) & ~(int64_t)255; }
+
+Layout layout(int64_t njobs, int64_t ntiles, int64_t nsegs, int64_t plane_bytes) {
+    Layout L;
+    L.jobs = 256;
+    L.tiles = align256(L.jobs + njobs * (int64_t)sizeof(DevJob));
+    L.segs = align256(L.tiles + ntiles * (int64_t)sizeof(DevTile));
+    L.planes = align256(L.segs + nsegs * (int64_t)sizeof(DevSeg));
+    L.total = align256(L.planes + plane_bytes);
+    return L;
+}
+
+// ---- the product tile: 16 x 64 outputs of every digit plane, 8 warps -------------------
+
+namespace bgemm {
+
+constexpr int BM = 16, BN = 64, BK = 64, STAGES = 3, RB = 80, SB = 68;
+constexpr int UPW = 3;            // (plane, column half) units per warp: 2 * MS_MAX / 8, rounded up
+
+__host__ __device__ constexpr int smem_bytes(int MS) {
+    return (STAGES * (MS * BM * RB + BN * RB)) > (MS * BM * SB * 4) ? (STAGES * (MS * BM * RB + BN * RB))
+                                                                    : (MS * BM * SB * 4);
+}
+
+__device__ __forceinline__ void transpose4x4(const uint32_t (&r)[4], uint32_t (&c)[4]) {
+    const uint32_t t0 = __byte_perm(r[0], r[1], 0x5140);
+    const uint32_t t1 = __byte_perm(r[0], r[1], 0x7362);
+    const uint32_t t2 = __byte_perm(r[2], r[3], 0x5140);
+    const uint32_t t3 = __byte_perm(r[2], r[3], 0x7362);
+    c[0] = __byte_perm(t0, t2, 0x5410);
+    c[1] = __byte_perm(t0, t2, 0x7632);
+    c[2] = __byte_perm(t1, t3, 0x5410);
+    c[3] = __byte_perm(t1, t3, 0x7632);
+}
+
+struct TileArgs {
+    const int8_t* planes;        // [M][S][rows][k]
+    const int8_t* G;             // [k][cols]
+    int64_t* out;                // [M][rows][cols]
+    uint32_t* flags;             // bitmap over i * cols + j (pre-zeroed) or null
+    unsigned long long* nflag;
+    const int64_t* fault_pos;    // sorted positions i * cols + j, or null
+    const int32_t* fault_stream;
+    const int32_t* fault_bit;
+    int64_t nfault;
+    int rows, cols, k, M, S, MS, l, r, fuse;
+    int shift[NE_MAX_DIGITS];
+};
+
+template <int MT>
+__device__ __forceinline__ void epilogue(const TileArgs& a, const int32_t* stash, int row0, int col0) {
+    const int M = MT ? MT : a.M;
+    const int S = a.S;
+    const int lane = threadIdx.x & 31;
+    const bool check = (a.fuse == NE_FUSE_EXTRACT_CHECK);
+    const bool need_r = (a.fuse != NE_FUSE_RECOVER);
+    const int64_t plane = (int64_t)a.rows * a.cols;
+    int64_t f0 = 0, f1 = 0;
+    if (a.nfault > 0) {
+        f0 = cconv::lower_bound(a.fault_pos, a.nfault, (int64_t)row0 * a.cols + col0);
+        f1 = cconv::lower_bound(a.fault_pos, a.nfault, (int64_t)(row0 + BM - 1) * a.cols + col0 + BN);
+    }
+    for (int base = threadIdx.x & ~31; base < BM * BN; base += THREADS) {
+        const int idx = base + lane;
+        const int i = idx / BN, j = idx % BN;
+        const int gi = row0 + i, gj = col0 + j;
+        if (gi >= a.rows || gj >= a.cols) continue;
+        const int32_t* sp = stash + i * SB + j;
+        const int64_t pos = (int64_t)gi * a.cols + gj;
+        int64_t rot[MT ? MT : 32], res[MT ? MT : 32];
+#pragma unroll
+        for (int jj = 0; jj < (MT ? MT : 32); jj++) {
+            if (!MT && jj >= M) break;
+            int m = a.r + jj;
+            if (m >= M) m -= M;
+            int64_t v = 0;
+            if (jj > 0 || need_r) {
+#pragma unroll
+                for (int s = 0; s < NE_MAX_DIGITS; s++)
+                    if (s < S) v += cconv::shl64(sp[(m * S + s) * BM * SB], a.shift[s]);
+                for (int64_t f = f0; f < f1; f++)
+                    if (a.fault_pos[f] == pos && a.fault_stream[f] == m) v ^= (int64_t)(1ull << a.fault_bit[f]);
+            }
+            rot[jj] = v;
+        }
+        const bool flag = extract_rot<MT>(rot, M, a.l, check, res);
+#pragma unroll
+        for (int jj = 0; jj < (MT ? MT : 32); jj++) {
+            if (!MT && jj >= M) break;
+            int m = a.r + jj;
+            if (m >= M) m -= M;
+            a.out[m * plane + pos] = res[jj];
+        }
+        if (flag) {
+            if (a.flags) atomicOr(&a.flags[pos >> 5], 1u << (pos & 31));
+            if (a.nflag) atomicAdd(a.nflag, 1ull);
+        }
+    }
+}
+
+template <int MT>
+__device__ __forceinline__ void tile(const TileArgs& a, uint8_t* smem, int row0, int col0) {
+    const int MS = a.MS;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int K = a.k, rows = a.rows, cols = a.cols;
+    const int KT = (K + BK - 1) / BK;
+    const bool recover = (a.fuse == NE_FUSE_RECOVER);
+
+    uint8_t* As = smem;                                    // [STAGES][MS][BM][RB]
+    uint8_t* Bs = smem + STAGES * MS * BM * RB;            // [STAGES][BN][RB] (G transposed)
+    const uint32_t As_s = smem_u32(As), Bs_s = smem_u32(Bs);
+
+    auto load_A = [&](int stage, int kt) {
+        const int k0 = kt * BK;
+        for (int e = tid; e < MS * BM * 4; e += THREADS) {
+            const int c16 = e & 3, r = (e >> 2) % BM, pl = (e >> 2) / BM;
+            const int gi = row0 + r, gk = k0 + 16 * c16;
+            const bool ok = gi < rows && gk < K && !(recover && pl / a.S == a.r);
+            const int8_t* src = a.planes + ((int64_t)pl * rows + (ok ? gi : 0)) * K + (ok ? gk : 0);
+            cp_async16(As_s + ((stage * MS + pl) * BM + r) * RB + 16 * c16, src, ok ? 16 : 0);
+        }
+    };
+    // G: one 4 x 4 byte block per thread and stage
+    const int nb = tid % (BN / 4), kb = tid / (BN / 4);
+    auto load_G = [&](int kt, uint32_t (&reg)[4]) {
+        const int gn = col0 + 4 * nb;
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const int gk = kt * BK + 4 * kb + q;
+            reg[q] = (gk < K && gn < cols) ? __ldg(reinterpret_cast<const uint32_t*>(a.G + (int64_t)gk * cols + gn)) : 0u;
+        }
+    };
+    auto store_G = [&](int stage, const uint32_t (&reg)[4]) {
+        uint32_t c[4];
+        transpose4x4(reg, c);
+#pragma unroll
+        for (int q = 0; q < 4; q++) *reinterpret_cast<uint32_t*>(Bs + (stage * BN + 4 * nb + q) * RB + 4 * kb) = c[q];
+    };
+
+    int acc[UPW][4][4];
+#pragma unroll
+    for (int i = 0; i < UPW; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) acc[i][j][0] = acc[i][j][1] = acc[i][j][2] = acc[i][j][3] = 0;
+
+    uint32_t greg[4];
+#pragma unroll
+    for (int st = 0; st < STAGES - 1; st++) {
+        if (st < KT) {
+            load_A(st, st);
+            load_G(st, greg);
+            store_G(st, greg);
+        }
+        cp_async_commit();
+    }
+    for (int kt = 0; kt < KT; kt++) {
+        cp_async_wait<STAGES - 2>();
+        __syncthreads();
+        const int pf = kt + STAGES - 1;
+        if (pf < KT) {
+            load_A(pf % STAGES, pf);
+            load_G(pf, greg);
+        }
+        cp_async_commit();
+        const int st = kt % STAGES;
+#pragma unroll
+        for (int ks = 0; ks < 2; ks++) {
+            const int t0 = 32 * ks;
+#pragma unroll
+            for (int i = 0; i < UPW; i++) {
+                const int u = warp + 8 * i;
+                if (u >= 2 * MS) break;
+                const int pl = u >> 1, nh = u & 1;
+                if (recover && pl / a.S == a.r) continue;
+                uint32_t af[4];
+                ldsm_x4(af, As_s + ((st * MS + pl) * BM + (lane & 15)) * RB + t0 + 16 * (lane >> 4));
+#pragma unroll
+                for (int nj = 0; nj < 4; nj += 2) {
+                    uint32_t bf[4];
+                    const int n = 32 * nh + 8 * (nj + (lane >> 4)) + (lane & 7);
+                    ldsm_x4(bf, Bs_s + (st * BN + n) * RB + t0 + 16 * ((lane >> 3) & 1));
+                    mma_s8(acc[i][nj], af, bf[0], bf[1]);
+                    mma_s8(acc[i][nj + 1], af, bf[2], bf[3]);
+                }
+            }
+        }
+        if (pf < KT) store_G(pf % STAGES, greg);
+    }
+    cp_async_wait<0>();
+    __syncthreads();
+
+    int32_t* stash = reinterpret_cast<int32_t*>(smem);    // [MS][BM][SB]
+    const int gq = lane >> 2, tq = lane & 3;
+#pragma unroll
+    for (int i = 0; i < UPW; i++) {
+        const int u = warp + 8 * i;
+        if (u >= 2 * MS) break;
+        const int pl = u >> 1, nh = u & 1;
+#pragma unroll
+        for (int nj = 0; nj < 4; nj++)
+#pragma unroll
+            for (int h = 0; h < 4; h++)
+                stash[(pl * BM + gq + 8 * (h >> 1)) * SB + 32 * nh + 8 * nj + 2 * tq + (h & 1)] = acc[i][nj][h];
+    }
+    __syncthreads();
+    epilogue<MT>(a, stash, row0, col0);
+}
+
+}  // namespace bgemm
+
+// ---- kernels -------------------------------------------------------------------------------
+
+struct BatchK {
+    const DevJob* jobs;
+    const DevTile* tiles;
+    const DevSeg* segs;
+    int32_t* counter;
+    int8_t* planes;
+    int ntiles, nsegs;
+    const int32_t* c;
+    const int8_t* ops;
+    int64_t* out;
+    uint32_t* flags;
+    unsigned long long* nflag;
+    const int64_t* fault_pos;
+    const int32_t* fault_stream;
+    const int32_t* fault_bit;
+    int32_t* status;
+};
+
+template <int MT>
+__device__ __forceinline__ bool entangle_segment(const BatchK& k, const DevJob* J, const DevSeg& sg) {
+    const int64_t n = J->npos;
+    const int32_t* cb = k.c + J->c_off;
+    int8_t* pb = k.planes + J->plane_off;
+    const FastPlan F = J->fp;
+    const int l = J->l;
+    bool ok = true;
+    const int64_t q1 = (sg.start + sg.count) / 8;
+    for (int64_t q = sg.start / 8 + threadIdx.x; q < q1; q += THREADS) ok &= entangle_chunk8<MT>(cb + q * 8, pb + q * 8, n, l, F);
+    return ok;
+}
+
+__global__ void __launch_bounds__(THREADS) k_batch_entangle(BatchK k) {
+    bool ok = true;
+    for (int si = blockIdx.x; si < k.nsegs; si += gridDim.x) {
+        const DevSeg sg = k.segs[si];
+        const DevJob* J = k.jobs + sg.job;
+        switch (J->M) {
+            case 3: ok &= entangle_segment<3>(k, J, sg); break;
+            case 4: ok &= entangle_segment<4>(k, J, sg); break;
+            default: ok &= entangle_segment<5>(k, J, sg); break;
+        }
+    }
+    if (!ok && k.status) atomicExch(k.status, (int32_t)NE_ERANGE);
+}
+
+__device__ __forceinline__ void fill_common(const BatchK& k, const DevJob* J, int64_t*& fpos, const int32_t*& fstr,
+                                            const int32_t*& fbit, int64_t& nf) {
+    if (k.fault_pos && J->fault_end > J->fault_begin) {
+        fpos = const_cast<int64_t*>(k.fault_pos) + J->fault_begin;
+        fstr = k.fault_stream + J->fault_begin;
+        fbit = k.fault_bit + J->fault_begin;
+        nf = J->fault_end - J->fault_begin;
+    } else {
+        fpos = nullptr;
+        fstr = nullptr;
+        fbit = nullptr;
+        nf = 0;
+    }
+}
+
+__device__ __noinline__ void run_cconv(const BatchK& k, const DevJob* J, const DevTile& tl, uint8_t* smem) {
+    cconv::TileArgs t;
+    t.planes = k.planes + J->plane_off;
+    t.g = k.ops + J->op_off;
+    t.out = k.out + J->out_off;
+    t.flags = (J->fuse == NE_FUSE_EXTRACT_CHECK && k.flags) ? k.flags + J->flag_off : nullptr;
+    t.nflag = (J->fuse == NE_FUSE_EXTRACT_CHECK) ? k.nflag : nullptr;
+    int64_t* fp;
+    fill_common(k, J, fp, t.fault_stream, t.fault_bit, t.nfault);
+    t.fault_pos = fp;
+    t.N = J->N;
+    t.M = J->M;
+    t.S = J->S;
+    t.MS = J->MS;
+    t.l = J->l;
+    t.r = J->r;
+    t.fuse = J->fuse;
+    t.flags_atomic = 1;
+#pragma unroll
+    for (int i = 0; i < NE_MAX_DIGITS; i++) t.shift[i] = J->shift[i];
+    const int NB = J->N / cconv::T;
+    const int p0 = tl.a * tl.b;
+    const int npb = min(tl.b, NB - p0);
+    switch (J->M) {
+        case 3: cconv::tile<10, 3>(t, smem, p0, npb); break;
+        case 4: cconv::tile<10, 4>(t, smem, p0, npb); break;
+        default: cconv::tile<10, 5>(t, smem, p0, npb); break;
+    }
+}
+
+__device__ __noinline__ void run_gemm(const BatchK& k, const DevJob* J, const DevTile& tl, uint8_t* smem) {
+    bgemm::TileArgs t;
+    t.planes = k.planes + J->plane_off;
+    t.G = k.ops + J->op_off;
+    t.out = k.out + J->out_off;
+    t.flags = (J->fuse == NE_FUSE_EXTRACT_CHECK && k.flags) ? k.flags + J->flag_off : nullptr;
+    t.nflag = (J->fuse == NE_FUSE_EXTRACT_CHECK) ? k.nflag : nullptr;
+    int64_t* fp;
+    fill_common(k, J, fp, t.fault_stream, t.fault_bit, t.nfault);
+    t.fault_pos = fp;
+    t.rows = J->rows;
+    t.cols = J->cols;
+    t.k = J->k;
+    t.M = J->M;
+    t.S = J->S;
+    t.MS = J->MS;
+    t.l = J->l;
+    t.r = J->r;
+    t.fuse = J->fuse;
+#pragma unroll
+    for (int i = 0; i < NE_MAX_DIGITS; i++) t.shift[i] = J->shift[i];
+    switch (J->M) {
+        case 3: bgemm::tile<3>(t, smem, tl.a * bgemm::BM, tl.b * bgemm::BN); break;
+        case 4: bgemm::tile<4>(t, smem, tl.a * bgemm::BM, tl.b * bgemm::BN); break;
+        default: bgemm::tile<5>(t, smem, tl.a * bgemm::BM, tl.b * bgemm::BN); break;
+    }
+}
+
+__global__ void __launch_bounds__(THREADS, 2) k_batch_op(BatchK k) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    __shared__ int s_tile;
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(k.counter, 1);
+        __syncthreads();
+        const int t = s_tile;
+        __syncthreads();
+        if (t >= k.ntiles) break;
+        const DevTile tl = k.tiles[t];
+        const DevJob* J = k.jobs + tl.job;
+        if (tl.kind == NE_JOB_CCONV) run_cconv(k, J, tl, smem);
+        else run_gemm(k, J, tl, smem);
+        __syncthreads();
+    }
+}
+
+constexpr int op_smem_bytes() {
+    return cconv::smem_bytes(MS_MAX) > bgemm::smem_bytes(MS_MAX) ? cconv::smem_bytes(MS_MAX) : bgemm::smem_bytes(MS_MAX);
+}
+
+}  // namespace
+
+extern "C" ne_status ne_batch_plan(const ne_job* jobs, int32_t njobs, ne_batch_config cfg, void* workspace,
+                                   int64_t workspace_bytes, ne_batch_info* info, cudaStream_t s) {
+    if (!info || (njobs > 0 && !jobs) || njobs < 0) return fail(NE_EINVAL, "ne_batch_plan: bad arguments");
+    if (cfg.ctas_per_sm < 1 || cfg.ctas_per_sm > 4) return fail(NE_EINVAL, "ne_batch_plan: ctas_per_sm=%d", cfg.ctas_per_sm);
+    if (cfg.order != NE_ORDER_JOB && cfg.order != NE_ORDER_LPT) return fail(NE_EINVAL, "ne_batch_plan: order=%d", cfg.order);
+    if (cfg.cconv_blocks != 4 && cfg.cconv_blocks != 8 && cfg.cconv_blocks != 16)
+        return fail(NE_EINVAL, "ne_batch_plan: cconv_blocks=%d", cfg.cconv_blocks);
+    if (cfg.l_policy != NE_L_BYTE && cfg.l_policy != NE_L_SMALLEST)
+        return fail(NE_EINVAL, "ne_batch_plan: l_policy=%d", cfg.l_policy);
+    std::vector<DevJob> dj((size_t)njobs);
+    std::vector<DevTile> tiles;
+    std::vector<DevSeg> segs;
+    std::vector<int64_t> cost;
+    int64_t plane_bytes = 0, flag_words = 0, mma_ops = 0, useful = 0;
+    for (int32_t i = 0; i < njobs; i++) {
+        const ne_job& j = jobs[i];
+        DevJob& d = dj[(size_t)i];
+        std::memset(&d, 0, sizeof(d));
+        if (j.kind != NE_JOB_GEMM && j.kind != NE_JOB_CCONV) return fail(NE_EINVAL, "job %d: kind %d", i, j.kind);
+        if (j.M < 3 || j.M > 5) return fail(NE_EINVAL, "job %d: M=%d (batches take 3..5 streams)", i, j.M);
+        if (j.fuse != NE_FUSE_EXTRACT_CHECK && j.fuse != NE_FUSE_RECOVER) return fail(NE_EINVAL, "job %d: fuse", i);
+        if (j.r < 0 || j.r >= j.M) return fail(NE_EINVAL, "job %d: r=%d", i, j.r);
+        if (j.cmin > j.cmax) return fail(NE_EINVAL, "job %d: empty value range", i);
+        if (j.c_off < 0 || j.c_off % 4 || j.op_off < 0 || j.out_off < 0 || j.flag_off < 0)
+            return fail(NE_EINVAL, "job %d: offsets (c_off must be a multiple of 4)", i);
+        if (j.fault_begin < 0 || j.fault_end < j.fault_begin) return fail(NE_EINVAL, "job %d: fault range", i);
+        int64_t K;
+        if (j.kind == NE_JOB_GEMM) {
+            if (j.rows < 1 || j.cols < 8 || j.cols % 8 || j.k < 16 || j.k % 16 || j.k > 131056)
+                return fail(NE_EINVAL, "job %d: GEMM %dx%dx%d (k multiple of 16, cols multiple of 8)", i, j.rows, j.cols, j.k);
+            if (j.op_off % 4) return fail(NE_EINVAL, "job %d: op_off must be a multiple of 4", i);
+            K = j.k;
+        } else {
+            if (j.N < 64 || j.N % 64 || j.N > 65536) return fail(NE_EINVAL, "job %d: N=%d", i, j.N);
+            K = j.N;
+        }
+        const int64_t amax = std::max((int64_t)std::abs((int64_t)j.cmin), (int64_t)std::abs((int64_t)j.cmax));
+        const int64_t bound = K * amax * 128;
+        int32_t l = j.l, kk = 0;
+        if (l == 0) {
+            ne_status st = ne_choose_l(j.M, 64, bound, cfg.l_policy, &l, &kk);
+            if (st) return fail(st, "job %d: no l covers the bound %lld", i, (long long)bound);
+        }
+        ne_params p{j.M, l, 64};
+        ne_status st = validate_params(p);
+        if (st) return fail(st, "job %d: l=%d", i, l);
+        ne_digits dg;
+        if ((st = ne_plan_digits(l, j.cmin, j.cmax, &dg))) return fail(st, "job %d: digit plan", i);
+        if (!make_fast_plan(dg, l, &d.fp)) return fail(NE_ERANGE, "job %d: words need digits above the fourth", i);
+        if (j.M * dg.S > MS_MAX) return fail(NE_EINVAL, "job %d: M*S=%d > %d", i, j.M * dg.S, MS_MAX);
+        d.kind = j.kind;
+        d.M = j.M;
+        d.l = l;
+        d.S = dg.S;
+        d.MS = j.M * dg.S;
+        d.rows = j.rows;
+        d.cols = j.cols;
+        d.k = j.k;
+        d.N = j.N;
+        d.r = j.r;
+        d.fuse = j.fuse;
+        for (int t = 0; t < NE_MAX_DIGITS; t++) d.shift[t] = t < dg.S ? dg.shift[t] : 0;
+        d.c_off = j.c_off;
+        d.op_off = j.op_off;
+        d.out_off = j.out_off;
+        d.flag_off = j.flag_off;
+        d.fault_begin = j.fault_begin;
+        d.fault_end = j.fault_end;
+        d.npos = j.kind == NE_JOB_GEMM ? (int64_t)j.rows * j.k : (int64_t)j.N;
+        d.nout = j.kind == NE_JOB_GEMM ? (int64_t)j.rows * j.cols : (int64_t)j.N;
+        d.plane_off = plane_bytes;
+        plane_bytes = align256(plane_bytes + (int64_t)d.MS * d.npos);
+        flag_words = std::max(flag_words, j.flag_off + (d.nout + 31) / 32);
+        for (int64_t s0 = 0; s0 < d.npos; s0 += SEG) segs.push_back(DevSeg{i, 0, s0, std::min<int64_t>(SEG, d.npos - s0)});
+        if (j.kind == NE_JOB_GEMM) {
+            const int rt = (j.rows + bgemm::BM - 1) / bgemm::BM, ct = (j.cols + bgemm::BN - 1) / bgemm::BN;
+            for (int a = 0; a < rt; a++)
+                for (int b = 0; b < ct; b++) {
+                    tiles.push_back(DevTile{i, NE_JOB_GEMM, a, b});
+                    cost.push_back((int64_t)d.MS * bgemm::BM * bgemm::BN * j.k);
+                }
+            mma_ops += 2LL * d.MS * rt * bgemm::BM * ct * bgemm::BN * j.k;
+            useful += 2LL * j.M * j.rows * j.cols * j.k;
+        } else {
+            const int NB = j.N / cconv::T;
+            const int npb = std::min(cfg.cconv_blocks, NB);
+            for (int a = 0; a * npb < NB; a++) {
+                tiles.push_back(DevTile{i, NE_JOB_CCONV, a, npb});
+                cost.push_back((int64_t)d.MS * std::min(npb, NB - a * npb) * cconv::T * j.N);
+            }
+            mma_ops += 2LL * d.MS * j.N * j.N;
+            useful += 2LL * j.M * j.N * j.N;
+        }
+    }
+    if (cfg.order == NE_ORDER_LPT) {
+        std::vector<size_t> idx(tiles.size());
+        for (size_t t = 0; t < idx.size(); t++) idx[t] = t;
+        std::stable_sort(idx.begin(), idx.end(), [&](size_t x, size_t y) { return cost[x] > cost[y]; });
+        std::vector<DevTile> sorted(tiles.size());
+        for (size_t t = 0; t < idx.size(); t++) sorted[t] = tiles[idx[t]];
+        tiles.swap(sorted);
+    }
+    if (tiles.size() > 0x7fffffff || segs.size() > 0x7fffffff) return fail(NE_EINVAL, "ne_batch_plan: batch too large");
+    const Layout L = layout(njobs, (int64_t)tiles.size(), (int64_t)segs.size(), plane_bytes);
+    info->njobs = njobs;
+    info->ntiles = (int32_t)tiles.size();
+    info->nsegs = (int32_t)segs.size();
+    info->grid = sm_count() * cfg.ctas_per_sm;
+    info->flag_words = flag_words;
+    info->workspace_bytes = L.total;
+    info->mma_ops = mma_ops;
+    info->useful_ops = useful;
+    if (!workspace) return NE_OK;
+    if (workspace_bytes < L.total) return fail(NE_ENOMEM, "ne_batch_plan: workspace %lld < %lld bytes",
+                                               (long long)workspace_bytes, (long long)L.total);
+    if (!aligned(workspace, 256)) return fail(NE_EINVAL, "ne_batch_plan: workspace must be 256-byte aligned");
+    std::vector<uint8_t> host((size_t)L.planes, 0);
+    std::memcpy(host.data() + L.jobs, dj.data(), dj.size() * sizeof(DevJob));
+    if (!tiles.empty()) std::memcpy(host.data() + L.tiles, tiles.data(), tiles.size() * sizeof(DevTile));
+    if (!segs.empty()) std::memcpy(host.data() + L.segs, segs.data(), segs.size() * sizeof(DevSeg));
+    if (cudaMemcpyAsync(workspace, host.data(), host.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return check_launch("ne_batch_plan: copy tables");
+    return NE_OK;
+}
+
+extern "C" ne_status ne_batch_run(ne_batch_info info, const int32_t* c, const int8_t* ops, int64_t* out, uint32_t* flags,
+                                  uint64_t* nflag, const int64_t* fault_pos, const int32_t* fault_stream,
+                                  const int32_t* fault_bit, void* workspace, int32_t* status, cudaStream_t s) {
+    if (!workspace || info.njobs < 0 || info.ntiles < 0 || info.grid < 1) return fail(NE_EINVAL, "ne_batch_run: bad plan");
+    if (info.njobs == 0) return NE_OK;
+    if (!c || !ops || !out) return fail(NE_EINVAL, "ne_batch_run: null pointer");
+    if ((fault_pos || fault_stream || fault_bit) && !(fault_pos && fault_stream && fault_bit))
+        return fail(NE_EINVAL, "ne_batch_run: give all three fault lists or none");
+    if (!aligned(c, 16) || !aligned(ops, 4) || !aligned(out, 8)) return fail(NE_EINVAL, "ne_batch_run: alignment");
+    const Layout L = layout(info.njobs, info.ntiles, info.nsegs, 0);
+    uint8_t* ws = static_cast<uint8_t*>(workspace);
+    BatchK k;
+    k.jobs = reinterpret_cast<const DevJob*>(ws + L.jobs);
+    k.tiles = reinterpret_cast<const DevTile*>(ws + L.tiles);
+    k.segs = reinterpret_cast<const DevSeg*>(ws + L.segs);
+    k.counter = reinterpret_cast<int32_t*>(ws);
+    k.planes = reinterpret_cast<int8_t*>(ws + L.planes);
+    k.ntiles = info.ntiles;
+    k.nsegs = info.nsegs;
+    k.c = c;
+    k.ops = ops;
+    k.out = out;
+    k.flags = flags;
+    k.nflag = reinterpret_cast<unsigned long long*>(nflag);
+    k.fault_pos = fault_pos;
+    k.fault_stream = fault_stream;
+    k.fault_bit = fault_bit;
+    k.status = status;
+    if (cudaMemsetAsync(k.counter, 0, sizeof(int32_t), s) != cudaSuccess) return check_launch("ne_batch_run: counter");
+    if (flags && info.flag_words > 0 && cudaMemsetAsync(flags, 0, (size_t)info.flag_words * 4, s) != cudaSuccess)
+        return check_launch("ne_batch_run: flags");
+    if (nflag && cudaMemsetAsync(nflag, 0, sizeof(uint64_t), s) != cudaSuccess) return check_launch("ne_batch_run: count");
+    static bool attr_set[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+        if (cudaFuncSetAttribute(k_batch_op, cudaFuncAttributeMaxDynamicSharedMemorySize, op_smem_bytes()) != cudaSuccess)
+            return check_launch("ne_batch_run: shared-memory attribute");
+        attr_set[dev] = true;
+    }
+    if (info.nsegs > 0) {
+        int eg = std::min(info.nsegs, sm_count() * 8);
+        k_batch_entangle<<<eg, THREADS, 0, s>>>(k);
+        ne_status st = check_launch("ne_batch_run: entangle");
+        if (st) return st;
+    }
+    if (info.ntiles > 0) {
+        k_batch_op<<<info.grid, THREADS, op_smem_bytes(), s>>>(k);
+        return check_launch("ne_batch_run: operation");
+    }
+    return NE_OK;
+}

@@ -1,0 +1,253 @@
+// One output tile of the batched circular convolution on the int8 tensor
+// path, shared by the stand-alone kernel (ne_cconv_digits) and the ragged
+// batch kernel (ne_batch_run).
+//
+// Every entangled word is held as balanced base-256 digit planes sigma_s, so
+//     delta_m[i] = sum_s 2^shift_s  sum_j sigma_{m,s}[j] g[(i - j) mod N]
+// and each inner sum is an exact int8 x int8 -> int32 contraction (|sum| <=
+// N 2^14 < 2^31 for N <= 65536).
+//
+// Block-Toeplitz form.  With i = T p + q and j = T p' + t (T = 64),
+//     sum_j sigma[j] g[(i - j) mod N] = sum_u sum_t G_u[q][t] sigma[T (p - u) + t],
+//     G_u[q][t] = g[(T u + q - t) mod N],
+// so for each shift u the block G_u (T x T, Toeplitz) multiplies a matrix
+// whose columns are the input blocks p - u of every digit plane.  A tile owns
+// up to NPB = 16 output blocks (1024 outputs) of one group and all planes:
+//   D[q][(p, plane)] += sum_t G_u[q][t] B_u[t][(p, plane)],
+// a dense T x (npb * planes) x T product per u, on mma.sync.m16n8k32.
+// G_u is read from four byte-shifted copies of a reversed window of g in
+// shared memory (every lane reads aligned words); the digit planes of the
+// input blocks a u-chunk needs sit in shared memory, block-major, 80-byte
+// rows, so the ldmatrix rows of any 8 consecutive columns hit distinct banks.
+// The epilogue recombines the digits in int64, optionally flips injected
+// fault bits into delta, then extracts/checks per position with the shared
+// device code of the stand-alone extraction kernel.
+#pragma once
+
+#include "ne_common.cuh"
+#include "ne_extract.cuh"
+#include "ne_mma.cuh"
+
+namespace ne {
+namespace cconv {
+
+constexpr int T = 64;                  // Toeplitz block
+constexpr int NPB = 16;                // output blocks per tile (at most)
+constexpr int UCH = 16;                // shifts u per chunk
+constexpr int ROWB = 80;               // bytes per (block, plane) row in shared memory
+constexpr int PADB = 16;               // margin of each g copy
+constexpr int GW = 1184;               // bytes per g copy (>= T (UCH+1) + 2 PADB, = 32 mod 128)
+constexpr int WBMAX = NPB + UCH - 1;   // input blocks a chunk can touch
+constexpr int THREADS = 256;           // 8 warps: 4 row tiles x 2 column halves
+constexpr int SP = 68;                 // stash row stride (int32) per output block
+
+__host__ __device__ constexpr int smem_bytes(int MS) {
+    return (WBMAX * MS * ROWB + 4 * GW) > (MS * NPB * SP * 4) ? (WBMAX * MS * ROWB + 4 * GW) : (MS * NPB * SP * 4);
+}
+
+// Everything a tile needs, already offset to its group.
+struct TileArgs {
+    const int8_t* planes;        // [M][S][N]
+    const int8_t* g;             // [N]
+    int64_t* out;                // [M][N]
+    uint32_t* flags;             // [N/32] or null
+    unsigned long long* nflag;   // or null
+    const int64_t* fault_pos;    // faults of this group, sorted by position (or null)
+    const int32_t* fault_stream;
+    const int32_t* fault_bit;
+    int64_t nfault;
+    int N, M, S, MS, l, r, fuse;
+    int flags_atomic;            // bitmap pre-zeroed: OR in the set bits instead of storing words
+    int shift[NE_MAX_DIGITS];
+};
+
+__device__ __forceinline__ int64_t shl64(int64_t x, int s) { return (int64_t)((uint64_t)x << s); }
+
+// first index f in [0, n) with pos[f] >= key (pos sorted ascending)
+__device__ __forceinline__ int64_t lower_bound(const int64_t* pos, int64_t n, int64_t key) {
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (pos[mid] < key) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+template <int MT>
+__device__ __forceinline__ void epilogue(const TileArgs& a, const int32_t* stash, int p0, int npb) {
+    const int M = MT ? MT : a.M;
+    const int S = a.S;
+    const int lane = threadIdx.x & 31;
+    const int npos = npb * T;
+    const int64_t i0 = (int64_t)p0 * T;
+    const bool check = (a.fuse == NE_FUSE_EXTRACT_CHECK);
+    const bool need_r = (a.fuse != NE_FUSE_RECOVER);
+    int64_t f0 = 0, f1 = 0;
+    if (a.nfault > 0) {
+        f0 = lower_bound(a.fault_pos, a.nfault, i0);
+        f1 = lower_bound(a.fault_pos, a.nfault, i0 + npos);
+    }
+    for (int base = threadIdx.x & ~31; base < npos; base += THREADS) {
+        const int i = base + lane;
+        const int pr = i / T, q = i % T;
+        const int32_t* sp = stash + pr * SP + q;
+        if (a.fuse == NE_FUSE_NONE) {
+            for (int m = 0; m < M; m++) {
+                int64_t v = 0;
+#pragma unroll
+                for (int s = 0; s < NE_MAX_DIGITS; s++)
+                    if (s < S) v += shl64(sp[(m * S + s) * NPB * SP], a.shift[s]);
+                for (int64_t f = f0; f < f1; f++)
+                    if (a.fault_pos[f] == i0 + i && a.fault_stream[f] == m) v ^= (int64_t)(1ull << a.fault_bit[f]);
+                a.out[(int64_t)m * a.N + i0 + i] = v;
+            }
+            continue;
+        }
+        int64_t rot[MT ? MT : 32], res[MT ? MT : 32];
+#pragma unroll
+        for (int j = 0; j < (MT ? MT : 32); j++) {
+            if (!MT && j >= M) break;
+            int m = a.r + j;
+            if (m >= M) m -= M;
+            int64_t v = 0;
+            if (j > 0 || need_r) {
+#pragma unroll
+                for (int s = 0; s < NE_MAX_DIGITS; s++)
+                    if (s < S) v += shl64(sp[(m * S + s) * NPB * SP], a.shift[s]);
+                for (int64_t f = f0; f < f1; f++)
+                    if (a.fault_pos[f] == i0 + i && a.fault_stream[f] == m) v ^= (int64_t)(1ull << a.fault_bit[f]);
+            }
+            rot[j] = v;
+        }
+        const bool flag = extract_rot<MT>(rot, M, a.l, check, res);
+#pragma unroll
+        for (int j = 0; j < (MT ? MT : 32); j++) {
+            if (!MT && j >= M) break;
+            int m = a.r + j;
+            if (m >= M) m -= M;
+            a.out[(int64_t)m * a.N + i0 + i] = res[j];
+        }
+        if (check) {
+            const uint32_t w = __ballot_sync(0xffffffffu, flag);
+            if (lane == 0 && w) {
+                if (a.flags) {
+                    if (a.flags_atomic) atomicOr(&a.flags[(i0 + base) / 32], w);
+                    else a.flags[(i0 + base) / 32] = w;
+                }
+                if (a.nflag) atomicAdd(a.nflag, (unsigned long long)__popc(w));
+            } else if (lane == 0 && a.flags && !a.flags_atomic) {
+                a.flags[(i0 + base) / 32] = 0u;
+            }
+        }
+    }
+}
+
+// The tile of output blocks [p0, p0 + npb) of one group; all 256 threads of
+// the block take part.  smem: smem_bytes(MS) bytes, 128-byte aligned.
+template <int NTW, int MT>
+__device__ __forceinline__ void tile(const TileArgs& a, uint8_t* smem, int p0, int npb) {
+    const int MS = a.MS;
+    const int N = a.N;
+    const int NB = N / T;
+    const int uch = min(UCH, NB);
+    const int WB = npb + uch - 1;
+    const int cols = npb * MS;
+    const int NT = (cols + 7) / 8;
+    const int NTH = (NT + 1) / 2;
+
+    uint8_t* sig = smem;                                  // [WB][MS][ROWB]
+    uint8_t* gcp = smem + WBMAX * MS * ROWB;              // 4 x GW
+    int32_t* stash = reinterpret_cast<int32_t*>(smem);    // after the main loop
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int mt = warp & 3, half = warp >> 2;
+    const int gq = lane >> 2, tq = lane & 3;
+    const int tile0 = half * NTH;
+    const int ntile = max(0, min(NT, tile0 + NTH) - tile0);
+    const int kh = (lane >> 3) & 1;
+    const int rho = (4 - (gq & 3)) & 3;                   // byte shift of this lane's G_u reads
+    const uint32_t gcp_s = smem_u32(gcp) + rho * GW + PADB - rho;
+    const uint32_t sig_s = smem_u32(sig);
+
+    int acc[NTW][4];
+#pragma unroll
+    for (int j = 0; j < NTW; j++) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0;
+
+    for (int u0 = 0; u0 < NB; u0 += uch) {
+        const int uc = min(uch, NB - u0);
+        // digit planes of input blocks (p0 - (u0 + uch - 1) + blk_rel) mod NB
+        const int nchunks = WB * MS * 4;
+        for (int e = tid; e < nchunks; e += THREADS) {
+            const int c16 = e & 3, row = e >> 2;
+            const int blk_rel = row / MS, ms = row - blk_rel * MS;
+            int ab = (p0 - (u0 + uch - 1) + blk_rel) % NB;
+            if (ab < 0) ab += NB;
+            const int8_t* src = a.planes + (int64_t)ms * N + (int64_t)ab * T + c16 * 16;
+            const bool lost = (a.fuse == NE_FUSE_RECOVER) && (ms / a.S == a.r);
+            cp_async16(sig_s + row * ROWB + c16 * 16, src, lost ? 0 : 16);
+        }
+        cp_async_commit();
+        // g copies: copy rr, byte z holds g[(T (u0 + uch) - (z + rr - PADB)) mod N]
+        const int top = T * (u0 + uch);
+        for (int e = tid; e < 4 * (GW / 4); e += THREADS) {
+            const int rr = e / (GW / 4), zw = e - rr * (GW / 4);
+            uint32_t w = 0;
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                int idx = (top - (4 * zw + k + rr - PADB)) % N;
+                if (idx < 0) idx += N;
+                w |= (uint32_t)(uint8_t)__ldg(a.g + idx) << (8 * k);
+            }
+            *reinterpret_cast<uint32_t*>(gcp + rr * GW + 4 * zw) = w;
+        }
+        cp_async_wait<0>();
+        __syncthreads();
+
+        for (int u = u0; u < u0 + uc; u++) {
+            const int ushift = u0 + uch - 1 - u;
+            const int Y0 = T * (u0 + uch - u) - 16 * mt - gq;
+#pragma unroll
+            for (int ks = 0; ks < 2; ks++) {
+                const int t0 = 32 * ks;
+                const uint32_t ya = gcp_s + Y0 + t0 + 4 * tq;
+                uint32_t af[4];
+                af[0] = lds32(ya);
+                af[1] = lds32(ya - 8);
+                af[2] = lds32(ya + 16);
+                af[3] = lds32(ya + 8);
+#pragma unroll
+                for (int jj = 0; jj < NTW; jj += 2) {
+                    if (jj >= ntile) break;
+                    int c = 8 * (tile0 + jj + (lane >> 4)) + (lane & 7);
+                    if (c >= cols) c = 0;    // padding column: any valid row, result dropped
+                    uint32_t bf[4];
+                    ldsm_x4(bf, sig_s + (c + MS * ushift) * ROWB + t0 + 16 * kh);
+                    mma_s8(acc[jj], af, bf[0], bf[1]);
+                    if (jj + 1 < ntile) mma_s8(acc[jj + 1], af, bf[2], bf[3]);
+                }
+            }
+        }
+        __syncthreads();
+    }
+
+    // int32 digit sums -> stash [plane][output block][q]
+#pragma unroll
+    for (int jj = 0; jj < NTW; jj++) {
+        if (jj >= ntile) break;
+#pragma unroll
+        for (int h = 0; h < 4; h++) {
+            const int c = 8 * (tile0 + jj) + 2 * tq + (h & 1);
+            const int q = 16 * mt + gq + 8 * (h >> 1);
+            if (c < cols) {
+                const int pr = c / MS, ms = c - pr * MS;
+                stash[(ms * NPB + pr) * SP + q] = acc[jj][h];
+            }
+        }
+    }
+    __syncthreads();
+    epilogue<MT>(a, stash, p0, npb);
+}
+
+}  // namespace cconv
+}  // namespace ne

@@ -7,19 +7,13 @@
 // walk the positions of a row in chunks of VEC, so no division is needed to
 // split a flat index into (group, position).
 #include "ne_common.cuh"
+#include "ne_entangle.cuh"
 
 namespace {
 
 using namespace ne;
 
 // ---- int64 words -------------------------------------------------------------
-
-// eps_m = c_m + 2^l c_{m-1} (mod M); the product is formed in unsigned
-// arithmetic so that it is the exact two's-complement value (|c| < 2^31 and
-// l <= 31 under Eq. 13 keep it far from 2^63).
-__device__ __forceinline__ int64_t entangle_word(int32_t cm, int32_t cprev, int l) {
-    return (int64_t)((uint64_t)(int64_t)cm + ((uint64_t)(int64_t)cprev << l));
-}
 
 template <int VEC>
 __global__ void __launch_bounds__(256) k_entangle(const int32_t* __restrict__ c, int64_t* __restrict__ eps,
@@ -210,65 +204,17 @@ __global__ void __launch_bounds__(256, 3) k_entangle_digits8(const int32_t* __re
     if (!ok && status) atomicExch(status, (int32_t)NE_ERANGE);
 }
 
-// Digit planes when the plan knows the stream-value range [lo, hi] it was
-// derived for and its top digit is at most 3.  Every input is checked to lie
-// in [lo, hi]; then every entangled word fits 32 bits, so it is formed in
-// 32-bit arithmetic, and its balanced digits are the bytes of y = x + OFF
-// with OFF = 0x80 in every digit position (digit t = byte t of y minus 128,
-// i.e. the byte XOR 0x80 read as int8).  Digits the plan does not store must
-// be exactly 0x80 in y, and y must stay below 256^(top+1).  Eight positions
-// per thread: the digit bytes of four words are gathered with byte permutes.
-struct FastPlan {
-    uint32_t off;        // 0x80 in digits 0..top
-    uint32_t ns_mask;    // bytes of digits <= top that are not stored
-    uint32_t ns_want;    // 0x80 in those bytes
-    uint32_t lim;        // 256^(top+1), 0 when top = 3 (no limit in 32 bits)
-    int S;
-    int byte_of[NE_MAX_DIGITS];   // stored plane s -> digit index
-};
-
+// Digit planes on the range-checked fast path (ne_entangle.cuh): eight
+// positions per thread over the flat (group, chunk) space.
 template <int MT>
 __global__ void __launch_bounds__(256) k_entangle_digits_fast(const int32_t* __restrict__ c, int8_t* __restrict__ planes,
-                                                              int l, FastPlan F, int32_t lo, int32_t hi, int64_t batch,
-                                                              int64_t n, int32_t* status) {
+                                                              int l, FastPlan F, int64_t batch, int64_t n,
+                                                              int32_t* status) {
     const int64_t nchunk = n / 8;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const uint32_t span = (uint32_t)hi - (uint32_t)lo;
     bool ok = true;
-    for (FlatWalk w((int64_t)blockIdx.x * blockDim.x + threadIdx.x, stride, nchunk); w.b < batch; w.next()) {
-        const int32_t* cb = c + w.b * MT * n + w.q * 8;
-        int32_t v[MT][8];
-#pragma unroll
-        for (int m = 0; m < MT; m++) {
-            const int4* src = reinterpret_cast<const int4*>(cb + (int64_t)m * n);
-            const int4 a = __ldcs(src), bb = __ldcs(src + 1);
-            v[m][0] = a.x; v[m][1] = a.y; v[m][2] = a.z; v[m][3] = a.w;
-            v[m][4] = bb.x; v[m][5] = bb.y; v[m][6] = bb.z; v[m][7] = bb.w;
-#pragma unroll
-            for (int e = 0; e < 8; e++) ok &= ((uint32_t)v[m][e] - (uint32_t)lo <= span);
-        }
-        int8_t* pb = planes + w.b * MT * F.S * n + w.q * 8;
-#pragma unroll
-        for (int m = 0; m < MT; m++) {
-            const int pm = (m + MT - 1) % MT;
-            uint32_t y[8];
-#pragma unroll
-            for (int e = 0; e < 8; e++) {
-                y[e] = (uint32_t)v[m][e] + ((uint32_t)v[pm][e] << l) + F.off;
-                ok &= ((y[e] & F.ns_mask) == F.ns_want) && (F.lim == 0 || y[e] < F.lim);
-            }
-#pragma unroll
-            for (int s = 0; s < 4; s++) {
-                if (s >= F.S) break;
-                const uint32_t t = (uint32_t)F.byte_of[s];
-                const uint32_t sel = t | ((t + 4) << 4);
-                const uint32_t w0 = __byte_perm(__byte_perm(y[0], y[1], sel), __byte_perm(y[2], y[3], sel), 0x5410);
-                const uint32_t w1 = __byte_perm(__byte_perm(y[4], y[5], sel), __byte_perm(y[6], y[7], sel), 0x5410);
-                __stcs(reinterpret_cast<uint2*>(pb + ((int64_t)m * F.S + s) * n),
-                       make_uint2(w0 ^ 0x80808080u, w1 ^ 0x80808080u));
-            }
-        }
-    }
+    for (FlatWalk w((int64_t)blockIdx.x * blockDim.x + threadIdx.x, stride, nchunk); w.b < batch; w.next())
+        ok &= entangle_chunk8<MT>(c + w.b * MT * n + w.q * 8, planes + w.b * MT * F.S * n + w.q * 8, n, l, F);
     if (!ok && status) atomicExch(status, (int32_t)NE_ERANGE);
 }
 
@@ -379,26 +325,13 @@ extern "C" ne_status ne_entangle_digits(ne_params p, ne_digits dg, const int32_t
     P.top = dg.shift[dg.S - 1] / 8;   // digits above the top planned one must be 0
     const int T = 256;
     const bool vec8 = n % 8 == 0 && aligned(c, 16) && aligned(planes, 8);
-    if (vec8 && p.M <= 5 && dg.lo <= dg.hi && dg.l == p.l && P.top <= 3) {
-        FastPlan F;
-        F.off = 0;
-        F.ns_mask = 0;
-        F.ns_want = 0;
-        for (int t = 0; t <= P.top; t++) {
-            F.off |= 0x80u << (8 * t);
-            if (!(P.stored & (1u << t))) {
-                F.ns_mask |= 0xffu << (8 * t);
-                F.ns_want |= 0x80u << (8 * t);
-            }
-        }
-        F.lim = P.top < 3 ? (1u << (8 * (P.top + 1))) : 0u;
-        F.S = dg.S;
-        for (int s2 = 0; s2 < NE_MAX_DIGITS; s2++) F.byte_of[s2] = s2 < dg.S ? dg.shift[s2] / 8 : 0;
+    FastPlan F;
+    if (vec8 && p.M <= 5 && make_fast_plan(dg, p.l, &F)) {
         const int blocks = flat_blocks(batch * (n / 8), T);
         switch (p.M) {
-            case 3: k_entangle_digits_fast<3><<<blocks, T, 0, s>>>(c, planes, p.l, F, dg.lo, dg.hi, batch, n, status); break;
-            case 4: k_entangle_digits_fast<4><<<blocks, T, 0, s>>>(c, planes, p.l, F, dg.lo, dg.hi, batch, n, status); break;
-            default: k_entangle_digits_fast<5><<<blocks, T, 0, s>>>(c, planes, p.l, F, dg.lo, dg.hi, batch, n, status); break;
+            case 3: k_entangle_digits_fast<3><<<blocks, T, 0, s>>>(c, planes, p.l, F, batch, n, status); break;
+            case 4: k_entangle_digits_fast<4><<<blocks, T, 0, s>>>(c, planes, p.l, F, batch, n, status); break;
+            default: k_entangle_digits_fast<5><<<blocks, T, 0, s>>>(c, planes, p.l, F, batch, n, status); break;
         }
     } else if (vec8 && p.M >= 3 && p.M <= 5) {
         const int64_t chunks = batch * (n / 8);

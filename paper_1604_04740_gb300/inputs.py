@@ -90,6 +90,34 @@ def log_uniform_int(seed: int, tag: int, start: int, count: int, lo: int, hi: in
     return np.clip(v, lo, hi)
 
 
+def _signed(v: int) -> int:
+    v &= 0xFFFFFFFFFFFFFFFF
+    return v - (1 << 64) if v >> 63 else v
+
+
+def int8_uniform_device(seed: int, tag: int, count: int, start: int, device, chunk: int = 1 << 25):
+    """The same values as int8_uniform(seed, tag, (count,), start), computed on
+    a CUDA device with torch int64 arithmetic (wrapping multiply, logical
+    shifts by masking).  Returns an int8 tensor."""
+    import torch
+    key = _signed(int(_key(seed, tag)))
+    g, m1, m2 = _signed(int(GAMMA)), _signed(int(_M1)), _signed(int(_M2))
+    out = torch.empty(count, dtype=torch.int8, device=device)
+
+    def lsr(x, s):
+        return (x >> s) & ((1 << (64 - s)) - 1)
+
+    for b in range(0, count, chunk):
+        e = min(count, b + chunk)
+        z = torch.arange(start + b + 1, start + e + 1, dtype=torch.int64, device=device)
+        z = z * g + key
+        z = (z ^ lsr(z, 30)) * m1
+        z = (z ^ lsr(z, 27)) * m2
+        z = z ^ lsr(z, 31)
+        out[b:e] = (z & 0xFF).to(torch.uint8).view(torch.int8)
+    return out
+
+
 # ---- workloads -------------------------------------------------------------
 
 def streams(seed: int, shape) -> np.ndarray:

@@ -43,6 +43,24 @@ class ne_digits(ctypes.Structure):
         return f"ne_digits(S={self.S}, shift={self.shifts})"
 
 
+NE_JOB_GEMM, NE_JOB_CCONV = 0, 1
+NE_ORDER_JOB, NE_ORDER_LPT = 0, 1
+
+
+class ne_job(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in ("kind", "M", "l", "rows", "cols", "k", "N", "r", "fuse", "cmin", "cmax")] + \
+               [(n, ctypes.c_int64) for n in ("c_off", "op_off", "out_off", "flag_off", "fault_begin", "fault_end")]
+
+
+class ne_batch_config(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in ("ctas_per_sm", "order", "cconv_blocks", "l_policy")]
+
+
+class ne_batch_info(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in ("njobs", "ntiles", "nsegs", "grid")] + \
+               [(n, ctypes.c_int64) for n in ("flag_words", "workspace_bytes", "mma_ops", "useful_ops")]
+
+
 def params(M: int, l: int, w: int = 64) -> ne_params:
     return ne_params(M, l, w)
 
@@ -81,6 +99,8 @@ def _load():
         "ne_abft_recover": [i32, P, i64, i64, i32, P],
         "ne_split_digits": [ne_digits, P, P, i64, i32, i64, P, P],
         "ne_probe_mma_peak": [i32, ctypes.POINTER(i64), P],
+        "ne_batch_plan": [ctypes.POINTER(ne_job), i32, ne_batch_config, P, i64, ctypes.POINTER(ne_batch_info), P],
+        "ne_batch_run": [ne_batch_info, P, P, P, P, P, P, P, P, P, P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -329,3 +349,29 @@ def ne_abft_recover(M: int, d: torch.Tensor, j: int) -> torch.Tensor:
     batch, n = _bmn(d, M + 1)
     _call("ne_abft_recover", M, _ptr(d, torch.int64, "d"), batch, n, j, _stream())
     return d
+
+
+# ---- ragged batches -------------------------------------------------------------------
+
+def ne_batch_plan(jobs, cfg: ne_batch_config, workspace: torch.Tensor | None = None) -> ne_batch_info:
+    """jobs: a ctypes array of ne_job (host).  With workspace None only sizes
+    the plan (info.workspace_bytes); otherwise writes the tables into it
+    (uint8 device tensor, 256-byte aligned)."""
+    info = ne_batch_info()
+    ws_ptr, ws_bytes = None, 0
+    if workspace is not None:
+        ws_ptr = _ptr(workspace, torch.uint8, "workspace")
+        ws_bytes = workspace.numel()
+    _call("ne_batch_plan", jobs, len(jobs), cfg, ws_ptr, ws_bytes, ctypes.byref(info), _stream())
+    return info
+
+
+def ne_batch_run(info: ne_batch_info, c: torch.Tensor, ops: torch.Tensor, out: torch.Tensor,
+                 flags: torch.Tensor | None, nflag: torch.Tensor | None, workspace: torch.Tensor,
+                 fault_pos: torch.Tensor | None = None, fault_stream: torch.Tensor | None = None,
+                 fault_bit: torch.Tensor | None = None, status: torch.Tensor | None = None):
+    _call("ne_batch_run", info, _ptr(c, torch.int32, "c"), _ptr(ops, torch.int8, "ops"),
+          _ptr(out, torch.int64, "out"), _ptr(flags, torch.int32, "flags", True),
+          _ptr(nflag, torch.int64, "nflag", True), _ptr(fault_pos, torch.int64, "fault_pos", True),
+          _ptr(fault_stream, torch.int32, "fault_stream", True), _ptr(fault_bit, torch.int32, "fault_bit", True),
+          _ptr(workspace, torch.uint8, "workspace"), _ptr(status, torch.int32, "status", True), _stream())
