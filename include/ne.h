@@ -306,6 +306,36 @@ ne_status ne_batch_run(ne_batch_info info, const int32_t* c, const int8_t* ops, 
                        uint64_t* nflag, const int64_t* fault_pos, const int32_t* fault_stream,
                        const int32_t* fault_bit, void* workspace, int32_t* status, cudaStream_t s);
 
+/* The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory themselves -- for example code that
+ * runs inside another framework's memory pool or under a fixed device-memory
+ * budget, or a hot loop where a cudaMalloc (which synchronises the device)
+ * is not acceptable -- and therefore cannot hand ne_batch_run a workspace.
+ *
+ * ne_batch_run_static plans the batch (as ne_batch_plan) and runs it (as
+ * ne_batch_run) with the scratch memory -- the plan's tables and every job's
+ * digit planes -- in one static device array of NE_STATIC_WORKSPACE_BYTES
+ * bytes that the library owns.  That array exists on every GPU the library
+ * is loaded on, from the first use until the process exits.  The caller
+ * still passes every input and output (device pointers, as for
+ * ne_batch_run; jobs and cfg are host data).  The call allocates no device
+ * memory.
+ *  - A batch whose scratch exceeds the array is rejected with NE_ENOMEM
+ *    before any device work.
+ *  - The first call on a device looks up the array's device address (one
+ *    runtime query with that device current); make that first call before
+ *    any stream capture.
+ *  - The planning copies the tables synchronously with respect to the host.
+ *  - All calls share the one array: calls whose work overlaps on the GPU
+ *    (other streams, other host threads) overwrite each other's scratch and
+ *    race.  The array keeps the last call's contents; everything a run needs
+ *    zeroed is cleared by the run itself. */
+#define NE_STATIC_WORKSPACE_BYTES (32LL << 20)
+ne_status ne_batch_run_static(const ne_job* jobs, int32_t njobs, ne_batch_config cfg, const int32_t* c,
+                              const int8_t* ops, int64_t* out, uint32_t* flags, uint64_t* nflag,
+                              const int64_t* fault_pos, const int32_t* fault_stream, const int32_t* fault_bit,
+                              int32_t* status, cudaStream_t s);
+
 /* ------------------------------------------------------------------------ */
 
 /* Measurement support (no counterpart in the paper): runs a register-resident

@@ -582,3 +582,45 @@ extern "C" ne_status ne_batch_run(ne_batch_info info, const int32_t* c, const in
     }
     return NE_OK;
 }
+
+// ---- the batch for callers that cannot allocate device memory ----------------------------------
+//
+// The scratch memory of a batch (plan tables and digit planes) lives in one
+// static device array owned by the library instead of a caller workspace.
+// Host code cannot use the array's name as a device address, so the first
+// call on each device looks the address up with that device current.
+
+namespace {
+
+__device__ __align__(256) uint8_t g_static_workspace[NE_STATIC_WORKSPACE_BYTES];
+void* g_static_workspace_ptr[64] = {nullptr};   // per device, filled on first use
+
+}  // namespace
+
+extern "C" ne_status ne_batch_run_static(const ne_job* jobs, int32_t njobs, ne_batch_config cfg, const int32_t* c,
+                                         const int8_t* ops, int64_t* out, uint32_t* flags, uint64_t* nflag,
+                                         const int64_t* fault_pos, const int32_t* fault_stream,
+                                         const int32_t* fault_bit, int32_t* status, cudaStream_t s) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
+        return fail(NE_ECUDA, "ne_batch_run_static: no usable current device");
+    if (!g_static_workspace_ptr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_static_workspace);
+        if (e != cudaSuccess || !p)
+            return fail(NE_ECUDA, "ne_batch_run_static: address of the static workspace: %s", cudaGetErrorString(e));
+        g_static_workspace_ptr[dev] = p;
+    }
+    ne_batch_info info;
+    ne_status st = ne_batch_plan(jobs, njobs, cfg, nullptr, 0, &info, s);
+    if (st) return st;
+    if (info.workspace_bytes > NE_STATIC_WORKSPACE_BYTES)
+        return fail(NE_ENOMEM,
+                    "ne_batch_run_static: the batch needs %lld bytes of scratch; the static workspace holds %lld "
+                    "(use ne_batch_plan/ne_batch_run with a workspace)",
+                    (long long)info.workspace_bytes, (long long)NE_STATIC_WORKSPACE_BYTES);
+    st = ne_batch_plan(jobs, njobs, cfg, g_static_workspace_ptr[dev], NE_STATIC_WORKSPACE_BYTES, &info, s);
+    if (st) return st;
+    return ne_batch_run(info, c, ops, out, flags, nflag, fault_pos, fault_stream, fault_bit,
+                        g_static_workspace_ptr[dev], status, s);
+}

@@ -101,6 +101,7 @@ def _load():
         "ne_probe_mma_peak": [i32, ctypes.POINTER(i64), P],
         "ne_batch_plan": [ctypes.POINTER(ne_job), i32, ne_batch_config, P, i64, ctypes.POINTER(ne_batch_info), P],
         "ne_batch_run": [ne_batch_info, P, P, P, P, P, P, P, P, P, P, P],
+        "ne_batch_run_static": [ctypes.POINTER(ne_job), i32, ne_batch_config, P, P, P, P, P, P, P, P, P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -375,3 +376,16 @@ def ne_batch_run(info: ne_batch_info, c: torch.Tensor, ops: torch.Tensor, out: t
           _ptr(nflag, torch.int64, "nflag", True), _ptr(fault_pos, torch.int64, "fault_pos", True),
           _ptr(fault_stream, torch.int32, "fault_stream", True), _ptr(fault_bit, torch.int32, "fault_bit", True),
           _ptr(workspace, torch.uint8, "workspace"), _ptr(status, torch.int32, "status", True), _stream())
+
+
+def ne_batch_run_static(jobs, cfg: ne_batch_config, c: torch.Tensor, ops: torch.Tensor, out: torch.Tensor,
+                        flags: torch.Tensor | None, nflag: torch.Tensor | None,
+                        fault_pos: torch.Tensor | None = None, fault_stream: torch.Tensor | None = None,
+                        fault_bit: torch.Tensor | None = None, status: torch.Tensor | None = None):
+    """Plan and run a batch with the library's static scratch array (no device
+    memory is allocated); see include/ne.h for the size limit and sharing."""
+    _call("ne_batch_run_static", jobs, len(jobs), cfg, _ptr(c, torch.int32, "c"), _ptr(ops, torch.int8, "ops"),
+          _ptr(out, torch.int64, "out"), _ptr(flags, torch.int32, "flags", True),
+          _ptr(nflag, torch.int64, "nflag", True), _ptr(fault_pos, torch.int64, "fault_pos", True),
+          _ptr(fault_stream, torch.int32, "fault_stream", True), _ptr(fault_bit, torch.int32, "fault_bit", True),
+          _ptr(status, torch.int32, "status", True), _stream())
