@@ -51,13 +51,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="cconv", choices=["cconv", "gemm", "gemm64", "batch"])
+    ap.add_argument("--workload", default="cconv", choices=["cconv", "gemm", "gemm64", "batch", "serve"])
     ap.add_argument("--jobs", type=int, default=2048, help="jobs of the ragged batch workload")
     ap.add_argument("--no-extras", action="store_true", help="skip overhead, ABFT and CPU-baseline legs")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target length of the CPU-baseline sample")
     a = ap.parse_args()
     if a.steps is None:
-        a.steps = {"cconv": 400, "gemm": 20, "gemm64": 2000, "batch": 10}[a.workload]
+        a.steps = {"cconv": 400, "gemm": 20, "gemm64": 2000, "batch": 10, "serve": 1}[a.workload]
     return a
 
 
@@ -725,13 +725,53 @@ def run_batch(args, rank, world, local_rank):
         print(json.dumps(line), flush=True)
 
 
+def run_serve(args, rank, world, local_rank):
+    """The serving loop: Poisson arrivals swept over rates, requests from the
+    ragged-batch distribution, 1 % of them with one lost stream, admission by
+    a 100 GB HBM budget, continuous batching on 4 lanes; p50/p99 latency and
+    throughput, entangled and plain."""
+    import torch
+    from paper_1604_04740_gb300 import batch as B
+    from paper_1604_04740_gb300 import serve as S
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    rates = [1000, 2000, 5000, 10000, 20000, 50000]
+    srv = S.Server(budget_bytes=100 * 10 ** 9, lanes=4, max_batch=256, device=dev, host_pool_elems=1 << 27)
+    # warm-up: the library, the allocator pool and both job kinds
+    srv.run(B.mixed_jobs(99, 32, conv=(256, 65536)), np.zeros(32))
+    out = {}
+    top = None
+    for rate in rates:
+        specs = B.mixed_jobs(rate, args.jobs, mnk=(32, 2048), conv=(256, 65536), recover_frac=0.01)
+        arr = S.poisson_arrivals(rate, len(specs), float(rate))
+        ent = S.summarize(srv.run(specs, arr, seed=rate))
+        pla = S.summarize(srv.run(S.plain_copy(specs), arr, seed=rate))
+        out[str(rate)] = {"entangled": ent, "plain": pla,
+                          "throughput_overhead_pct": 100 * (pla["jobs_per_s"] / ent["jobs_per_s"] - 1)}
+        top = ent
+    if rank == 0:
+        line = {"metric": METRIC, "value": top["useful_Gop_s"] * world, "unit": "Gop/s", "n_gpus": world,
+                "steps": len(rates), "warmup": 1, "ms_per_step": 1e3 / top["jobs_per_s"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "s8", "data": "synthetic",
+                "config": {"workload": f"serving: Poisson arrivals at {rates} jobs/s, {args.jobs} requests per rate "
+                                       "from the ragged-batch distribution, 1% lose one stream, 100 GB HBM budget, "
+                                       "continuous batching on 4 CUDA-stream lanes (max 256 requests per micro-batch)",
+                           "value_is": "useful Gop/s at the highest rate", "results": "device-resident"},
+                "serving": out, "roofline": None, "cpu_baseline": None,
+                "e2e": {"value": top["useful_Gop_s"] * world, "unit": "Gop/s",
+                        "note": "requests' inputs are copied from pinned host memory inside the loop"},
+                "clocks": None, "gpu_launches": None}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
-        if args.workload == "batch":
+        if args.workload in ("batch", "serve"):
             print(json.dumps({"impl": "reference", "unavailable": "the CPU oracle covers this workload only by "
                               "sampled jobs (bench.py --workload batch reports them in cpu_baseline)"}))
             return
@@ -744,6 +784,10 @@ def main():
         dist.init_process_group("nccl")
     if args.workload == "batch":
         run_batch(args, rank, world, local_rank)
+    elif args.workload == "serve":
+        if args.jobs == 2048:
+            args.jobs = 4000
+        run_serve(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
     if world > 1:

@@ -260,8 +260,12 @@ typedef struct {
                                   k a multiple of 16, cols a multiple of 8                    */
     int32_t N;                 /* CCONV: signal length, a multiple of 64 in [64, 65536]       */
     int32_t r;                 /* checked stream (EXTRACT_CHECK) or lost stream (RECOVER)     */
-    int32_t fuse;              /* NE_FUSE_EXTRACT_CHECK or NE_FUSE_RECOVER                    */
+    int32_t fuse;              /* NE_FUSE_EXTRACT_CHECK, NE_FUSE_RECOVER, or NE_FUSE_NONE
+                                  (outputs are the words delta_m; no check)                  */
     int32_t cmin, cmax;        /* range of the stream values (bound and digit plan)           */
+    int32_t plain;             /* 1: the plain operation on the M raw streams (no
+                                  entanglement, outputs d_m; requires NE_FUSE_NONE) -- the
+                                  unprotected path entanglement is compared with             */
     int64_t c_off;             /* int32 element offset of the job's streams [M][positions]    */
     int64_t op_off;            /* byte offset of the job's operator: G [k][cols] or g [N]     */
     int64_t out_off;           /* int64 element offset of the job's outputs [M][positions]    */
@@ -337,6 +341,14 @@ ne_status ne_batch_run_static(const ne_job* jobs, int32_t njobs, ne_batch_config
                               int32_t* status, cudaStream_t s);
 
 /* ------------------------------------------------------------------------ */
+
+/* Serving runtime support (no counterpart in the paper): copy `count`
+ * regions host -> device on stream s, region i being nbytes[i] bytes from
+ * src_base + src_off[i] (host; pinned for the copies to be asynchronous) to
+ * dst_base + dst_off[i] (device).  One cudaMemcpyAsync per region, issued in
+ * order; the three arrays are host arrays read during the call. */
+ne_status ne_copy_regions_h2d(void* dst_base, const void* src_base, const int64_t* dst_off, const int64_t* src_off,
+                              const int64_t* nbytes, int64_t count, cudaStream_t s);
 
 /* Measurement support (no counterpart in the paper): runs a register-resident
  * loop of mma.sync.m16n8k32 s8 instructions on every SM -- the throughput

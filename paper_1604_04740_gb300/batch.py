@@ -31,6 +31,7 @@ class JobSpec:
     fuse: int = ne.NE_FUSE_EXTRACT_CHECK
     r: int = 0
     l: int = 0                # 0: the plan chooses l from the job's bound
+    plain: int = 0            # 1: the plain operation on the raw streams (fuse must be NONE)
 
     @property
     def positions_in(self) -> int:
@@ -111,7 +112,7 @@ class Batch:
             jb = self.jobs[j]
             jb.kind, jb.M, jb.l = s.kind, s.M, s.l
             jb.rows, jb.cols, jb.k, jb.N = s.rows, s.cols, s.k, s.N
-            jb.r, jb.fuse, jb.cmin, jb.cmax = s.r, s.fuse, cmin, cmax
+            jb.r, jb.fuse, jb.cmin, jb.cmax, jb.plain = s.r, s.fuse, cmin, cmax, s.plain
             jb.c_off, jb.op_off, jb.out_off, jb.flag_off = c_off, op_off, out_off, flag_off
             c_off = _align(c_off + s.M * s.positions_in, 4)
             op_off = _align(op_off + s.op_bytes, 16)

@@ -136,7 +136,19 @@ __device__ __forceinline__ void epilogue(const TileArgs& a, const int32_t* stash
             }
             rot[jj] = v;
         }
-        const bool flag = extract_rot<MT>(rot, M, a.l, check, res);
+        bool flag = false;
+        if (a.fuse == NE_FUSE_NONE) {
+            // the operation's words themselves (entangled delta, or the plain d)
+#pragma unroll
+            for (int jj = 0; jj < (MT ? MT : 32); jj++) {
+                if (!MT && jj >= M) break;
+                int m = a.r + jj;
+                if (m >= M) m -= M;
+                a.out[m * plane + pos] = rot[jj];
+            }
+            continue;
+        }
+        flag = extract_rot<MT>(rot, M, a.l, check, res);
 #pragma unroll
         for (int jj = 0; jj < (MT ? MT : 32); jj++) {
             if (!MT && jj >= M) break;
@@ -398,6 +410,33 @@ __global__ void __launch_bounds__(THREADS, 2) k_batch_op(BatchK k) {
     }
 }
 
+// Balanced base-256 digits that occur among the values [lo, hi] themselves.
+ne_status plain_digits(int32_t lo, int32_t hi, ne_digits* dg) {
+    uint32_t used = 0;
+    if ((int64_t)hi - lo <= 65536) {
+        for (int64_t a = lo; a <= hi; a++) {
+            int64_t x = a;
+            for (int t = 0; t < 8 && x != 0; t++) {
+                const int8_t d = (int8_t)(x & 0xff);
+                if (d) used |= 1u << t;
+                x = (x - d) >> 8;
+            }
+        }
+    } else {
+        used = 0xf;   // any int32: four digits
+    }
+    if (!used) used = 1;
+    int S = 0;
+    for (int t = 0; t < 8; t++)
+        if (used & (1u << t)) dg->shift[S++] = 8 * t;
+    for (int s = S; s < NE_MAX_DIGITS; s++) dg->shift[s] = 0;
+    dg->S = S;
+    dg->l = 0;
+    dg->lo = lo;
+    dg->hi = hi;
+    return NE_OK;
+}
+
 constexpr int op_smem_bytes() {
     return cconv::smem_bytes(MS_MAX) > bgemm::smem_bytes(MS_MAX) ? cconv::smem_bytes(MS_MAX) : bgemm::smem_bytes(MS_MAX);
 }
@@ -424,7 +463,10 @@ extern "C" ne_status ne_batch_plan(const ne_job* jobs, int32_t njobs, ne_batch_c
         std::memset(&d, 0, sizeof(d));
         if (j.kind != NE_JOB_GEMM && j.kind != NE_JOB_CCONV) return fail(NE_EINVAL, "job %d: kind %d", i, j.kind);
         if (j.M < 3 || j.M > 5) return fail(NE_EINVAL, "job %d: M=%d (batches take 3..5 streams)", i, j.M);
-        if (j.fuse != NE_FUSE_EXTRACT_CHECK && j.fuse != NE_FUSE_RECOVER) return fail(NE_EINVAL, "job %d: fuse", i);
+        if (j.fuse != NE_FUSE_EXTRACT_CHECK && j.fuse != NE_FUSE_RECOVER && j.fuse != NE_FUSE_NONE)
+            return fail(NE_EINVAL, "job %d: fuse", i);
+        if (j.plain != 0 && (j.plain != 1 || j.fuse != NE_FUSE_NONE))
+            return fail(NE_EINVAL, "job %d: a plain job has no check or recovery (fuse must be NE_FUSE_NONE)", i);
         if (j.r < 0 || j.r >= j.M) return fail(NE_EINVAL, "job %d: r=%d", i, j.r);
         if (j.cmin > j.cmax) return fail(NE_EINVAL, "job %d: empty value range", i);
         if (j.c_off < 0 || j.c_off % 4 || j.op_off < 0 || j.out_off < 0 || j.flag_off < 0)
@@ -443,16 +485,24 @@ extern "C" ne_status ne_batch_plan(const ne_job* jobs, int32_t njobs, ne_batch_c
         const int64_t amax = std::max((int64_t)std::abs((int64_t)j.cmin), (int64_t)std::abs((int64_t)j.cmax));
         const int64_t bound = K * amax * 128;
         int32_t l = j.l, kk = 0;
-        if (l == 0) {
-            ne_status st = ne_choose_l(j.M, 64, bound, cfg.l_policy, &l, &kk);
-            if (st) return fail(st, "job %d: no l covers the bound %lld", i, (long long)bound);
-        }
-        ne_params p{j.M, l, 64};
-        ne_status st = validate_params(p);
-        if (st) return fail(st, "job %d: l=%d", i, l);
         ne_digits dg;
-        if ((st = ne_plan_digits(l, j.cmin, j.cmax, &dg))) return fail(st, "job %d: digit plan", i);
-        if (!make_fast_plan(dg, l, &d.fp)) return fail(NE_ERANGE, "job %d: words need digits above the fourth", i);
+        ne_status st;
+        if (j.plain) {
+            // the raw streams: digits of the values themselves (no predecessor term)
+            if ((st = plain_digits(j.cmin, j.cmax, &dg))) return fail(st, "job %d: digit plan", i);
+            l = 0;
+            if (!make_fast_plan(dg, 0, &d.fp)) return fail(NE_ERANGE, "job %d: values need digits above the fourth", i);
+            d.fp.pmask = 0;
+        } else {
+            if (l == 0) {
+                st = ne_choose_l(j.M, 64, bound, cfg.l_policy, &l, &kk);
+                if (st) return fail(st, "job %d: no l covers the bound %lld", i, (long long)bound);
+            }
+            ne_params p{j.M, l, 64};
+            if ((st = validate_params(p))) return fail(st, "job %d: l=%d", i, l);
+            if ((st = ne_plan_digits(l, j.cmin, j.cmax, &dg))) return fail(st, "job %d: digit plan", i);
+            if (!make_fast_plan(dg, l, &d.fp)) return fail(NE_ERANGE, "job %d: words need digits above the fourth", i);
+        }
         if (j.M * dg.S > MS_MAX) return fail(NE_EINVAL, "job %d: M*S=%d > %d", i, j.M * dg.S, MS_MAX);
         d.kind = j.kind;
         d.M = j.M;

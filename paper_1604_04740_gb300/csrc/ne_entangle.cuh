@@ -29,6 +29,7 @@ struct FastPlan {
     int S;
     int lo, hi;          // the stream-value range the plan covers
     int byte_of[4];      // stored plane s -> digit index
+    uint32_t pmask;      // all ones: entangle with the predecessor; 0: digits of the raw stream
 };
 
 // false when the plan has no input range, does not match l, or needs a
@@ -54,6 +55,7 @@ inline bool make_fast_plan(const ne_digits& dg, int l, FastPlan* F) {
     F->lo = dg.lo;
     F->hi = dg.hi;
     for (int s = 0; s < 4; s++) F->byte_of[s] = s < dg.S ? dg.shift[s] / 8 : 0;
+    F->pmask = 0xffffffffu;
     return true;
 }
 
@@ -82,7 +84,7 @@ __device__ __forceinline__ bool entangle_chunk8(const int32_t* __restrict__ cb, 
         uint32_t y[8];
 #pragma unroll
         for (int e = 0; e < 8; e++) {
-            y[e] = (uint32_t)v[m][e] + ((uint32_t)v[pm][e] << l) + F.off;
+            y[e] = (uint32_t)v[m][e] + (((uint32_t)v[pm][e] & F.pmask) << l) + F.off;
             ok &= ((y[e] & F.ns_mask) == F.ns_want) && (F.lim == 0 || y[e] < F.lim);
         }
 #pragma unroll

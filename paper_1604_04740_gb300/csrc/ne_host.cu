@@ -104,9 +104,36 @@ extern "C" ne_status ne_choose_l(int32_t M, int32_t w, int64_t out_bound, int32_
     return fail(NE_EINVAL, "ne_choose_l: unknown policy %d", policy);
 }
 
+static ne_status plan_digits_uncached(int32_t l, int32_t cmin, int32_t cmax, ne_digits* dg);
+
+namespace {
+// recent plans of this host thread (the enumeration below costs ~10^5 steps)
+struct PlanCacheEntry {
+    int32_t l, lo, hi;
+    ne_digits dg;
+    bool valid;
+};
+thread_local PlanCacheEntry g_plan_cache[16] = {};
+thread_local int g_plan_next = 0;
+}  // namespace
+
 extern "C" ne_status ne_plan_digits(int32_t l, int32_t cmin, int32_t cmax, ne_digits* dg) {
     if (!dg) return fail(NE_EINVAL, "ne_plan_digits: null output");
     if (l < 1 || l > 62 || cmin > cmax) return fail(NE_EINVAL, "ne_plan_digits: l=%d range [%d, %d]", l, cmin, cmax);
+    for (const PlanCacheEntry& e : g_plan_cache)
+        if (e.valid && e.l == l && e.lo == cmin && e.hi == cmax) {
+            *dg = e.dg;
+            return NE_OK;
+        }
+    ne_status st = plan_digits_uncached(l, cmin, cmax, dg);
+    if (st == NE_OK) {
+        g_plan_cache[g_plan_next] = PlanCacheEntry{l, cmin, cmax, *dg, true};
+        g_plan_next = (g_plan_next + 1) % 16;
+    }
+    return st;
+}
+
+static ne_status plan_digits_uncached(int32_t l, int32_t cmin, int32_t cmax, ne_digits* dg) {
     uint32_t used = 0;   // bit s set: digit s (weight 2^(8s)) can be non-zero
     int64_t span = (int64_t)cmax - cmin + 1;
     if (span <= 4096) {

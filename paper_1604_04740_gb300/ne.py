@@ -48,7 +48,8 @@ NE_ORDER_JOB, NE_ORDER_LPT = 0, 1
 
 
 class ne_job(ctypes.Structure):
-    _fields_ = [(n, ctypes.c_int32) for n in ("kind", "M", "l", "rows", "cols", "k", "N", "r", "fuse", "cmin", "cmax")] + \
+    _fields_ = [(n, ctypes.c_int32) for n in ("kind", "M", "l", "rows", "cols", "k", "N", "r", "fuse", "cmin", "cmax",
+                                              "plain")] + \
                [(n, ctypes.c_int64) for n in ("c_off", "op_off", "out_off", "flag_off", "fault_begin", "fault_end")]
 
 
@@ -102,6 +103,7 @@ def _load():
         "ne_batch_plan": [ctypes.POINTER(ne_job), i32, ne_batch_config, P, i64, ctypes.POINTER(ne_batch_info), P],
         "ne_batch_run": [ne_batch_info, P, P, P, P, P, P, P, P, P, P, P],
         "ne_batch_run_static": [ctypes.POINTER(ne_job), i32, ne_batch_config, P, P, P, P, P, P, P, P, P, P],
+        "ne_copy_regions_h2d": [P, P, P, P, P, i64, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -354,17 +356,51 @@ def ne_abft_recover(M: int, d: torch.Tensor, j: int) -> torch.Tensor:
 
 # ---- ragged batches -------------------------------------------------------------------
 
+JOB_DTYPE = None   # numpy structured dtype with the layout of ne_job (set below)
+
+
+def _job_array(jobs):
+    """(pointer, count) of a ctypes ne_job array or a numpy JOB_DTYPE array."""
+    if isinstance(jobs, ctypes.Array):
+        return jobs, len(jobs)
+    import numpy as np
+    a = np.ascontiguousarray(jobs)
+    if a.dtype != JOB_DTYPE:
+        raise TypeError("jobs must be ne_job structures or a JOB_DTYPE array")
+    return ctypes.cast(a.ctypes.data, ctypes.POINTER(ne_job)), len(a)
+
+
 def ne_batch_plan(jobs, cfg: ne_batch_config, workspace: torch.Tensor | None = None) -> ne_batch_info:
-    """jobs: a ctypes array of ne_job (host).  With workspace None only sizes
-    the plan (info.workspace_bytes); otherwise writes the tables into it
-    (uint8 device tensor, 256-byte aligned)."""
+    """jobs: a ctypes array of ne_job or a numpy JOB_DTYPE array (host).
+    With workspace None only sizes the plan (info.workspace_bytes); otherwise
+    writes the tables into it (uint8 device tensor, 256-byte aligned)."""
     info = ne_batch_info()
     ws_ptr, ws_bytes = None, 0
     if workspace is not None:
         ws_ptr = _ptr(workspace, torch.uint8, "workspace")
         ws_bytes = workspace.numel()
-    _call("ne_batch_plan", jobs, len(jobs), cfg, ws_ptr, ws_bytes, ctypes.byref(info), _stream())
+    ptr, n = _job_array(jobs)
+    _call("ne_batch_plan", ptr, n, cfg, ws_ptr, ws_bytes, ctypes.byref(info), _stream())
     return info
+
+
+def ne_copy_regions_h2d(dst: torch.Tensor, src: torch.Tensor, dst_off, src_off, nbytes):
+    """Byte regions of the pinned host tensor src into the device tensor dst
+    (offsets and sizes in bytes, int64 numpy arrays)."""
+    import numpy as np
+    if not dst.is_cuda or src.is_cuda or not src.is_pinned():
+        raise ValueError("dst must be a CUDA tensor and src a pinned host tensor")
+    d = np.ascontiguousarray(dst_off, np.int64)
+    s_ = np.ascontiguousarray(src_off, np.int64)
+    b = np.ascontiguousarray(nbytes, np.int64)
+    if not (len(d) == len(s_) == len(b)):
+        raise ValueError("region lists differ in length")
+    if len(b) and (int((d + b).max()) > dst.numel() * dst.element_size() or
+                   int((s_ + b).max()) > src.numel() * src.element_size()):
+        raise ValueError("a region lies outside its tensor")
+    _call("ne_copy_regions_h2d", ctypes.c_void_p(dst.data_ptr()), ctypes.c_void_p(src.data_ptr()),
+          ctypes.c_void_p(d.ctypes.data), ctypes.c_void_p(s_.ctypes.data), ctypes.c_void_p(b.ctypes.data),
+          len(b), _stream())
 
 
 def ne_batch_run(info: ne_batch_info, c: torch.Tensor, ops: torch.Tensor, out: torch.Tensor,
@@ -389,3 +425,14 @@ def ne_batch_run_static(jobs, cfg: ne_batch_config, c: torch.Tensor, ops: torch.
           _ptr(nflag, torch.int64, "nflag", True), _ptr(fault_pos, torch.int64, "fault_pos", True),
           _ptr(fault_stream, torch.int32, "fault_stream", True), _ptr(fault_bit, torch.int32, "fault_bit", True),
           _ptr(status, torch.int32, "status", True), _stream())
+
+
+def _make_job_dtype():
+    import numpy as np
+    fields = [(name, np.int32 if t is ctypes.c_int32 else np.int64) for name, t in ne_job._fields_]
+    dt = np.dtype(fields, align=True)
+    assert dt.itemsize == ctypes.sizeof(ne_job), "ne_job layout"
+    return dt
+
+
+JOB_DTYPE = _make_job_dtype()
