@@ -390,12 +390,38 @@ def run_ours(args, rank, world, local_rank):
         ops = ne.ne_probe_mma_peak(4096)
         e1.record(stream)
         torch.cuda.synchronize()
-        peak = ops / (e0.elapsed_time(e1) * 1e-3) / 1e12
+        peak_mma = ops / (e0.elapsed_time(e1) * 1e-3) / 1e12
+        ne.ne_probe_dp4a_peak(64)
+        e0.record(stream)
+        ops = ne.ne_probe_dp4a_peak(8192)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        peak_dp4a = ops / (e0.elapsed_time(e1) * 1e-3) / 1e12
         achieved = mma_ops_per_launch / (inner_avg * 1e-3) / 1e12
+        hybrid = wl.name == "cconv" and os.environ.get("NE_CCONV_HYBRID", "") != "0"
+        peak_mixed = {}
+        if hybrid:
+            # both int8 pipes in the convolution kernel's warp layout (8 tensor + 2 dp4a warps,
+            # 3 blocks per SM), swept over the share of the work given to dp4a; the ceiling
+            # is the best split (the kernel gives dp4a 4 of 16 output blocks, a quarter)
+            I = 2048
+            for num, den in ((0, 1), (1, 8), (1, 4), (3, 8), (1, 2)):
+                idp = (128 * I * num) // (den - num)
+                ne.ne_probe_mixed_peak(16, (128 * 16 * num) // (den - num), 8, 2, 3)
+                e0.record(stream)
+                ops = ne.ne_probe_mixed_peak(I, idp, 8, 2, 3)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                peak_mixed[f"{num}/{den}"] = ops / (e0.elapsed_time(e1) * 1e-3) / 1e12
+        peak = max(peak_mixed.values()) if hybrid else peak_mma
+        src = ("measured in this run: mma.sync.m16n8k32 s8 register-resident probe (ne_probe_mma_peak)"
+               + ("; the kernel splits each group between the two int8 pipes (12 of 16 blocks on the tensor "
+                  "pipe, 4 on dp4a), so the peak is the best of ne_probe_mixed_peak (both pipes in the "
+                  "kernel's warp layout) over the dp4a work shares in peak_mixed" if hybrid else "")
+               + "; MEASURED_PEAKS.json has no int8 figure and sm_103a has no tcgen05 integer MMA")
         roof = {"bound": "tensor", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "TOP/s",
-                "frac": achieved / peak, "traffic": traffic_for(dominant, dom_src),
-                "peak_source": "measured in this run: mma.sync.m16n8k32 s8 register-resident probe (ne_probe_mma_peak); "
-                               "MEASURED_PEAKS.json has no int8 figure and sm_103a has no tcgen05 integer MMA",
+                "frac": achieved / peak, "traffic": traffic_for(dominant, dom_src), "peak_source": src,
+                "peak_mma": peak_mma, "peak_dp4a": peak_dp4a, "peak_mixed": peak_mixed or None,
                 "algorithmic": f"{mma_ops_per_launch} int8 ops per launch (2 x M x S x units)",
                 "ms_per_launch": inner_avg}
     else:
@@ -532,6 +558,21 @@ def cconv_extras(torch, ne, wl, dev, flush, step, p, dg, planes, g, out, ms_step
 
     t_e, _ = timed_steps(torch, ent_only, K, W, flush)
     ent_bytes = wl.c.nbytes + planes.numel()
+    # (8) the stand-alone linear passes of the int64 family (Eq. 16, Eq. 17-20 with
+    # Eq. 24, Eq. 24 alone, Proposition 3), each against the HBM roofline
+    ne.ne_entangle(pl, c, eps)
+    ne.ne_cconv(eps, g, d64)
+    nw = G * M * N
+    passes = {
+        "entangle_i64": (lambda ev: ne.ne_entangle(pl, c, eps), nw * 4 + nw * 8),
+        "extract_check": (lambda ev: ne.ne_extract(pl, d64, o64, 0, fl, None), nw * 16 + fl.numel() * 4),
+        "check": (lambda ev: ne.ne_check(pl, d64, 0, fl, None), nw * 8 + fl.numel() * 4),
+        "recover": (lambda ev: ne.ne_recover(pl, d64, 1, o64), nw * 8 * (M - 1) // M + nw * 8),
+    }
+    pass_ms = {}
+    for name, (fn, _) in passes.items():
+        tp, _ = timed_steps(torch, fn, K, W, flush)
+        pass_ms[name] = tp / K
     torch.cuda.synchronize()
     ms = lambda t, k: t / k  # noqa: E731
     res["overhead_pct"] = {
@@ -548,6 +589,10 @@ def cconv_extras(torch, ne, wl, dev, flush, step, p, dg, planes, g, out, ms_step
     res["entangle_pass_hbm"] = {"bytes": ent_bytes, "GB/s": ent_bytes / (ms(t_e, K) * 1e-3) / 1e9,
                                 "peak_GB/s": hbm_peak, "frac": (ent_bytes / (ms(t_e, K) * 1e-3) / 1e9 / hbm_peak)
                                 if hbm_peak else None}
+    res["linear_passes_hbm"] = {
+        name: {"bytes": nbytes, "ms": pass_ms[name], "GB/s": nbytes / (pass_ms[name] * 1e-3) / 1e9,
+               "frac": nbytes / (pass_ms[name] * 1e-3) / 1e9 / hbm_peak if hbm_peak else None}
+        for name, (_, nbytes) in passes.items()}
     return res
 
 

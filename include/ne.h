@@ -357,6 +357,19 @@ ne_status ne_copy_regions_h2d(void* dst_base, const void* src_base, const int64_
  * The caller times the launch on stream s. */
 ne_status ne_probe_mma_peak(int32_t iters, int64_t* ops, cudaStream_t s);
 
+/* The same for dp4a on the CUDA cores (four int8 products added into an
+ * int32 per instruction), the second int8 pipe the convolution uses. */
+ne_status ne_probe_dp4a_peak(int32_t iters, int64_t* ops, cudaStream_t s);
+
+/* Both int8 pipes together: blocks_per_sm blocks per SM, each with mma_warps
+ * warps running iters_mma rounds of the tensor loop above and dp4a_warps warps
+ * running iters_dp4a rounds of the dp4a loop, so the split of work between the
+ * pipes can match that of a kernel using both.  *ops receives the total int8
+ * operations.  mma_warps + dp4a_warps in [1, 16]; blocks_per_sm in [1, 8]. */
+ne_status ne_probe_mixed_peak(int32_t iters_mma, int32_t iters_dp4a, int32_t mma_warps,
+                              int32_t dp4a_warps, int32_t blocks_per_sm, int64_t* ops,
+                              cudaStream_t s);
+
 /* Message of the last failed call on this host thread ("" if none). */
 const char* ne_last_error(void);
 

@@ -300,10 +300,16 @@ __device__ __forceinline__ bool entangle_segment(const BatchK& k, const DevJob* 
     int8_t* pb = k.planes + J->plane_off;
     const FastPlan F = J->fp;
     const int l = J->l;
-    bool ok = true;
+    uint32_t worst = 0;
     const int64_t q1 = (sg.start + sg.count) / 8;
-    for (int64_t q = sg.start / 8 + threadIdx.x; q < q1; q += THREADS) ok &= entangle_chunk8<MT>(cb + q * 8, pb + q * 8, n, l, F);
-    return ok;
+    if (F.pmask == 0) {   // a plain job: digits of the raw streams
+        for (int64_t q = sg.start / 8 + threadIdx.x; q < q1; q += THREADS)
+            worst = max(worst, entangle_chunk8<MT, true>(cb + q * 8, pb + q * 8, n, l, F));
+    } else {
+        for (int64_t q = sg.start / 8 + threadIdx.x; q < q1; q += THREADS)
+            worst = max(worst, entangle_chunk8<MT>(cb + q * 8, pb + q * 8, n, l, F));
+    }
+    return worst <= (uint32_t)F.hi - (uint32_t)F.lo;
 }
 
 __global__ void __launch_bounds__(THREADS) k_batch_entangle(BatchK k) {

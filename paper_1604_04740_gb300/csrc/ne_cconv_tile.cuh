@@ -75,7 +75,8 @@ __device__ __forceinline__ int64_t lower_bound(const int64_t* pos, int64_t n, in
 }
 
 template <int MT>
-__device__ __forceinline__ void epilogue(const TileArgs& a, const int32_t* stash, int p0, int npb) {
+__device__ __forceinline__ void epilogue(const TileArgs& a, const int32_t* stash, int p0, int npb,
+                                         int nthreads = THREADS) {
     const int M = MT ? MT : a.M;
     const int S = a.S;
     const int lane = threadIdx.x & 31;
@@ -88,7 +89,7 @@ __device__ __forceinline__ void epilogue(const TileArgs& a, const int32_t* stash
         f0 = lower_bound(a.fault_pos, a.nfault, i0);
         f1 = lower_bound(a.fault_pos, a.nfault, i0 + npos);
     }
-    for (int base = threadIdx.x & ~31; base < npos; base += THREADS) {
+    for (int base = threadIdx.x & ~31; base < npos; base += nthreads) {
         const int i = base + lane;
         const int pr = i / T, q = i % T;
         const int32_t* sp = stash + pr * SP + q;
@@ -247,6 +248,179 @@ __device__ __forceinline__ void tile(const TileArgs& a, uint8_t* smem, int p0, i
     }
     __syncthreads();
     epilogue<MT>(a, stash, p0, npb);
+}
+
+// ---- hybrid tile: the int8 tensor pipe and the CUDA-core dp4a pipe together -----------------
+//
+// On sm_103a the int8 tensor instruction and dp4a (four int8 products added
+// into an int32, on the integer ALUs) have about the same throughput and run
+// on separate pipes.  For groups of 9..16 blocks (N in (512, 1024]) the
+// hybrid tile gives the last HW * R / 2 output blocks to HW extra warps that
+// compute them with dp4a, while the 8 MMA warps compute the other blocks as
+// tile() does; both finish into the same stash and the same epilogue.  A
+// dp4a thread owns R outputs (stride 32 HW) for every digit plane: per 4
+// inputs it loads each plane's digit word once (a broadcast) and one word
+// of the reversed filter per output, from four byte-shifted copies so that
+// every read is aligned and the 32 lanes hit 32 distinct banks.
+__host__ __device__ constexpr int hybrid_threads(int HW) { return THREADS + 32 * HW; }
+constexpr int GDP = 2144;                     // bytes per filter copy: >= 2 * 1024 + 8, = 24 words mod 32
+
+// [digit-plane window + tensor-pipe filter window][dp4a filter copies][stash]:
+// the stash has its own space, so a warp may write its results as soon as it
+// is done, while other warps still read the windows.
+__host__ __device__ constexpr int hybrid_smem_bytes(int MS) {
+    return WBMAX * MS * ROWB + 4 * GW + 4 * GDP + MS * NPB * SP * 4;
+}
+
+template <int MT, int MSC, int HW, int R>
+__device__ __forceinline__ void tile_hybrid(const TileArgs& a, uint8_t* smem) {
+    constexpr int MS = MSC;
+    constexpr int NTHR = hybrid_threads(HW);
+    constexpr int DT = 32 * HW;           // dp4a threads
+    static_assert((DT * R) % T == 0, "dp4a outputs must be whole blocks");
+    const int N = a.N;
+    const int NB = N / T;                 // DT * R / T + 1 .. 16
+    const int uch = NB;                   // a single chunk of shifts
+    const int npb = NB - DT * R / T;      // output blocks on the tensor pipe
+    const int WB = npb + uch - 1;
+    const int cols = npb * MS;
+    const int NT = (cols + 7) / 8;
+    const int NTH = (NT + 1) / 2;
+
+    uint8_t* sig = smem;                                  // [WB][MS][ROWB]
+    uint8_t* gcp = smem + WBMAX * MS * ROWB;              // 4 x GW (tensor-pipe filter window)
+    uint8_t* gdp = gcp + 4 * GW;                          // 4 x GDP (dp4a filter copies)
+    int32_t* stash = reinterpret_cast<int32_t*>(gdp + 4 * GDP);   // [MS][NPB][SP], its own space
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t sig_s = smem_u32(sig);
+
+    // -- loads (every thread) --
+    for (int e = tid; e < WB * MS * 4; e += NTHR) {
+        const int c16 = e & 3, row = e >> 2;
+        const int blk_rel = row / MS, ms = row - blk_rel * MS;
+        int ab = (blk_rel - (uch - 1)) % NB;
+        if (ab < 0) ab += NB;
+        const bool lost = (a.fuse == NE_FUSE_RECOVER) && (ms / a.S == a.r);
+        cp_async16(sig_s + row * ROWB + c16 * 16, a.planes + (int64_t)ms * N + (int64_t)ab * T + c16 * 16, lost ? 0 : 16);
+    }
+    cp_async_commit();
+    const int top = T * uch;
+    for (int e = tid; e < 4 * (GW / 4); e += NTHR) {
+        const int rr = e / (GW / 4), zw = e - rr * (GW / 4);
+        uint32_t w = 0;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            int idx = (top - (4 * zw + k + rr - PADB)) % N;
+            if (idx < 0) idx += N;
+            w |= (uint32_t)(uint8_t)__ldg(a.g + idx) << (8 * k);
+        }
+        *reinterpret_cast<uint32_t*>(gcp + rr * GW + 4 * zw) = w;
+    }
+    // dp4a copies: copy rr, byte z holds g[(N + 4 - z - rr) mod N], i.e. the
+    // reversed filter at offset y = z + rr - N - 4
+    for (int e = tid; e < 4 * (GDP / 4); e += NTHR) {
+        const int rr = e / (GDP / 4), zw = e - rr * (GDP / 4);
+        uint32_t w = 0;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            int idx = (N + 4 - (4 * zw + k) - rr) % N;
+            if (idx < 0) idx += N;
+            w |= (uint32_t)(uint8_t)__ldg(a.g + idx) << (8 * k);
+        }
+        *reinterpret_cast<uint32_t*>(gdp + rr * GDP + 4 * zw) = w;
+    }
+    cp_async_wait<0>();
+    __syncthreads();
+
+    if (warp < THREADS / 32) {
+        // -- tensor pipe: output blocks [0, npb), as in tile() --
+        const int mt = warp & 3, half = warp >> 2;
+        const int gq = lane >> 2, tq = lane & 3;
+        const int tile0 = half * NTH;
+        const int ntile = max(0, min(NT, tile0 + NTH) - tile0);
+        const int kh = (lane >> 3) & 1;
+        const int rho = (4 - (gq & 3)) & 3;
+        const uint32_t gcp_s = smem_u32(gcp) + rho * GW + PADB - rho;
+        constexpr int NTW = (16 * MS / 8 + 1) / 2;
+        int acc[NTW][4];
+#pragma unroll
+        for (int j = 0; j < NTW; j++) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0;
+        for (int u = 0; u < uch; u++) {
+            const int ushift = uch - 1 - u;
+            const int Y0 = T * (uch - u) - 16 * mt - gq;
+#pragma unroll
+            for (int ks = 0; ks < 2; ks++) {
+                const int t0 = 32 * ks;
+                const uint32_t ya = gcp_s + Y0 + t0 + 4 * tq;
+                uint32_t af[4];
+                af[0] = lds32(ya);
+                af[1] = lds32(ya - 8);
+                af[2] = lds32(ya + 16);
+                af[3] = lds32(ya + 8);
+#pragma unroll
+                for (int jj = 0; jj < NTW; jj += 2) {
+                    if (jj >= ntile) break;
+                    int c = 8 * (tile0 + jj + (lane >> 4)) + (lane & 7);
+                    if (c >= cols) c = 0;
+                    uint32_t bf[4];
+                    ldsm_x4(bf, sig_s + (c + MS * ushift) * ROWB + t0 + 16 * kh);
+                    mma_s8(acc[jj], af, bf[0], bf[1]);
+                    if (jj + 1 < ntile) mma_s8(acc[jj + 1], af, bf[2], bf[3]);
+                }
+            }
+        }
+#pragma unroll
+        for (int jj = 0; jj < NTW; jj++) {
+            if (jj >= ntile) break;
+#pragma unroll
+            for (int h = 0; h < 4; h++) {
+                const int c = 8 * (tile0 + jj) + 2 * tq + (h & 1);
+                const int q = 16 * mt + gq + 8 * (h >> 1);
+                if (c < cols) {
+                    const int pr = c / MS, ms = c - pr * MS;
+                    stash[(ms * NPB + pr) * SP + q] = acc[jj][h];
+                }
+            }
+        }
+    } else {
+        // -- dp4a pipe: outputs i = npb * T + t + 64 r, r = 0..7, every plane --
+        const int t = tid - THREADS;               // 0 .. DT - 1
+        const int i_base = npb * T + t;
+        const int rho = (4 - (t & 3)) & 3;         // byte shift of this thread's filter reads
+        const uint32_t gd = smem_u32(gdp) + rho * GDP + N + 4 - rho - i_base;
+        int acc[R][MS];
+#pragma unroll
+        for (int r = 0; r < R; r++)
+#pragma unroll
+            for (int ms = 0; ms < MS; ms++) acc[r][ms] = 0;
+        for (int jb = 0; jb < NB; jb++) {
+            const int blk_rel = (jb + uch - 1) % NB;     // where input block jb sits in the window
+            const uint32_t srow = sig_s + blk_rel * MS * ROWB;
+#pragma unroll 2
+            for (int jj = 0; jj < T; jj += 4) {
+                const int j = jb * T + jj;
+                uint32_t s[MS];
+#pragma unroll
+                for (int ms = 0; ms < MS; ms++) s[ms] = lds32(srow + ms * ROWB + jj);
+                uint32_t gw[R];
+#pragma unroll
+                for (int r = 0; r < R; r++) gw[r] = lds32(gd + j - DT * r);
+#pragma unroll
+                for (int r = 0; r < R; r++)
+#pragma unroll
+                    for (int ms = 0; ms < MS; ms++) acc[r][ms] = __dp4a((int)s[ms], (int)gw[r], acc[r][ms]);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            const int o = t + DT * r;              // output index - npb * T
+#pragma unroll
+            for (int ms = 0; ms < MS; ms++) stash[(ms * NPB + npb + o / T) * SP + o % T] = acc[r][ms];
+        }
+    }
+    __syncthreads();
+    epilogue<MT>(a, stash, 0, NB, NTHR);
 }
 
 }  // namespace cconv

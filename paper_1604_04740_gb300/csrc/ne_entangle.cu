@@ -212,10 +212,10 @@ __global__ void __launch_bounds__(256) k_entangle_digits_fast(const int32_t* __r
                                                               int32_t* status) {
     const int64_t nchunk = n / 8;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    bool ok = true;
+    uint32_t worst = 0;
     for (FlatWalk w((int64_t)blockIdx.x * blockDim.x + threadIdx.x, stride, nchunk); w.b < batch; w.next())
-        ok &= entangle_chunk8<MT>(c + w.b * MT * n + w.q * 8, planes + w.b * MT * F.S * n + w.q * 8, n, l, F);
-    if (!ok && status) atomicExch(status, (int32_t)NE_ERANGE);
+        worst = max(worst, entangle_chunk8<MT>(c + w.b * MT * n + w.q * 8, planes + w.b * MT * F.S * n + w.q * 8, n, l, F));
+    if (worst > (uint32_t)F.hi - (uint32_t)F.lo && status) atomicExch(status, (int32_t)NE_ERANGE);
 }
 
 // int64 words with the same flat traversal: four positions per thread, the
@@ -325,8 +325,19 @@ extern "C" ne_status ne_entangle_digits(ne_params p, ne_digits dg, const int32_t
     P.top = dg.shift[dg.S - 1] / 8;   // digits above the top planned one must be 0
     const int T = 256;
     const bool vec8 = n % 8 == 0 && aligned(c, 16) && aligned(planes, 8);
+    // The fast path trusts the digit set only when it is exactly the plan of
+    // its recorded (l, lo, hi): then every in-range input forms words whose
+    // digits are in the set, and checking the inputs suffices.
     FastPlan F;
-    if (vec8 && p.M <= 5 && make_fast_plan(dg, p.l, &F)) {
+    bool planned = false;
+    if (dg.lo <= dg.hi && dg.l == p.l) {
+        ne_digits ref;
+        if (ne_plan_digits(dg.l, dg.lo, dg.hi, &ref) == NE_OK && ref.S == dg.S) {
+            planned = true;
+            for (int s2 = 0; s2 < dg.S; s2++) planned = planned && ref.shift[s2] == dg.shift[s2];
+        }
+    }
+    if (vec8 && p.M <= 5 && planned && make_fast_plan(dg, p.l, &F)) {
         const int blocks = flat_blocks(batch * (n / 8), T);
         switch (p.M) {
             case 3: k_entangle_digits_fast<3><<<blocks, T, 0, s>>>(c, planes, p.l, F, batch, n, status); break;

@@ -62,12 +62,14 @@ inline bool make_fast_plan(const ne_digits& dg, int l, FastPlan* F) {
 // Eight consecutive positions of the MT streams starting at cb (stream
 // stride n): 2 x 16-byte loads per stream, issued before any arithmetic, and
 // one 8-byte store per stored digit plane and stream (plane stride n, planes
-// of stream m at pb + m * S * n).  Returns false on an out-of-plan input.
-template <int MT>
-__device__ __forceinline__ bool entangle_chunk8(const int32_t* __restrict__ cb, int8_t* __restrict__ pb, int64_t n,
-                                                int l, const FastPlan& F) {
-    const uint32_t span = (uint32_t)F.hi - (uint32_t)F.lo;
-    bool ok = true;
+// of stream m at pb + m * S * n).  PLAIN: digits of the raw streams (no
+// predecessor term).  Returns the largest (value - lo) seen, as unsigned:
+// the inputs were in range iff it is <= hi - lo.  In-range inputs need no
+// further check: the plan enumerated the digits of every word they form.
+template <int MT, bool PLAIN = false>
+__device__ __forceinline__ uint32_t entangle_chunk8(const int32_t* __restrict__ cb, int8_t* __restrict__ pb,
+                                                    int64_t n, int l, const FastPlan& F) {
+    uint32_t worst = 0;
     int32_t v[MT][8];
 #pragma unroll
     for (int m = 0; m < MT; m++) {
@@ -76,7 +78,7 @@ __device__ __forceinline__ bool entangle_chunk8(const int32_t* __restrict__ cb, 
         v[m][0] = a.x; v[m][1] = a.y; v[m][2] = a.z; v[m][3] = a.w;
         v[m][4] = bb.x; v[m][5] = bb.y; v[m][6] = bb.z; v[m][7] = bb.w;
 #pragma unroll
-        for (int e = 0; e < 8; e++) ok &= ((uint32_t)v[m][e] - (uint32_t)F.lo <= span);
+        for (int e = 0; e < 8; e++) worst = max(worst, (uint32_t)v[m][e] - (uint32_t)F.lo);
     }
 #pragma unroll
     for (int m = 0; m < MT; m++) {
@@ -84,8 +86,8 @@ __device__ __forceinline__ bool entangle_chunk8(const int32_t* __restrict__ cb, 
         uint32_t y[8];
 #pragma unroll
         for (int e = 0; e < 8; e++) {
-            y[e] = (uint32_t)v[m][e] + (((uint32_t)v[pm][e] & F.pmask) << l) + F.off;
-            ok &= ((y[e] & F.ns_mask) == F.ns_want) && (F.lim == 0 || y[e] < F.lim);
+            if constexpr (PLAIN) y[e] = (uint32_t)v[m][e] + F.off;
+            else y[e] = (uint32_t)v[m][e] + ((uint32_t)v[pm][e] << l) + F.off;
         }
 #pragma unroll
         for (int s = 0; s < 4; s++) {
@@ -98,7 +100,7 @@ __device__ __forceinline__ bool entangle_chunk8(const int32_t* __restrict__ cb, 
                    make_uint2(w0 ^ 0x80808080u, w1 ^ 0x80808080u));
         }
     }
-    return ok;
+    return worst;
 }
 
 }  // namespace ne

@@ -100,6 +100,8 @@ def _load():
         "ne_abft_recover": [i32, P, i64, i64, i32, P],
         "ne_split_digits": [ne_digits, P, P, i64, i32, i64, P, P],
         "ne_probe_mma_peak": [i32, ctypes.POINTER(i64), P],
+        "ne_probe_dp4a_peak": [i32, ctypes.POINTER(i64), P],
+        "ne_probe_mixed_peak": [i32, i32, i32, i32, i32, ctypes.POINTER(i64), P],
         "ne_batch_plan": [ctypes.POINTER(ne_job), i32, ne_batch_config, P, i64, ctypes.POINTER(ne_batch_info), P],
         "ne_batch_run": [ne_batch_info, P, P, P, P, P, P, P, P, P, P, P],
         "ne_batch_run_static": [ctypes.POINTER(ne_job), i32, ne_batch_config, P, P, P, P, P, P, P, P, P, P],
@@ -209,6 +211,22 @@ def ne_split_digits(dg: ne_digits, x: torch.Tensor, P: int, planes: torch.Tensor
     _call("ne_split_digits", dg, _ptr(x, torch.int64, "x"), _ptr(planes, torch.int8, "planes"), batch, P, n,
           _ptr(status, torch.int32, "status", True), _stream())
     return planes
+
+
+def ne_probe_dp4a_peak(iters: int) -> int:
+    """The dp4a counterpart of ne_probe_mma_peak."""
+    ops = ctypes.c_int64()
+    _call("ne_probe_dp4a_peak", iters, ctypes.byref(ops), _stream())
+    return ops.value
+
+
+def ne_probe_mixed_peak(iters_mma: int, iters_dp4a: int, mma_warps: int, dp4a_warps: int,
+                        blocks_per_sm: int) -> int:
+    """Both int8 pipes in one launch (see ne_probe_mma_peak); returns the int8 operations issued."""
+    ops = ctypes.c_int64(0)
+    _call("ne_probe_mixed_peak", iters_mma, iters_dp4a, mma_warps, dp4a_warps, blocks_per_sm,
+          ctypes.byref(ops), _stream())
+    return ops.value
 
 
 def ne_probe_mma_peak(iters: int) -> int:

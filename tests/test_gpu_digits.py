@@ -49,6 +49,11 @@ CCONV_CASES = [
     (1, 4, 4096, 16, (-128, 127)),
     (2, 6, 256, 8, (-128, 127)),        # generic M
     (2, 3, 320, 14, (-1000, 1000)),     # wider inputs (|d| <= 320 * 1000 * 128 needs l = 14)
+    # 9..16 blocks with M*S in {6, 8}: the hybrid tile (tensor pipe + dp4a pipe)
+    (3, 3, 576, 16, (-128, 127)),       # one block on the tensor pipe, eight on dp4a
+    (2, 3, 960, 16, (-128, 127)),
+    (2, 4, 1024, 16, (-128, 127)),
+    (1, 4, 704, 16, (-128, 127)),
 ]
 
 
