@@ -60,11 +60,15 @@ def _L():
         lib.or_elementwise.argtypes = [i32, p, p, p, i64]
         lib.or_entangle_kernel_self.argtypes = [i32, p, p, i64]
         lib.or_extract.argtypes = [i32, i32, p, i64, i32, p, p]
+        lib.or_inner.argtypes = [p, p, p, i64, i64, i64]
+        lib.or_outer.argtypes = [p, p, p, i64, i64, i64, i64]
+        lib.or_permute.argtypes = [p, p, p, i64, i64, i64]
+        lib.or_cxcorr.argtypes = [p, p, p, i64, i64, i64]
         lib.or_abft_encode.argtypes = [i32, p, i64, p]
         lib.or_abft_check.argtypes = [i32, p, i64, p]
         lib.or_abft_recover.argtypes = [i32, p, i64, i32]
         for f in ("or_entangle", "or_gemm", "or_cconv", "or_elementwise", "or_entangle_kernel_self",
-                  "or_extract", "or_abft_encode", "or_abft_check", "or_abft_recover", "or_choose_l"):
+                  "or_extract", "or_inner", "or_outer", "or_permute", "or_cxcorr", "or_abft_encode", "or_abft_check", "or_abft_recover", "or_choose_l"):
             getattr(lib, f).restype = i32
         _lib = lib
     return _lib
@@ -163,6 +167,52 @@ def entangle_kernel_self(g, l: int):
     return out
 
 
+def inner(x, g):
+    """Inner products y[b, s] = sum_i x[b, s, i] g[b, i]; x int64 [B, S, n], g int64 [B, n]."""
+    x, px = _arr(x, np.int64)
+    g, pg = _arr(g, np.int64)
+    B, S, n = x.shape
+    assert g.shape == (B, n)
+    y = np.empty((B, S), np.int64)
+    _chk(_L().or_inner(px, pg, y.ctypes.data, B, S, n), "inner")
+    return y
+
+
+def outer(x, g):
+    """Outer products y[b, s, i, j] = x[b, s, i] g[b, j]; x int64 [B, S, n], g int64 [B, k]."""
+    x, px = _arr(x, np.int64)
+    g, pg = _arr(g, np.int64)
+    B, S, n = x.shape
+    k = g.shape[1]
+    assert g.shape[0] == B
+    y = np.empty((B, S, n, k), np.int64)
+    _chk(_L().or_outer(px, pg, y.ctypes.data, B, S, n, k), "outer")
+    return y
+
+
+def permute(x, g):
+    """y[b, s, i] = x[b, s, g[i]]; x int64 [B, S, n], g a permutation of range(n)."""
+    x, px = _arr(x, np.int64)
+    g, pg = _arr(g, np.int64)
+    B, S, n = x.shape
+    assert g.shape == (n,)
+    y = np.empty_like(x)
+    _chk(_L().or_permute(px, pg, y.ctypes.data, B, S, n), "permute")
+    return y
+
+
+def cxcorr(x, g):
+    """Circular cross-correlation y[.., i] = sum_j x[.., (i + j) mod N] g[.., j];
+    x int64 [B, S, N], g int8 [B, N]."""
+    x, px = _arr(x, np.int64)
+    g, pg = _arr(g, np.int8)
+    B, S, N = x.shape
+    assert g.shape == (B, N)
+    y = np.empty_like(x)
+    _chk(_L().or_cxcorr(px, pg, y.ctypes.data, B, S, N), "cxcorr")
+    return y
+
+
 # ---- extraction / check / recovery (Eq. 17-20, Eq. 24) ---------------------
 
 def extract(delta, l: int, r: int = 0, check: bool = True):
@@ -243,3 +293,37 @@ def cconv_entangled(c, g, l: int, r: int = 0):
     delta = cconv(eps, g)
     dhat, flags = extract(delta, l, r)
     return dhat, flags, delta
+
+
+LSB_OPS = ("add", "sub", "mul", "inner", "outer", "permute", "cxcorr")
+
+
+def lsb_apply(op: str, x, g):
+    """The operator of Eq. 2 on every signal of x (int64 [B, S, n]).  g: int64
+    [B, n] (add/sub/mul/inner), int64 [B, k] (outer), a permutation of
+    range(n) (permute) or int8 [B, n] (cxcorr)."""
+    x = np.asarray(x, np.int64)
+    if op in ("add", "sub", "mul"):
+        code = {"add": OP_ADD, "sub": OP_SUB, "mul": OP_MUL}[op]
+        return elementwise(code, x, np.broadcast_to(np.asarray(g, np.int64)[:, None, :], x.shape))
+    return {"inner": inner, "outer": outer, "permute": permute, "cxcorr": cxcorr}[op](x, g)
+
+
+def lsb_direct(op: str, c, g):
+    """The operator on the raw streams c (int32 [B, M, n])."""
+    return lsb_apply(op, np.asarray(c, np.int64), g)
+
+
+def lsb_entangled(op: str, c, g, l: int, r: int = 0):
+    """entangle (Eq. 16) -> the operator on every entangled stream (Eq. 10;
+    for + and - the kernel is first entangled with itself, the footnote to
+    Eq. 10) -> extract/check (Eq. 17-20, Eq. 24).  Returns (dhat, flags,
+    delta); delta is [B, M, ...] and flags cover each group's output
+    positions in row-major order."""
+    B, M = np.asarray(c).shape[:2]
+    eps = entangle(c, l)
+    if op in ("add", "sub"):
+        g = entangle_kernel_self(np.asarray(g, np.int64), l)
+    delta = lsb_apply(op, eps, g)
+    dhat, flags = extract(delta.reshape(B, M, -1), l, r)
+    return dhat.reshape(delta.shape), flags, delta

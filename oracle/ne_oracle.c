@@ -294,6 +294,94 @@ int or_entangle_kernel_self(int l, const int64_t *g, int64_t *ge, int64_t n) {
     return err;
 }
 
+/*
+ * The remaining LSB operators of Eq. 2, batched like or_cconv: B groups of S
+ * signals of length n, one kernel g per group.
+ *
+ * Inner product, op = <.,.>:  y[b][s] = sum_i x[b][s][i] g[b][i]
+ *   (x [B][S][n], g [B][n], y [B][S]); every partial sum must fit int64.
+ */
+int or_inner(const int64_t *x, const int64_t *g, int64_t *y, int64_t B, int64_t S, int64_t n) {
+    if (B < 0 || S < 0 || n < 0) return OR_EINVAL;
+    int err = OR_OK;
+    for (int64_t b = 0; b < B; b++) {
+        for (int64_t s = 0; s < S; s++) {
+            i128 acc = 0;
+            for (int64_t i = 0; i < n; i++) {
+                acc = checked_add(acc, checked_mul((i128)x[(b * S + s) * n + i], (i128)g[b * n + i], &err), &err);
+                if (!fits_i64(acc)) err = OR_EOVERFLOW;
+            }
+            y[b * S + s] = low64(acc);
+        }
+    }
+    return err;
+}
+
+/*
+ * Outer product, op = (x):  y[b][s][i][j] = x[b][s][i] g[b][j]
+ *   (x [B][S][n], g [B][k], y [B][S][n][k]).
+ */
+int or_outer(const int64_t *x, const int64_t *g, int64_t *y, int64_t B, int64_t S, int64_t n, int64_t k) {
+    if (B < 0 || S < 0 || n < 0 || k < 0) return OR_EINVAL;
+    int err = OR_OK;
+    for (int64_t b = 0; b < B; b++)
+        for (int64_t s = 0; s < S; s++)
+            for (int64_t i = 0; i < n; i++)
+                for (int64_t j = 0; j < k; j++) {
+                    i128 v = checked_mul((i128)x[(b * S + s) * n + i], (i128)g[b * k + j], &err);
+                    if (!fits_i64(v)) err = OR_EOVERFLOW;
+                    y[((b * S + s) * n + i) * k + j] = low64(v);
+                }
+    return err;
+}
+
+/*
+ * Permutation, op = (I over G), a bijection from the sequential index set to
+ * the index set given by g: output position i holds the input element at
+ * index g[i], y[b][s][i] = x[b][s][g[i]].  One index set serves every signal
+ * (the method covers data-independent permutations only).  g must be a
+ * permutation of 0..n-1; anything else is OR_EINVAL.
+ */
+int or_permute(const int64_t *x, const int64_t *g, int64_t *y, int64_t B, int64_t S, int64_t n) {
+    if (B < 0 || S < 0 || n < 0) return OR_EINVAL;
+    for (int64_t i = 0; i < n; i++)
+        if (g[i] < 0 || g[i] >= n) return OR_EINVAL;
+    for (int64_t i = 0; i < n; i++)           /* bijective: no index repeats */
+        for (int64_t j = i + 1; j < n; j++)
+            if (g[i] == g[j]) return OR_EINVAL;
+    for (int64_t bs = 0; bs < B * S; bs++)
+        for (int64_t i = 0; i < n; i++) y[bs * n + i] = x[bs * n + g[i]];
+    return OR_OK;
+}
+
+/*
+ * Circular cross-correlation, the correlation form of the star operator of
+ * Eq. 2:  y[b][s][i] = sum_{j=0}^{N-1} x[b][s][(i + j) mod N] g[b][j].
+ */
+int or_cxcorr(const int64_t *x, const int8_t *g, int64_t *y, int64_t B, int64_t S, int64_t N) {
+    if (B < 0 || S < 0 || N < 1) return OR_EINVAL;
+    int err = OR_OK;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int64_t bs = 0; bs < B * S; bs++) {
+        int lerr = OR_OK;
+        const int64_t *xs = x + bs * N;
+        const int8_t *gb = g + (bs / S) * N;
+        for (int64_t i = 0; i < N; i++) {
+            i128 acc = 0;
+            for (int64_t j = 0; j < N; j++) {
+                int64_t idx = (int64_t)floor_mod((i128)(i + j), (i128)N);
+                acc = checked_add(acc, checked_mul((i128)xs[idx], (i128)gb[j], &lerr), &lerr);
+                if (!fits_i64(acc)) lerr = OR_EOVERFLOW;
+            }
+            y[bs * N + i] = low64(acc);
+        }
+        if (lerr) set_err(&err, lerr);
+    }
+    return err;
+}
+
 /* ---- disentanglement, check and recovery (Eq. 17-20, Eq. 24) ------------ */
 
 /*

@@ -134,3 +134,92 @@ def test_inputs_generator_is_stable():
     gi, pos, j, b = inputs.fault_list(1, 10, 100, 3, 50)
     assert len(set(zip(gi.tolist(), pos.tolist()))) == 50
     assert j.max() < 3 and b.max() < 64
+
+
+# ---- the remaining LSB operators of Eq. 2 ----------------------------------
+
+def test_inner_matches_einsum_and_big_int():
+    rng = np.random.default_rng(7)
+    for B, S, n in [(1, 1, 1), (2, 3, 17), (3, 4, 256)]:
+        x = rng.integers(-(2 ** 30), 2 ** 30, (B, S, n), dtype=np.int64)
+        g = rng.integers(-(2 ** 20), 2 ** 20, (B, n), dtype=np.int64)
+        assert (oracle.inner(x, g) == np.einsum("bsi,bi->bs", x, g)).all()
+    x = np.array([[[2 ** 40, -3, 5]]], np.int64)
+    g = np.array([[2 ** 20, 7, -(2 ** 21)]], np.int64)
+    assert oracle.inner(x, g).tolist() == [[2 ** 60 - 21 - 5 * 2 ** 21]]
+    with pytest.raises(oracle.OracleError):       # a partial sum leaves int64
+        oracle.inner(np.array([[[2 ** 62, 2 ** 62]]], np.int64), np.array([[2, -2]], np.int64))
+
+
+def test_outer_matches_einsum():
+    rng = np.random.default_rng(8)
+    x = rng.integers(-(2 ** 30), 2 ** 30, (2, 3, 7), dtype=np.int64)
+    g = rng.integers(-(2 ** 20), 2 ** 20, (2, 5), dtype=np.int64)
+    assert (oracle.outer(x, g) == np.einsum("bsi,bj->bsij", x, g)).all()
+    assert oracle.outer(np.array([[[2, -3]]], np.int64), np.array([[5, 7, -1]], np.int64)).tolist() == \
+        [[[[10, 14, -2], [-15, -21, 3]]]]
+
+
+def test_permute_gathers_and_composes():
+    rng = np.random.default_rng(9)
+    n = 37
+    x = rng.integers(-(2 ** 40), 2 ** 40, (2, 3, n), dtype=np.int64)
+    p, q = rng.permutation(n), rng.permutation(n)
+    assert (oracle.permute(x, p) == x[..., p]).all()
+    assert (oracle.permute(x, np.arange(n)) == x).all()
+    # gathering by p then by q is gathering by p[q]
+    assert (oracle.permute(oracle.permute(x, p), q) == oracle.permute(x, p[q])).all()
+    # the inverse permutation undoes it
+    assert (oracle.permute(oracle.permute(x, p), np.argsort(p)) == x).all()
+    assert oracle.permute(np.array([[[10, 20, 30]]], np.int64), np.array([2, 0, 1])).tolist() == [[[30, 10, 20]]]
+    for bad in ([0, 0, 1], [0, 1, 3], [-1, 0, 1]):   # not a bijection of {0, 1, 2}
+        with pytest.raises(oracle.OracleError):
+            oracle.permute(np.zeros((1, 1, 3), np.int64), np.array(bad))
+
+
+def test_cxcorr_matches_numpy_correlate_and_brute_force():
+    rng = np.random.default_rng(10)
+    for N in (1, 2, 5, 64, 129):
+        x = rng.integers(-(2 ** 20), 2 ** 20, (2, 2, N), dtype=np.int64)
+        g = rng.integers(-128, 128, (2, N)).astype(np.int8)
+        y = oracle.cxcorr(x, g)
+        for b in range(2):
+            for s in range(2):
+                # linear correlation of the doubled signal, first N lags
+                want = np.correlate(np.concatenate([x[b, s], x[b, s]]), g[b].astype(np.int64), "valid")[:N]
+                assert (y[b, s] == want).all()
+    # y[i] = sum_j x[(i + j) mod 3] g[j] with g = (1, 0, -1):  y_i = x_i - x_{i+2}
+    x = np.array([[[1, 2, 4]]], np.int64)
+    assert oracle.cxcorr(x, np.array([[1, 0, -1]], np.int8))[0, 0].tolist() == [1 - 4, 2 - 1, 4 - 2]
+
+
+def lsb_operand(op, B, n, seed):
+    rng = np.random.default_rng(seed)
+    if op == "outer":
+        return rng.integers(-128, 128, (B, 9), dtype=np.int64)
+    if op == "permute":
+        return rng.permutation(n)
+    if op == "cxcorr":
+        return rng.integers(-128, 128, (B, n)).astype(np.int8)
+    return rng.integers(-128, 128, (B, n), dtype=np.int64)
+
+
+@pytest.mark.parametrize("op", oracle.LSB_OPS)
+@pytest.mark.parametrize("M,l", [(3, 16), (4, 16), (5, 12)])
+def test_lsb_pipeline_equals_direct_flags_and_recovers(op, M, l):
+    B, n = 2, 40
+    c = inputs.streams(2, (B, M, n))
+    g = lsb_operand(op, B, n, M)
+    direct = oracle.lsb_direct(op, c, g)
+    for r in range(M):
+        dh, fl, delta = oracle.lsb_entangled(op, c, g, l, r)
+        assert (dh == direct).all() and not fl.any()
+        flat = delta.reshape(B, M, -1)
+        # Prop. 3: any one stream rebuilt from the others
+        assert (oracle.recover(flat, l, (r + 1) % M).reshape(dh.shape) == direct).all()
+        # Prop. 4: a bit flip in any one stream is flagged at exactly that position
+        bad = flat.copy()
+        pos = flat.shape[-1] // 2
+        bad[1, (r + 2) % M, pos] ^= np.int64(1) << np.int64(5 + r)
+        _, f2 = oracle.extract(bad, l, r)
+        assert f2[1, pos] and f2.sum() == 1
