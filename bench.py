@@ -569,10 +569,49 @@ def cconv_extras(torch, ne, wl, dev, flush, step, p, dg, planes, g, out, ms_step
         "check": (lambda ev: ne.ne_check(pl, d64, 0, fl, None), nw * 8 + fl.numel() * 4),
         "recover": (lambda ev: ne.ne_recover(pl, d64, 1, o64), nw * 8 * (M - 1) // M + nw * 8),
     }
+    # (9) the other LSB operators of Eq. 2 on the same entangled streams, each one
+    # pass with the extract/check fused behind it (HBM roofline)
+    g64 = torch.from_numpy(wl.g.astype(np.int64)).to(dev)
+    ge64 = ne.ne_entangle_kernel_self(pl.l, g64)
+    perm = torch.from_numpy(np.random.default_rng(0).permutation(N).astype(np.int32)).to(dev)
+    kout = 8
+    gk = g64[:, :kout].contiguous()
+    outk = torch.empty((G, M, N, kout), dtype=torch.int64, device=dev)
+    flk = torch.empty(G * N * kout // 32, dtype=torch.int32, device=dev)
+    inner_out = torch.empty((G, M), dtype=torch.int64, device=dev)
+    fli = torch.empty(G, dtype=torch.int32, device=dev)
+    FX = ne.NE_FUSE_EXTRACT_CHECK
+    passes.update({
+        "elementwise_mul_extract_check": (
+            lambda ev: ne.ne_elementwise(pl, ne.NE_OP_MUL, eps, g64, o64, fl, None, FX, 0),
+            nw * 16 + G * N * 8 + fl.numel() * 4),
+        "elementwise_add_extract_check": (
+            lambda ev: ne.ne_elementwise(pl, ne.NE_OP_ADD, eps, ge64, o64, fl, None, FX, 0),
+            nw * 16 + G * N * 8 + fl.numel() * 4),
+        "permute_extract_check": (
+            lambda ev: ne.ne_permute(pl, eps, perm, o64, fl, None, FX, 0),
+            nw * 16 + N * 4 + fl.numel() * 4),
+        "inner_extract_check": (
+            lambda ev: ne.ne_inner(pl, eps, g64, inner_out, fli, None, FX, 0),
+            nw * 8 + G * N * 8 + G * M * 8 + G * 4),
+        f"outer_k{kout}_extract_check": (
+            lambda ev: ne.ne_outer(pl, eps, gk, outk, flk, None, FX, 0),
+            nw * 8 + G * kout * 8 + nw * kout * 8 + flk.numel() * 4),
+    })
     pass_ms = {}
     for name, (fn, _) in passes.items():
         tp, _ = timed_steps(torch, fn, K, W, flush)
         pass_ms[name] = tp / K
+    # circular cross-correlation: the convolution step with the operand reversed first
+    grev = torch.empty_like(g)
+
+    def xcorr(ev):
+        ne.ne_reverse_operand(g, grev)
+        ne.ne_entangle_digits(p, dg, c, planes)
+        ne.ne_cconv_digits(p, dg, planes, grev, out2, fl, None, FX, 0)
+
+    t_x, _ = timed_steps(torch, xcorr, K, W, flush)
+    del outk
     torch.cuda.synchronize()
     ms = lambda t, k: t / k  # noqa: E731
     res["overhead_pct"] = {
@@ -585,7 +624,7 @@ def cconv_extras(torch, ne, wl, dev, flush, step, p, dg, planes, g, out, ms_step
     res["ms"] = {"entangled_step": ent_ms, "plain_same_digits": ms(t_same, K), "plain_one_digit": ms(t_min, K),
                  "plain_int64": ms(t_pi, Ki), "entangled_int64": ms(t_ei, Ki), "abft_tensor": ms(t_abft, K),
                  "abft_int64": ms(t_ai, Ki), "fail_stop_recovery_step": ms(t_rec, K),
-                 "entangle_digits_pass": ms(t_e, K)}
+                 "entangle_digits_pass": ms(t_e, K), "cross_correlation_step": ms(t_x, K)}
     res["entangle_pass_hbm"] = {"bytes": ent_bytes, "GB/s": ent_bytes / (ms(t_e, K) * 1e-3) / 1e9,
                                 "peak_GB/s": hbm_peak, "frac": (ent_bytes / (ms(t_e, K) * 1e-3) / 1e9 / hbm_peak)
                                 if hbm_peak else None}

@@ -213,6 +213,67 @@ ne_status ne_inject(int64_t* delta, int32_t P, int64_t batch, int64_t n,
                     const int64_t* bit, int64_t count, int32_t* status, cudaStream_t s);
 
 /* ------------------------------------------------------------------------ */
+/* The other LSB operators of Eq. 2 on the entangled streams                 */
+/* ------------------------------------------------------------------------ */
+/*
+ * Each call applies its operator to every entangled stream eps[b][m] (int64
+ * [batch][M][n]) in wrapping 64-bit arithmetic -- exact whenever the true
+ * results fit 64 bits, which the choice of l guarantees for in-range inputs --
+ * and fuses the same epilogues as ne_gemm_digits behind it:
+ *  fuse = NE_FUSE_NONE:          out = delta_m for every stream (r ignored).
+ *  fuse = NE_FUSE_EXTRACT_CHECK: out = d_hat of Eq. 17-20 using every stream
+ *        but r; flags (nullable) get the Eq. 24 check of stream r, one bit per
+ *        output position, uint32 [batch][ceil(P/32)] with P the output
+ *        positions per group; *nflag (nullable) their count.
+ *  fuse = NE_FUSE_RECOVER:       stream r is neither read nor computed; out =
+ *        d_hat from the other M-1 streams (Prop. 3).
+ * out must not overlap eps.  The operand of group b is at g + b * g_stride
+ * (g_stride = 0: one operand shared by every group).
+ */
+#define NE_OP_ADD 0
+#define NE_OP_SUB 1
+#define NE_OP_MUL 2
+
+/* Element-wise +, -, x (Eq. 2): delta[b][m][i] = eps[b][m][i] op g_b[i];
+ * out: int64 [batch][M][n].  For + and - the operand must be entangled with
+ * itself first (ne_entangle_kernel_self, the footnote to Eq. 10) so that
+ * the result is again a codeword of Eq. 16. */
+ne_status ne_elementwise(ne_params p, int32_t op, const int64_t* eps, const int64_t* g, int64_t g_stride,
+                         int64_t* out, uint32_t* flags, uint64_t* nflag, int64_t batch, int64_t n,
+                         int32_t fuse, int32_t r, cudaStream_t s);
+
+/* The footnote to Eq. 10: ge[i] = 2^l g[i] + g[i] (int64, n entries). */
+ne_status ne_entangle_kernel_self(int32_t l, const int64_t* g, int64_t* ge, int64_t n, cudaStream_t s);
+
+/* Outer product (Eq. 2): delta[b][m][i][j] = eps[b][m][i] g_b[j], j < k;
+ * out: int64 [batch][M][n][k]; output positions i*k + j (P = n*k). */
+ne_status ne_outer(ne_params p, const int64_t* eps, const int64_t* g, int64_t g_stride, int64_t* out,
+                   uint32_t* flags, uint64_t* nflag, int64_t batch, int64_t n, int64_t k,
+                   int32_t fuse, int32_t r, cudaStream_t s);
+
+/* Permutation (Eq. 2, the bijection from the sequential index set to the
+ * index set perm): delta[b][m][i] = eps[b][m][perm[i]]; perm: int32 [n],
+ * one index set for every group (data-independent, as the method requires),
+ * a permutation of 0..n-1 by contract.  An entry outside [0, n) is not
+ * followed (position 0 is read instead) and sets *status = NE_EINVAL
+ * (status: device int32, nullable). */
+ne_status ne_permute(ne_params p, const int64_t* eps, const int32_t* perm, int64_t* out,
+                     uint32_t* flags, uint64_t* nflag, int64_t batch, int64_t n,
+                     int32_t fuse, int32_t r, int32_t* status, cudaStream_t s);
+
+/* Inner product (Eq. 2): delta[b][m] = sum_i eps[b][m][i] g_b[i];
+ * out: int64 [batch][M]; one output position per group (flags [batch]). */
+ne_status ne_inner(ne_params p, const int64_t* eps, const int64_t* g, int64_t g_stride, int64_t* out,
+                   uint32_t* flags, uint64_t* nflag, int64_t batch, int64_t n,
+                   int32_t fuse, int32_t r, cudaStream_t s);
+
+/* Circular cross-correlation y[i] = sum_j x[(i + j) mod N] g[j] is the
+ * circular convolution of x with g_rev[j] = g[(N - j) mod N]: this writes
+ * g_rev (int8 [batch][N]) so that ne_cconv / ne_cconv_digits compute the
+ * correlation form of the star operator of Eq. 2.  g_rev must not alias g. */
+ne_status ne_reverse_operand(const int8_t* g, int8_t* g_rev, int64_t batch, int64_t N, cudaStream_t s);
+
+/* ------------------------------------------------------------------------ */
 /* Checksum ABFT comparator (Eq. 3-6, Sec. II-A)                             */
 /* ------------------------------------------------------------------------ */
 

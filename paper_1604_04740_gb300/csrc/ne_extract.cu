@@ -8,6 +8,7 @@
 // warp shuffles, not atomics.
 #include "ne_common.cuh"
 #include "ne_extract.cuh"
+#include "ne_flags.cuh"
 
 namespace {
 
@@ -15,28 +16,6 @@ using namespace ne;
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-
-// flags of one segment: VEC bits per lane -> bitmap words (see file comment)
-template <int VEC>
-__device__ __forceinline__ void emit_flags(uint32_t f, int lane, int64_t seg, int64_t wpr,
-                                           uint32_t* flags_row, unsigned long long* nflag) {
-    if constexpr (VEC == 2) {
-        uint32_t v = halfwarp_or(f << (2 * (lane & 15)));
-        if ((lane & 15) == 0) {
-            int64_t w = 2 * seg + (lane >> 4);
-            if (w < wpr) {
-                if (flags_row) flags_row[w] = v;
-                if (nflag && v) atomicAdd(nflag, (unsigned long long)__popc(v));
-            }
-        }
-    } else {
-        uint32_t v = __ballot_sync(0xffffffffu, f != 0);
-        if (lane == 0 && seg < wpr) {
-            if (flags_row) flags_row[seg] = v;
-            if (nflag && v) atomicAdd(nflag, (unsigned long long)__popc(v));
-        }
-    }
-}
 
 template <int MT, int VEC, bool WRITE_D, bool CHECK>
 __global__ void __launch_bounds__(kThreads) k_extract(const int64_t* __restrict__ delta, int64_t* __restrict__ dhat,

@@ -106,6 +106,12 @@ def _load():
         "ne_batch_run": [ne_batch_info, P, P, P, P, P, P, P, P, P, P, P],
         "ne_batch_run_static": [ctypes.POINTER(ne_job), i32, ne_batch_config, P, P, P, P, P, P, P, P, P, P],
         "ne_copy_regions_h2d": [P, P, P, P, P, i64, P],
+        "ne_elementwise": [ne_params, i32, P, P, i64, P, P, P, i64, i64, i32, i32, P],
+        "ne_entangle_kernel_self": [i32, P, P, i64, P],
+        "ne_outer": [ne_params, P, P, i64, P, P, P, i64, i64, i64, i32, i32, P],
+        "ne_permute": [ne_params, P, P, P, P, P, i64, i64, i32, i32, P, P],
+        "ne_inner": [ne_params, P, P, i64, P, P, P, i64, i64, i32, i32, P],
+        "ne_reverse_operand": [P, P, i64, i64, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -297,6 +303,98 @@ def ne_cconv_digits(p: ne_params, dg: ne_digits, planes: torch.Tensor, g: torch.
           _ptr(out, torch.int64, "out"), _ptr(flags, torch.int32, "flags", True),
           _ptr(nflag, torch.int64, "nflag", True), batch, N, fuse, r, _stream())
     return out
+
+
+# ---- the other LSB operators of Eq. 2 ----------------------------------------------
+
+NE_OP_ADD, NE_OP_SUB, NE_OP_MUL = 0, 1, 2
+
+
+def _operand_stride(g: torch.Tensor, batch: int, length: int) -> int:
+    """g is one operand [length] shared by every group, or [batch, length]."""
+    if g.dim() == 1 and g.shape[0] == length:
+        return 0
+    if tuple(g.shape) == (batch, length):
+        return length
+    raise ValueError(f"operand must be [{length}] or [{batch}, {length}], got {tuple(g.shape)}")
+
+
+def ne_elementwise(p: ne_params, op: int, eps: torch.Tensor, g: torch.Tensor, out: torch.Tensor | None = None,
+                   flags: torch.Tensor | None = None, nflag: torch.Tensor | None = None,
+                   fuse: int = NE_FUSE_EXTRACT_CHECK, r: int = 0) -> torch.Tensor:
+    """eps int64 [..., M, n]; g int64 [n] or [batch, n] -> int64 like eps."""
+    batch, n = _bmn(eps, p.M)
+    gs = _operand_stride(g, batch, n)
+    if out is None:
+        out = torch.empty_like(eps)
+    _call("ne_elementwise", p, op, _ptr(eps, torch.int64, "eps"), _ptr(g, torch.int64, "g"), gs,
+          _ptr(out, torch.int64, "out"), _ptr(flags, torch.int32, "flags", True),
+          _ptr(nflag, torch.int64, "nflag", True), batch, n, fuse, r, _stream())
+    return out
+
+
+def ne_entangle_kernel_self(l: int, g: torch.Tensor, ge: torch.Tensor | None = None) -> torch.Tensor:
+    if ge is None:
+        ge = torch.empty_like(g)
+    _call("ne_entangle_kernel_self", l, _ptr(g, torch.int64, "g"), _ptr(ge, torch.int64, "ge"), g.numel(),
+          _stream())
+    return ge
+
+
+def ne_outer(p: ne_params, eps: torch.Tensor, g: torch.Tensor, out: torch.Tensor | None = None,
+             flags: torch.Tensor | None = None, nflag: torch.Tensor | None = None,
+             fuse: int = NE_FUSE_EXTRACT_CHECK, r: int = 0) -> torch.Tensor:
+    """eps int64 [batch, M, n]; g int64 [k] or [batch, k] -> int64 [batch, M, n, k]."""
+    batch, M, n = eps.shape
+    if M != p.M:
+        raise ValueError("eps must be [batch, M, n]")
+    k = g.shape[-1]
+    gs = _operand_stride(g, batch, k)
+    if out is None:
+        out = torch.empty((batch, M, n, k), dtype=torch.int64, device=eps.device)
+    _call("ne_outer", p, _ptr(eps, torch.int64, "eps"), _ptr(g, torch.int64, "g"), gs,
+          _ptr(out, torch.int64, "out"), _ptr(flags, torch.int32, "flags", True),
+          _ptr(nflag, torch.int64, "nflag", True), batch, n, k, fuse, r, _stream())
+    return out
+
+
+def ne_permute(p: ne_params, eps: torch.Tensor, perm: torch.Tensor, out: torch.Tensor | None = None,
+               flags: torch.Tensor | None = None, nflag: torch.Tensor | None = None,
+               fuse: int = NE_FUSE_EXTRACT_CHECK, r: int = 0, status: torch.Tensor | None = None) -> torch.Tensor:
+    """eps int64 [..., M, n]; perm int32 [n] -> int64 like eps (out[..., i] = eps[..., perm[i]])."""
+    batch, n = _bmn(eps, p.M)
+    if tuple(perm.shape) != (n,):
+        raise ValueError("perm must be [n]")
+    if out is None:
+        out = torch.empty_like(eps)
+    _call("ne_permute", p, _ptr(eps, torch.int64, "eps"), _ptr(perm, torch.int32, "perm"),
+          _ptr(out, torch.int64, "out"), _ptr(flags, torch.int32, "flags", True),
+          _ptr(nflag, torch.int64, "nflag", True), batch, n, fuse, r, _ptr(status, torch.int32, "status", True),
+          _stream())
+    return out
+
+
+def ne_inner(p: ne_params, eps: torch.Tensor, g: torch.Tensor, out: torch.Tensor | None = None,
+             flags: torch.Tensor | None = None, nflag: torch.Tensor | None = None,
+             fuse: int = NE_FUSE_EXTRACT_CHECK, r: int = 0) -> torch.Tensor:
+    """eps int64 [..., M, n]; g int64 [n] or [batch, n] -> int64 [..., M]."""
+    batch, n = _bmn(eps, p.M)
+    gs = _operand_stride(g, batch, n)
+    if out is None:
+        out = torch.empty(tuple(eps.shape[:-1]), dtype=torch.int64, device=eps.device)
+    _call("ne_inner", p, _ptr(eps, torch.int64, "eps"), _ptr(g, torch.int64, "g"), gs,
+          _ptr(out, torch.int64, "out"), _ptr(flags, torch.int32, "flags", True),
+          _ptr(nflag, torch.int64, "nflag", True), batch, n, fuse, r, _stream())
+    return out
+
+
+def ne_reverse_operand(g: torch.Tensor, g_rev: torch.Tensor | None = None) -> torch.Tensor:
+    """g int8 [batch, N] -> g_rev[b, j] = g[b, (N - j) mod N]."""
+    batch, N = g.shape
+    if g_rev is None:
+        g_rev = torch.empty_like(g)
+    _call("ne_reverse_operand", _ptr(g, torch.int8, "g"), _ptr(g_rev, torch.int8, "g_rev"), batch, N, _stream())
+    return g_rev
 
 
 # ---- extraction / check / recovery ---------------------------------------------

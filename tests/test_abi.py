@@ -114,3 +114,33 @@ def test_host_argument_checks_reject_before_any_launch(lib):
     assert lib.ne_entangle(Params(3, 11, 64), None, fake, 1, 8, None) == 1
     # empty problem is a no-op
     assert lib.ne_entangle(Params(3, 11, 64), None, None, 0, 0, None) == 0
+
+
+def test_lsb_operator_argument_checks(lib):
+    P, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    lib.ne_elementwise.argtypes = [Params, i32, P, P, i64, P, P, P, i64, i64, i32, i32, P]
+    lib.ne_outer.argtypes = [Params, P, P, i64, P, P, P, i64, i64, i64, i32, i32, P]
+    lib.ne_permute.argtypes = [Params, P, P, P, P, P, i64, i64, i32, i32, P, P]
+    lib.ne_inner.argtypes = [Params, P, P, i64, P, P, P, i64, i64, i32, i32, P]
+    lib.ne_entangle_kernel_self.argtypes = [i32, P, P, i64, P]
+    lib.ne_reverse_operand.argtypes = [P, P, i64, i64, P]
+    fake = ctypes.c_void_p(0x1000)
+    ok = Params(3, 16, 64)
+    # unknown operator, negative operand stride, unknown epilogue, r out of range
+    assert lib.ne_elementwise(ok, 3, fake, fake, 0, fake, None, None, 1, 8, 0, 0, None) == 1
+    assert lib.ne_elementwise(ok, 0, fake, fake, -1, fake, None, None, 1, 8, 0, 0, None) == 1
+    assert lib.ne_elementwise(ok, 0, fake, fake, 0, fake, None, None, 1, 8, 7, 0, None) == 1
+    assert lib.ne_elementwise(ok, 0, fake, fake, 0, fake, None, None, 1, 8, 1, 3, None) == 1
+    # Eq. 13 still applies
+    assert lib.ne_inner(Params(3, 32, 64), fake, fake, 0, fake, None, None, 1, 8, 0, 0, None) == 2
+    # null operand / index set
+    assert lib.ne_outer(ok, fake, None, 0, fake, None, None, 1, 8, 4, 0, 0, None) == 1
+    assert lib.ne_permute(ok, fake, None, fake, None, None, 1, 8, 0, 0, None, None) == 1
+    # n * k beyond the supported output size
+    assert lib.ne_outer(ok, fake, fake, 0, fake, None, None, 1, 1 << 30, 1 << 30, 0, 0, None) == 1
+    # operand preparations: bad l, aliasing
+    assert lib.ne_entangle_kernel_self(0, fake, fake, 8, None) == 1
+    assert lib.ne_reverse_operand(fake, fake, 1, 8, None) == 1
+    # empty problems are no-ops
+    assert lib.ne_elementwise(ok, 0, None, None, 0, None, None, None, 0, 0, 0, 0, None) == 0
+    assert lib.ne_inner(ok, None, None, 0, None, None, None, 0, 0, 0, 0, None) == 0
