@@ -10,6 +10,8 @@ Workloads (--workload):
   cconv   batched circular convolution: 4096 groups x M = 3 streams of
           length-1024 int32 signals in [-128, 127], one int8 filter per group
           (the default; the configuration the headline metric is quoted on)
+  cconv_ntt  the same convolution through the exact number-theoretic transform
+          (one fused launch from the raw streams to the extracted outputs)
   gemm    M = 4 streams of 4096 x 4096 int32 matrices times one shared
           4096 x 4096 int8 matrix
   gemm64  M = 3 streams of 64 x 64 times a shared 64 x 64 int8 matrix on the
@@ -43,6 +45,23 @@ sys.path.insert(0, ROOT)
 
 METRIC = "entangled int GEMM/conv Gop/s & overhead % vs plain, same GB300, bit-exact"
 L2_FLUSH_BYTES = 256 << 20
+L2_NOTE = ("flushed before every timed step: 256 MiB written, then a second 256 MiB buffer read, so the "
+           "step's inputs are not in L2 and the flush's own dirty lines are written back before the step")
+
+
+class L2Flush:
+    """Evicts the previous step's data from L2 outside the timed region: a
+    buffer larger than L2 is written, then another one is read so that the
+    written lines are written back now rather than during the next step."""
+
+    def __init__(self, torch, dev):
+        self.w = torch.zeros(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+        self.r = torch.ones(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+        self.sink = torch.zeros((), dtype=torch.int64, device=dev)
+
+    def __call__(self):
+        self.w.add_(1)
+        self.sink.copy_(self.r.sum())
 
 
 def parse():
@@ -51,13 +70,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="cconv", choices=["cconv", "gemm", "gemm64", "batch", "serve"])
+    ap.add_argument("--workload", default="cconv", choices=["cconv", "cconv_ntt", "gemm", "gemm64", "batch", "serve"])
     ap.add_argument("--jobs", type=int, default=2048, help="jobs of the ragged batch workload")
     ap.add_argument("--no-extras", action="store_true", help="skip overhead, ABFT and CPU-baseline legs")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target length of the CPU-baseline sample")
     a = ap.parse_args()
     if a.steps is None:
-        a.steps = {"cconv": 400, "gemm": 20, "gemm64": 2000, "batch": 10, "serve": 1}[a.workload]
+        a.steps = {"cconv": 400, "cconv_ntt": 400, "gemm": 20, "gemm64": 2000, "batch": 10, "serve": 1}[a.workload]
     return a
 
 
@@ -67,13 +86,15 @@ class Workload:
     def __init__(self, name):
         from paper_1604_04740_gb300 import inputs
         self.name = name
-        if name == "cconv":
+        if name in ("cconv", "cconv_ntt"):
             self.G, self.M, self.N = 4096, 3, 1024
             self.c = inputs.streams(0, (self.G, self.M, self.N))
             self.g = inputs.operator_int8(0, (self.G, self.N))
             self.bound = self.N * 2 ** 14
             self.useful_ops = 2 * self.G * self.M * self.N ** 2
             self.desc = f"batched circular convolution: {self.G} groups x M={self.M} x N={self.N}, int8 filter per group"
+            if name == "cconv_ntt":
+                self.desc += ", number-theoretic transform"
         elif name == "gemm":
             self.M, self.n = 4, 4096
             self.c = inputs.streams(0, (self.M, self.n, self.n))
@@ -149,7 +170,7 @@ def timed_steps(torch, step, K, W, flush, inner=None):
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
     inner_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
     for k in range(K):
-        flush.add_(1)
+        flush()
         ev[k][0].record(stream)
         step(inner_ev[k])
         ev[k][1].record(stream)
@@ -180,6 +201,18 @@ def traffic_for(kernel, src_files):
     return rec.get("bytes_per_launch")
 
 
+def ntt_imad_per_group(planes, N):
+    """32-bit multiplies of the transform convolution per group: every digit
+    plane (planes of them) is transformed forward and back and the filter
+    forward; a 1024-point transform is two in-register 32-point transforms
+    (49 non-trivial butterflies each, one 3-multiply Shoup product per
+    butterfly) and 32 twiddle products per lane; the pointwise products and
+    the filter's scaling are 4-multiply Montgomery products."""
+    assert N == 1024
+    per_transform = 32 * (2 * 49 * 3 + 32 * 3)
+    return (2 * planes + 1) * per_transform + (planes + 1) * N * 4
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -194,7 +227,7 @@ def oracle_sample(wl, seconds, compare=None):
     workload.  Returns (Gop/s, threads, sample description, parity)."""
     import oracle
     from paper_1604_04740_gb300 import inputs  # noqa: F401
-    if wl.name == "cconv":
+    if wl.name in ("cconv", "cconv_ntt"):
         l, _ = oracle.choose_l(wl.M, 64, wl.bound, oracle.POLICY_BYTE)
         t0 = time.perf_counter()
         oracle.cconv_entangled(wl.c[:1], wl.g[:1], l, 0)
@@ -257,7 +290,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(dev)
     wl = Workload(args.workload)
     K, W = args.steps, args.warmup
-    flush = torch.zeros(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    flush = L2Flush(torch, dev)
     extras = {}
 
     if wl.name == "cconv":
@@ -289,7 +322,36 @@ def run_ours(args, rank, world, local_rank):
         h2d = wl.c.nbytes + wl.g.nbytes
         d2h = out.numel() * 8 + flags.numel() * 4 + 8
         cfg = {"workload": wl.desc, "l": l, "k": k, "digits": list(dg.shifts), "global_batch": G,
-               "l2": "flushed (256 MiB write) before every timed step", "parallelism": f"replicas x{world}"}
+               "l2": L2_NOTE, "parallelism": f"replicas x{world}"}
+    elif wl.name == "cconv_ntt":
+        M, G, N = wl.M, wl.G, wl.N
+        l, k = ne.ne_choose_l(M, 64, wl.bound, ne.NE_L_BYTE)
+        p = ne.params(M, l)
+        dg = ne.ne_plan_digits(l, -128, 127)
+        c = torch.from_numpy(wl.c).to(dev)
+        g = torch.from_numpy(wl.g).to(dev)
+        out = torch.empty((G, M, N), dtype=torch.int64, device=dev)
+        flags = torch.empty(G * N // 32, dtype=torch.int32, device=dev)
+        nflag = torch.zeros(1, dtype=torch.int64, device=dev)
+        status = torch.zeros(1, dtype=torch.int32, device=dev)
+        stream = torch.cuda.current_stream()
+
+        def step(ev):
+            if ev is not None:
+                ev[0].record(stream)
+            ne.ne_cconv_ntt(p, dg, c, g, out, flags, nflag, ne.NE_FUSE_EXTRACT_CHECK, 0, status=status)
+            if ev is not None:
+                ev[1].record(stream)
+
+        launches_per_step = 1
+        mma_ops_per_launch = None
+        imad_per_launch = G * ntt_imad_per_group(M * dg.S, N)
+        dominant = "ne_cconv_ntt"
+        dom_src = ("ne_ntt.cu", "ne_entangle.cuh", "ne_extract.cuh")
+        h2d = wl.c.nbytes + wl.g.nbytes
+        d2h = out.numel() * 8 + flags.numel() * 4 + 8
+        cfg = {"workload": wl.desc, "l": l, "k": k, "digits": list(dg.shifts), "global_batch": G,
+               "l2": L2_NOTE, "parallelism": f"replicas x{world}"}
     elif wl.name == "gemm":
         M, n = wl.M, wl.n
         l, k = ne.ne_choose_l(M, 64, wl.bound, ne.NE_L_BYTE)
@@ -320,7 +382,7 @@ def run_ours(args, rank, world, local_rank):
         h2d = wl.c.nbytes + wl.Gm.nbytes
         d2h = out.numel() * 8 + flags.numel() * 4 + 8
         cfg = {"workload": wl.desc, "l": l, "k": k, "digits": list(dg.shifts),
-               "l2": "flushed (256 MiB write) before every timed step", "parallelism": f"replicas x{world}"}
+               "l2": L2_NOTE, "parallelism": f"replicas x{world}"}
     else:
         M, n = wl.M, wl.n
         l, k = ne.ne_choose_l(M, 64, wl.bound, ne.NE_L_SMALLEST)
@@ -349,7 +411,7 @@ def run_ours(args, rank, world, local_rank):
         dom_src = ("ne_ops_i64.cu",)
         h2d = wl.c.nbytes + wl.Gm.nbytes
         d2h = out.numel() * 8 + flags.numel() * 4 + 8
-        cfg = {"workload": wl.desc, "l": l, "k": k, "l2": "flushed (256 MiB write) before every timed step",
+        cfg = {"workload": wl.desc, "l": l, "k": k, "l2": L2_NOTE,
                "parallelism": f"replicas x{world}"}
 
     # --- main timed region ---------------------------------------------------------------
@@ -424,6 +486,22 @@ def run_ours(args, rank, world, local_rank):
                 "peak_mma": peak_mma, "peak_dp4a": peak_dp4a, "peak_mixed": peak_mixed or None,
                 "algorithmic": f"{mma_ops_per_launch} int8 ops per launch (2 x M x S x units)",
                 "ms_per_launch": inner_avg}
+    elif wl.name == "cconv_ntt":
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ne.ne_probe_imad_peak(64)
+        e0.record(stream)
+        ops = ne.ne_probe_imad_peak(16384)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        peak_imad = ops / (e0.elapsed_time(e1) * 1e-3) / 1e12
+        achieved = imad_per_launch / (inner_avg * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": peak_imad,
+                "unit": "T int32 multiply-adds/s", "frac": achieved / peak_imad,
+                "traffic": traffic_for(dominant, dom_src),
+                "peak_source": "measured in this run: register-resident 32-bit IMAD probe (ne_probe_imad_peak)",
+                "algorithmic": f"{imad_per_launch} 32-bit multiplies per launch (Shoup twiddle products: 3, "
+                               "Montgomery pointwise products: 4; see ntt_imad_per_group)",
+                "ms_per_launch": inner_avg}
     else:
         roof = {"bound": "alu", "kernel": dominant, "achieved": wl.useful_ops / (inner_avg * 1e-3) / 1e12,
                 "peak": None, "unit": "TOP/s", "frac": None, "traffic": None, "ms_per_launch": inner_avg}
@@ -431,12 +509,12 @@ def run_ours(args, rank, world, local_rank):
 
     # --- end to end through host buffers -----------------------------------------------------
     c_host = torch.from_numpy(wl.c).pin_memory()
-    op_host = torch.from_numpy(wl.g if wl.name == "cconv" else wl.Gm).pin_memory()
+    op_host = torch.from_numpy(wl.g if wl.name in ("cconv", "cconv_ntt") else wl.Gm).pin_memory()
     out_host = torch.empty(out.shape, dtype=torch.int64).pin_memory()
     flags_host = torch.empty(flags.shape, dtype=torch.int32).pin_memory()
     nflag_host = torch.empty(1, dtype=torch.int64).pin_memory()
     c_dev_view = c.view(wl.c.shape)
-    op_dev = g if wl.name == "cconv" else Gm
+    op_dev = g if wl.name in ("cconv", "cconv_ntt") else Gm
 
     def e2e_step(ev):
         c_dev_view.copy_(c_host, non_blocking=True)
@@ -612,6 +690,16 @@ def cconv_extras(torch, ne, wl, dev, flush, step, p, dg, planes, g, out, ms_step
 
     t_x, _ = timed_steps(torch, xcorr, K, W, flush)
     del outk
+    # the number-theoretic-transform convolution: entangled (one fused launch from the
+    # raw streams to the extracted outputs) against the plain operation (one digit)
+    def ntt_ent(ev):
+        ne.ne_cconv_ntt(p, dg, c, g, out2, fl, None, FX, 0)
+
+    def ntt_plain(ev):
+        ne.ne_cconv_ntt(p, dg1, c, g, out2, None, None, ne.NE_FUSE_NONE, 0, plain=True)
+
+    t_ne, _ = timed_steps(torch, ntt_ent, K, W, flush)
+    t_np, _ = timed_steps(torch, ntt_plain, K, W, flush)
     torch.cuda.synchronize()
     ms = lambda t, k: t / k  # noqa: E731
     res["overhead_pct"] = {
@@ -620,11 +708,13 @@ def cconv_extras(torch, ne, wl, dev, flush, step, p, dg, planes, g, out, ms_step
         "int64_family": 100 * (ms(t_ei, Ki) / ms(t_pi, Ki) - 1),
         "abft_tensor_vs_plain_same_kernel": 100 * (ms(t_abft, K) / ms(t_same, K) - 1),
         "abft_int64_vs_plain_int64": 100 * (ms(t_ai, Ki) / ms(t_pi, Ki) - 1),
+        "ntt_vs_plain_ntt": 100 * (ms(t_ne, K) / ms(t_np, K) - 1),
     }
     res["ms"] = {"entangled_step": ent_ms, "plain_same_digits": ms(t_same, K), "plain_one_digit": ms(t_min, K),
                  "plain_int64": ms(t_pi, Ki), "entangled_int64": ms(t_ei, Ki), "abft_tensor": ms(t_abft, K),
                  "abft_int64": ms(t_ai, Ki), "fail_stop_recovery_step": ms(t_rec, K),
-                 "entangle_digits_pass": ms(t_e, K), "cross_correlation_step": ms(t_x, K)}
+                 "entangle_digits_pass": ms(t_e, K), "cross_correlation_step": ms(t_x, K),
+                 "ntt_entangled_step": ms(t_ne, K), "ntt_plain_step": ms(t_np, K)}
     res["entangle_pass_hbm"] = {"bytes": ent_bytes, "GB/s": ent_bytes / (ms(t_e, K) * 1e-3) / 1e9,
                                 "peak_GB/s": hbm_peak, "frac": (ent_bytes / (ms(t_e, K) * 1e-3) / 1e9 / hbm_peak)
                                 if hbm_peak else None}

@@ -172,6 +172,22 @@ ne_status ne_cconv_digits(ne_params p, ne_digits dg, const int8_t* planes, const
                           int64_t* out, uint32_t* flags, uint64_t* nflag,
                           int64_t batch, int64_t N, int32_t fuse, int32_t r, cudaStream_t s);
 
+/* The same batched convolution through an exact number-theoretic transform
+ * (the integer-exact form of the frequency-domain convolution of Sec. V),
+ * fused from the raw streams to the extracted outputs: every word of Eq. 16
+ * (c_m + 2^l c_{m-1}; plain = 1: c_m itself, no entanglement) is split into
+ * the balanced base-256 digits of dg, each digit plane is convolved with g
+ * modulo the prime 119 * 2^23 + 1 (exact: a digit plane's convolution is at
+ * most N * 2^14 in magnitude), the digits are recombined in int64 and the
+ * epilogue of ne_cconv_digits follows (fuse, r, flags, nflag as there; plain
+ * requires NE_FUSE_NONE).  A word with a non-zero digit outside dg sets
+ * *status = NE_ERANGE (status: device int32, nullable).
+ * c: int32 [batch][M][N]; g: int8 [batch][N]; out: int64 [batch][M][N].
+ * N = 1024; M * dg.S <= 15. */
+ne_status ne_cconv_ntt(ne_params p, ne_digits dg, const int32_t* c, const int8_t* g, int64_t* out,
+                       uint32_t* flags, uint64_t* nflag, int64_t batch, int64_t N, int32_t fuse,
+                       int32_t r, int32_t plain, int32_t* status, cudaStream_t s);
+
 /* ------------------------------------------------------------------------ */
 /* Extraction, check and recovery (Eq. 17-20, Eq. 24, Prop. 3)               */
 /* ------------------------------------------------------------------------ */
@@ -421,6 +437,10 @@ ne_status ne_probe_mma_peak(int32_t iters, int64_t* ops, cudaStream_t s);
 /* The same for dp4a on the CUDA cores (four int8 products added into an
  * int32 per instruction), the second int8 pipe the convolution uses. */
 ne_status ne_probe_dp4a_peak(int32_t iters, int64_t* ops, cudaStream_t s);
+
+/* The 32-bit integer multiply-add (IMAD) rate of the CUDA cores: *ops
+ * receives the multiply-adds issued. */
+ne_status ne_probe_imad_peak(int32_t iters, int64_t* ops, cudaStream_t s);
 
 /* Both int8 pipes together: blocks_per_sm blocks per SM, each with mma_warps
  * warps running iters_mma rounds of the tensor loop above and dp4a_warps warps

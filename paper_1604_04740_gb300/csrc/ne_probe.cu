@@ -119,3 +119,33 @@ extern "C" ne_status ne_probe_mixed_peak(int32_t iters_mma, int32_t iters_dp4a, 
                               (int64_t)dp4a_warps * 32 * iters_dp4a * 8 * 8);
     return check_launch("ne_probe_mixed_peak");
 }
+
+// The 32-bit integer multiply-add rate of the CUDA cores (IMAD, the unit the
+// modular arithmetic of the number-theoretic transform is bound by):
+// eight independent multiply-add chains per thread on register operands.
+namespace {
+
+__global__ void __launch_bounds__(256) k_probe_imad(int iters) {
+    uint32_t d[8];
+    const uint32_t b = threadIdx.x * 2654435761u + 1u, c = threadIdx.x ^ 0x9e3779b9u;
+#pragma unroll
+    for (int i = 0; i < 8; i++) d[i] = i * 0x01000193u + threadIdx.x;
+    for (int it = 0; it < iters; it++) {
+#pragma unroll
+        for (int i = 0; i < 8; i++) d[i] = d[i] * b + c;
+    }
+    uint32_t s = 0;
+#pragma unroll
+    for (int i = 0; i < 8; i++) s ^= d[i];
+    if (s == 0x7fffffffu) g_probe_sink = (int)s;
+}
+
+}  // namespace
+
+extern "C" ne_status ne_probe_imad_peak(int32_t iters, int64_t* ops, cudaStream_t s) {
+    if (iters < 1 || !ops) return fail(NE_EINVAL, "ne_probe_imad_peak: bad arguments");
+    const int blocks = sm_count() * 8, threads = 256;
+    k_probe_imad<<<blocks, threads, 0, s>>>(iters);
+    *ops = (int64_t)blocks * threads * (int64_t)iters * 8;   // 32-bit multiply-adds
+    return check_launch("ne_probe_imad_peak");
+}

@@ -101,11 +101,13 @@ def _load():
         "ne_split_digits": [ne_digits, P, P, i64, i32, i64, P, P],
         "ne_probe_mma_peak": [i32, ctypes.POINTER(i64), P],
         "ne_probe_dp4a_peak": [i32, ctypes.POINTER(i64), P],
+        "ne_probe_imad_peak": [i32, ctypes.POINTER(i64), P],
         "ne_probe_mixed_peak": [i32, i32, i32, i32, i32, ctypes.POINTER(i64), P],
         "ne_batch_plan": [ctypes.POINTER(ne_job), i32, ne_batch_config, P, i64, ctypes.POINTER(ne_batch_info), P],
         "ne_batch_run": [ne_batch_info, P, P, P, P, P, P, P, P, P, P, P],
         "ne_batch_run_static": [ctypes.POINTER(ne_job), i32, ne_batch_config, P, P, P, P, P, P, P, P, P, P],
         "ne_copy_regions_h2d": [P, P, P, P, P, i64, P],
+        "ne_cconv_ntt": [ne_params, ne_digits, P, P, P, P, P, i64, i64, i32, i32, i32, P, P],
         "ne_elementwise": [ne_params, i32, P, P, i64, P, P, P, i64, i64, i32, i32, P],
         "ne_entangle_kernel_self": [i32, P, P, i64, P],
         "ne_outer": [ne_params, P, P, i64, P, P, P, i64, i64, i64, i32, i32, P],
@@ -235,6 +237,13 @@ def ne_probe_mixed_peak(iters_mma: int, iters_dp4a: int, mma_warps: int, dp4a_wa
     return ops.value
 
 
+def ne_probe_imad_peak(iters: int) -> int:
+    """32-bit IMAD throughput probe; returns the multiply-adds issued."""
+    ops = ctypes.c_int64(0)
+    _call("ne_probe_imad_peak", iters, ctypes.byref(ops), _stream())
+    return ops.value
+
+
 def ne_probe_mma_peak(iters: int) -> int:
     """Launch the int8 tensor-path throughput probe on the current stream;
     returns the number of int8 operations it issues (time it with events)."""
@@ -302,6 +311,23 @@ def ne_cconv_digits(p: ne_params, dg: ne_digits, planes: torch.Tensor, g: torch.
     _call("ne_cconv_digits", p, dg, _ptr(planes, torch.int8, "planes"), _ptr(g, torch.int8, "g"),
           _ptr(out, torch.int64, "out"), _ptr(flags, torch.int32, "flags", True),
           _ptr(nflag, torch.int64, "nflag", True), batch, N, fuse, r, _stream())
+    return out
+
+
+def ne_cconv_ntt(p: ne_params, dg: ne_digits, c: torch.Tensor, g: torch.Tensor, out: torch.Tensor | None = None,
+                 flags: torch.Tensor | None = None, nflag: torch.Tensor | None = None,
+                 fuse: int = NE_FUSE_EXTRACT_CHECK, r: int = 0, plain: bool = False,
+                 status: torch.Tensor | None = None) -> torch.Tensor:
+    """c int32 [batch, M, N] (raw streams); g int8 [batch, N] -> int64 [batch, M, N]."""
+    batch, M, N = c.shape
+    if M != p.M or tuple(g.shape) != (batch, N):
+        raise ValueError("c / g shapes")
+    if out is None:
+        out = torch.empty((batch, M, N), dtype=torch.int64, device=c.device)
+    _call("ne_cconv_ntt", p, dg, _ptr(c, torch.int32, "c"), _ptr(g, torch.int8, "g"),
+          _ptr(out, torch.int64, "out"), _ptr(flags, torch.int32, "flags", True),
+          _ptr(nflag, torch.int64, "nflag", True), batch, N, fuse, r, 1 if plain else 0,
+          _ptr(status, torch.int32, "status", True), _stream())
     return out
 
 
