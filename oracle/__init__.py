@@ -61,6 +61,10 @@ def _L():
         lib.or_entangle_kernel_self.argtypes = [i32, p, p, i64]
         lib.or_extract.argtypes = [i32, i32, p, i64, i32, p, p]
         lib.or_inner.argtypes = [p, p, p, i64, i64, i64]
+        lib.or_rc_encode.argtypes = [p, p, i64, i64, i64, p, p]
+        lib.or_gemm64.argtypes = [p, p, p, i64, i64, i64]
+        lib.or_rc_check.argtypes = [p, i64, i64, p, p]
+        lib.or_rc_correct.argtypes = [p, i64, i64, ctypes.POINTER(i32)]
         lib.or_outer.argtypes = [p, p, p, i64, i64, i64, i64]
         lib.or_permute.argtypes = [p, p, p, i64, i64, i64]
         lib.or_cxcorr.argtypes = [p, p, p, i64, i64, i64]
@@ -68,7 +72,7 @@ def _L():
         lib.or_abft_check.argtypes = [i32, p, i64, p]
         lib.or_abft_recover.argtypes = [i32, p, i64, i32]
         for f in ("or_entangle", "or_gemm", "or_cconv", "or_elementwise", "or_entangle_kernel_self",
-                  "or_extract", "or_inner", "or_outer", "or_permute", "or_cxcorr", "or_abft_encode", "or_abft_check", "or_abft_recover", "or_choose_l"):
+                  "or_extract", "or_rc_encode", "or_gemm64", "or_rc_check", "or_rc_correct", "or_inner", "or_outer", "or_permute", "or_cxcorr", "or_abft_encode", "or_abft_check", "or_abft_recover", "or_choose_l"):
             getattr(lib, f).restype = i32
         _lib = lib
     return _lib
@@ -262,6 +266,56 @@ def abft_recover(d, j: int):
     M = d.shape[0] - 1
     _chk(_L().or_abft_recover(M, d.ctypes.data, d.shape[1], j), "abft_recover")
     return d
+
+
+# ---- row/column checksum ABFT of a product (ABFT RC-check, Sec. V) ----------
+
+def rc_encode(A, B):
+    """Column-checksum matrix of A [m, k] and row-checksum matrix of B (int8 [k, n]):
+    returns (ac [m+1, k], br [k, n+1]), int64."""
+    A, pa = _arr(A, np.int64)
+    B, pb = _arr(B, np.int8)
+    m, k = A.shape
+    n = B.shape[1]
+    ac = np.empty((m + 1, k), np.int64)
+    br = np.empty((k, n + 1), np.int64)
+    _chk(_L().or_rc_encode(pa, pb, m, k, n, ac.ctypes.data, br.ctypes.data), "rc_encode")
+    return ac, br
+
+
+def gemm64(X, Y):
+    """Z = X Y exactly for int64 matrices."""
+    X, px = _arr(X, np.int64)
+    Y, py = _arr(Y, np.int64)
+    m, k = X.shape
+    n = Y.shape[1]
+    Z = np.empty((m, n), np.int64)
+    _chk(_L().or_gemm64(px, py, Z.ctypes.data, m, k, n), "gemm64")
+    return Z
+
+
+def rc_full(A, B):
+    """The full-checksum matrix of C = A B, [m+1, n+1]."""
+    ac, br = rc_encode(A, B)
+    return gemm64(ac, br)
+
+
+def rc_check(Cf):
+    """(rowbad [m+1], colbad [n+1]) of a full-checksum matrix."""
+    Cf, pc = _arr(Cf, np.int64)
+    m, n = Cf.shape[0] - 1, Cf.shape[1] - 1
+    rb = np.zeros(m + 1, np.uint8)
+    cb = np.zeros(n + 1, np.uint8)
+    _chk(_L().or_rc_check(pc, m, n, rb.ctypes.data, cb.ctypes.data), "rc_check")
+    return rb, cb
+
+
+def rc_correct(Cf):
+    """Single-error correction; returns (corrected copy, whether an entry was replaced)."""
+    Cf = np.array(Cf, dtype=np.int64, order="C", copy=True)
+    done = ctypes.c_int(0)
+    _chk(_L().or_rc_correct(Cf.ctypes.data, Cf.shape[0] - 1, Cf.shape[1] - 1, ctypes.byref(done)), "rc_correct")
+    return Cf, bool(done.value)
 
 
 # ---- the pipelines composed from the steps ---------------------------------

@@ -491,3 +491,119 @@ int or_abft_recover(int M, int64_t *d, int64_t n, int j) {
     }
     return err;
 }
+
+/* ---- row/column checksum ABFT of a product (the "ABFT RC-check" comparator
+ *      of Sec. V, after Huang and Abraham) -------------------------------- */
+
+/*
+ * Encoding: the column-checksum matrix of A (m x k) is A with the row e^T A
+ * appended, ac [m+1][k]; the row-checksum matrix of B (k x n) is B with the
+ * column B e appended, br [k][n+1].  Their product is the full-checksum
+ * matrix of C = A B: C bordered by the row e^T C and the column C e.
+ */
+int or_rc_encode(const int64_t *A, const int8_t *B, int64_t m, int64_t k, int64_t n, int64_t *ac, int64_t *br) {
+    if (m < 0 || k < 0 || n < 0) return OR_EINVAL;
+    int err = OR_OK;
+    for (int64_t t = 0; t < k; t++) {
+        i128 s = 0;
+        for (int64_t i = 0; i < m; i++) {
+            ac[i * k + t] = A[i * k + t];
+            s = checked_add(s, (i128)A[i * k + t], &err);
+        }
+        if (!fits_i64(s)) err = OR_EOVERFLOW;
+        ac[m * k + t] = low64(s);
+    }
+    for (int64_t t = 0; t < k; t++) {
+        i128 s = 0;
+        for (int64_t j = 0; j < n; j++) {
+            br[t * (n + 1) + j] = B[t * n + j];
+            s += (i128)B[t * n + j];
+        }
+        br[t * (n + 1) + n] = low64(s);
+    }
+    return err;
+}
+
+/* The product of two int64 matrices, Z = X Y (X [m][k], Y [k][n]); every
+ * partial sum must fit int64. */
+int or_gemm64(const int64_t *X, const int64_t *Y, int64_t *Z, int64_t m, int64_t k, int64_t n) {
+    if (m < 0 || k < 0 || n < 0) return OR_EINVAL;
+    int err = OR_OK;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int64_t i = 0; i < m; i++) {
+        int lerr = OR_OK;
+        for (int64_t j = 0; j < n; j++) {
+            i128 acc = 0;
+            for (int64_t t = 0; t < k; t++) {
+                acc = checked_add(acc, checked_mul((i128)X[i * k + t], (i128)Y[t * n + j], &lerr), &lerr);
+                if (!fits_i64(acc)) lerr = OR_EOVERFLOW;
+            }
+            Z[i * n + j] = low64(acc);
+        }
+        if (lerr) set_err(&err, lerr);
+    }
+    return err;
+}
+
+/*
+ * The check of a full-checksum matrix Cf [m+1][n+1]: row i (i <= m) is
+ * inconsistent when the sum of its first n entries differs from Cf[i][n];
+ * column j (j <= n) when the sum of its first m entries differs from Cf[m][j].
+ * rowbad [m+1], colbad [n+1].
+ */
+int or_rc_check(const int64_t *Cf, int64_t m, int64_t n, uint8_t *rowbad, uint8_t *colbad) {
+    if (m < 0 || n < 0) return OR_EINVAL;
+    const int64_t w = n + 1;
+    for (int64_t i = 0; i <= m; i++) {
+        i128 s = 0;
+        for (int64_t j = 0; j < n; j++) s += (i128)Cf[i * w + j];
+        rowbad[i] = (uint8_t)(s != (i128)Cf[i * w + n]);
+    }
+    for (int64_t j = 0; j <= n; j++) {
+        i128 s = 0;
+        for (int64_t i = 0; i < m; i++) s += (i128)Cf[i * w + j];
+        colbad[j] = (uint8_t)(s != (i128)Cf[m * w + j]);
+    }
+    return OR_OK;
+}
+
+/*
+ * Single-error correction: when exactly one row i and one column j are
+ * inconsistent, the entry Cf[i][j] is the faulty one.  For j < n it is
+ * replaced by Cf[i][n] minus the other entries of row i; for j = n (a row
+ * checksum, or the corner when i = m) by the sum of the first n entries of
+ * row i.  *corrected = 1 when an entry was replaced.
+ */
+int or_rc_correct(int64_t *Cf, int64_t m, int64_t n, int *corrected) {
+    if (m < 0 || n < 0) return OR_EINVAL;
+    const int64_t w = n + 1;
+    int64_t bi = -1, bj = -1, nbi = 0, nbj = 0;
+    for (int64_t i = 0; i <= m; i++) {
+        i128 s = 0;
+        for (int64_t j = 0; j < n; j++) s += (i128)Cf[i * w + j];
+        if (s != (i128)Cf[i * w + n]) { bi = i; nbi++; }
+    }
+    for (int64_t j = 0; j <= n; j++) {
+        i128 s = 0;
+        for (int64_t i = 0; i < m; i++) s += (i128)Cf[i * w + j];
+        if (s != (i128)Cf[m * w + j]) { bj = j; nbj++; }
+    }
+    *corrected = 0;
+    if (nbi != 1 || nbj != 1) return OR_OK;
+    int err = OR_OK;
+    i128 v;
+    if (bj < n) {
+        v = (i128)Cf[bi * w + n];
+        for (int64_t j = 0; j < n; j++)
+            if (j != bj) v = checked_sub(v, (i128)Cf[bi * w + j], &err);
+    } else {
+        v = 0;
+        for (int64_t j = 0; j < n; j++) v = checked_add(v, (i128)Cf[bi * w + j], &err);
+    }
+    if (!fits_i64(v)) err = OR_EOVERFLOW;
+    Cf[bi * w + bj] = low64(v);
+    *corrected = 1;
+    return err;
+}

@@ -223,3 +223,60 @@ def test_lsb_pipeline_equals_direct_flags_and_recovers(op, M, l):
         bad[1, (r + 2) % M, pos] ^= np.int64(1) << np.int64(5 + r)
         _, f2 = oracle.extract(bad, l, r)
         assert f2[1, pos] and f2.sum() == 1
+
+
+# ---- row/column checksum ABFT of a product (ABFT RC-check) -----------------
+
+def test_gemm64_matches_numpy():
+    rng = np.random.default_rng(12)
+    X = rng.integers(-(2 ** 20), 2 ** 20, (9, 13), dtype=np.int64)
+    Y = rng.integers(-(2 ** 20), 2 ** 20, (13, 7), dtype=np.int64)
+    assert (oracle.gemm64(X, Y) == X @ Y).all()
+    with pytest.raises(oracle.OracleError):
+        oracle.gemm64(np.array([[2 ** 40]], np.int64), np.array([[2 ** 30]], np.int64))
+
+
+def test_rc_full_checksum_matrix_borders_the_product():
+    rng = np.random.default_rng(13)
+    m, k, n = 17, 23, 11
+    A = rng.integers(-128, 128, (m, k), dtype=np.int64)
+    B = rng.integers(-128, 128, (k, n)).astype(np.int8)
+    ac, br = oracle.rc_encode(A, B)
+    assert (ac[:m] == A).all() and (ac[m] == A.sum(0)).all()
+    assert (br[:, :n] == B).all() and (br[:, n] == B.astype(np.int64).sum(1)).all()
+    Cf = oracle.rc_full(A, B)
+    C = A @ B.astype(np.int64)
+    assert (Cf[:m, :n] == C).all()
+    assert (Cf[:m, n] == C.sum(1)).all() and (Cf[m, :n] == C.sum(0)).all() and Cf[m, n] == C.sum()
+    rb, cb = oracle.rc_check(Cf)
+    assert not rb.any() and not cb.any()
+
+
+def test_rc_single_error_is_located_and_corrected_anywhere():
+    rng = np.random.default_rng(14)
+    m, k, n = 6, 9, 5
+    A = rng.integers(-128, 128, (m, k), dtype=np.int64)
+    B = rng.integers(-128, 128, (k, n)).astype(np.int8)
+    Cf = oracle.rc_full(A, B)
+    for i in range(m + 1):
+        for j in range(n + 1):
+            bad = Cf.copy()
+            bad[i, j] ^= np.int64(1) << np.int64((3 * i + j) % 60)
+            rb, cb = oracle.rc_check(bad)
+            assert np.flatnonzero(rb).tolist() == [i] and np.flatnonzero(cb).tolist() == [j]
+            fixed, done = oracle.rc_correct(bad)
+            assert done and (fixed == Cf).all()
+
+
+def test_rc_two_errors_are_detected_not_corrected():
+    rng = np.random.default_rng(15)
+    A = rng.integers(-128, 128, (8, 8), dtype=np.int64)
+    B = rng.integers(-128, 128, (8, 8)).astype(np.int8)
+    Cf = oracle.rc_full(A, B)
+    bad = Cf.copy()
+    bad[1, 2] += 5
+    bad[4, 6] -= 3
+    rb, cb = oracle.rc_check(bad)
+    assert np.flatnonzero(rb).tolist() == [1, 4] and np.flatnonzero(cb).tolist() == [2, 6]
+    fixed, done = oracle.rc_correct(bad)
+    assert not done and (fixed == bad).all()
