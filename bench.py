@@ -56,7 +56,7 @@ class L2Flush:
 
     def __init__(self, torch, dev):
         self.w = torch.zeros(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
-        self.r = torch.ones(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+        self.r = torch.ones(L2_FLUSH_BYTES // 8, dtype=torch.int64, device=dev)
         self.sink = torch.zeros((), dtype=torch.int64, device=dev)
 
     def __call__(self):
@@ -746,9 +746,53 @@ def gemm_extras(torch, ne, wl, dev, flush, p, dg, planes, Gm, out, ms_step):
         ne.ne_gemm_digits(p, dg1, raw1, Gm, out2, None, None, ne.NE_FUSE_NONE, 0)
 
     t_min, _ = timed_steps(torch, plain_min, K, W, flush)
+    # checksum ABFT (Eq. 3-6): the checksum stream as an (M+1)-th stream, two digits
+    c32 = torch.from_numpy(wl.c).to(dev).reshape(M, n * n)
+    x5 = torch.empty((M + 1, n * n), dtype=torch.int64, device=dev)
+    dgA = ne.digits((0, 8))
+    aplanes = torch.empty((M + 1, 2, n, n), dtype=torch.int8, device=dev)
+    aout = torch.empty((M + 1, n, n), dtype=torch.int64, device=dev)
+    pA = ne.params(M + 1, 1)
+    fla = torch.empty(n * n // 32, dtype=torch.int32, device=dev)
+    nfa = torch.zeros(1, dtype=torch.int64, device=dev)
+
+    def abft_stream(ev):
+        ne.ne_abft_encode(M, c32.view(1, M, n * n), x5.view(1, M + 1, n * n))
+        ne.ne_split_digits(dgA, x5, M + 1, aplanes.view(M + 1, 2, n * n))
+        ne.ne_gemm_digits(pA, dgA, aplanes, Gm, aout, None, None, ne.NE_FUSE_NONE, 0)
+        ne.ne_abft_check(M, aout.view(1, M + 1, n * n), fla, nfa)
+
+    t_abft, _ = timed_steps(torch, abft_stream, K, W, flush)
+    # row/column checksum ABFT (ABFT RC-check) around the plain one-digit product of every stream
+    A3 = c32.view(M, n, n)
+    ac = torch.empty((M, n), dtype=torch.int64, device=dev)
+    br = torch.empty(n, dtype=torch.int64, device=dev)
+    work = torch.empty((M, 2 * (n + n + 1)), dtype=torch.int64, device=dev)
+    rw, cw = ne.rc_flag_words(M, n, n)
+    rb = torch.empty(rw, dtype=torch.int32, device=dev)
+    cb = torch.empty(cw, dtype=torch.int32, device=dev)
+    nbad = torch.zeros(2, dtype=torch.int64, device=dev)
+
+    def abft_rc(ev):
+        plain_min(ev)
+        ne.ne_abft_rc_encode(A3, Gm, ac, br)
+        ne.ne_abft_rc_check(out2, A3, Gm, ac, br, work, rb, cb, nbad)
+
+    def rc_only(ev):
+        ne.ne_abft_rc_encode(A3, Gm, ac, br)
+        ne.ne_abft_rc_check(out2, A3, Gm, ac, br, work, rb, cb, nbad)
+
+    t_rc, _ = timed_steps(torch, abft_rc, K, W, flush)
+    t_rco, _ = timed_steps(torch, rc_only, K, W, flush)
+    torch.cuda.synchronize()
+    assert int(nbad.sum().item()) == 0 and int(nfa.item()) == 0, "clean products flagged by an ABFT check"
     return {"overhead_pct": {"vs_plain_same_kernel_same_digits": 100 * (ms_step / (t_same / K) - 1),
-                             "vs_plain_fewest_digits": 100 * (ms_step / (t_min / K) - 1)},
-            "ms": {"entangled_step": ms_step, "plain_same_digits": t_same / K, "plain_one_digit": t_min / K}}
+                             "vs_plain_fewest_digits": 100 * (ms_step / (t_min / K) - 1),
+                             "abft_checksum_stream_vs_plain_fewest_digits": 100 * (t_abft / t_min - 1),
+                             "abft_rc_check_vs_plain_fewest_digits": 100 * (t_rc / t_min - 1)},
+            "ms": {"entangled_step": ms_step, "plain_same_digits": t_same / K, "plain_one_digit": t_min / K,
+                   "abft_checksum_stream": t_abft / K, "abft_rc_check_step": t_rc / K,
+                   "abft_rc_encode_and_check_alone": t_rco / K}}
 
 
 def run_batch(args, rank, world, local_rank):

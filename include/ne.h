@@ -229,6 +229,45 @@ ne_status ne_inject(int64_t* delta, int32_t P, int64_t batch, int64_t n,
                     const int64_t* bit, int64_t count, int32_t* status, cudaStream_t s);
 
 /* ------------------------------------------------------------------------ */
+/* Row/column checksum ABFT of a product (the "ABFT RC-check" of Sec. V)     */
+/* ------------------------------------------------------------------------ */
+/*
+ * The comparator the paper measures against for GEMM (after Huang and
+ * Abraham): C_b = A_b B is bordered by the checksum row e^T C_b and the
+ * checksum column C_b e, computed from the checksum row of A_b and the
+ * checksum column of B; a row or column whose sum disagrees with its checksum
+ * is flagged, and a single faulty entry is located and corrected.
+ * A: int32 [batch][m][k]; B: int8 [k][n] (one operand for every product);
+ * C: int64 [batch][m][n].  batch <= 65535.  All device pointers.
+ */
+
+/* Encoding: ac[b][t] = sum_i A_b[i][t] (int64 [batch][k]) and
+ * br[t] = sum_j B[t][j] (int64 [k]). */
+ne_status ne_abft_rc_encode(const int32_t* A, const int8_t* B, int64_t* ac, int64_t* br,
+                            int64_t batch, int64_t m, int64_t k, int64_t n, cudaStream_t s);
+
+/* Check.  work: int64 [batch][2 (m + n + 1)] (caller-owned scratch, written):
+ * per product the border [C e (m) | e^T C (n) | e^T C e] computed as
+ * A_b (B e), (e^T A_b) B and (e^T A_b)(B e), followed by the row and column
+ * sums of C_b [m | n] and one word of border-consistency bits.  row_bad: uint32 [batch][ceil((m+1)/32)],
+ * bit i < m: row i of C_b disagrees with its checksum, bit m: the checksum
+ * row disagrees with the corner; col_bad: uint32 [batch][ceil((n+1)/32)],
+ * likewise for the columns.  nbad (nullable): uint64 [2], the numbers of
+ * flagged rows and columns over all products. */
+ne_status ne_abft_rc_check(const int64_t* C, const int32_t* A, const int8_t* B, const int64_t* ac,
+                           const int64_t* br, int64_t* work, uint32_t* row_bad, uint32_t* col_bad,
+                           uint64_t* nbad, int64_t batch, int64_t m, int64_t k, int64_t n,
+                           cudaStream_t s);
+
+/* Correction after ne_abft_rc_check: in every product with exactly one
+ * flagged row i and one flagged column j, the entry C_b[i][j] (i < m, j < n)
+ * is corrected from its row checksum; a fault located in the border leaves
+ * C_b unchanged.  ncorrected (nullable): uint64, the entries corrected. */
+ne_status ne_abft_rc_correct(int64_t* C, const int64_t* work, const uint32_t* row_bad,
+                             const uint32_t* col_bad, uint64_t* ncorrected, int64_t batch,
+                             int64_t m, int64_t n, cudaStream_t s);
+
+/* ------------------------------------------------------------------------ */
 /* The other LSB operators of Eq. 2 on the entangled streams                 */
 /* ------------------------------------------------------------------------ */
 /*

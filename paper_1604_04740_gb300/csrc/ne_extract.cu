@@ -17,10 +17,13 @@ using namespace ne;
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 
-template <int MT, int VEC, bool WRITE_D, bool CHECK>
+// U segments per warp and iteration: all their loads are issued before any
+// arithmetic, so a warp keeps U * M * 32 * VEC words in flight.
+template <int MT, int VEC, int U, bool WRITE_D, bool CHECK>
 __global__ void __launch_bounds__(kThreads) k_extract(const int64_t* __restrict__ delta, int64_t* __restrict__ dhat,
                                                       int M, int l, int r, int64_t batch, int64_t n,
                                                       uint32_t* __restrict__ flags, unsigned long long* nflag) {
+    constexpr int MR = MT ? MT : 32;
     const int Mv = MT ? MT : M;
     const int lane = threadIdx.x & 31;
     const int64_t seg_len = 32 * VEC;
@@ -30,15 +33,16 @@ __global__ void __launch_bounds__(kThreads) k_extract(const int64_t* __restrict_
         const int64_t* db = delta + b * Mv * n;
         int64_t* ob = dhat + b * Mv * n;
         uint32_t* fb = flags ? flags + b * wpr : nullptr;
-        for (int64_t seg = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5); seg < nseg;
-             seg += (int64_t)gridDim.x * kWarps) {
-            const int64_t i = seg * seg_len + lane * VEC;
-            uint32_t f = 0;
-            if (i < n) {
-                int64_t rot[VEC][MT ? MT : 32];
-                // rotate while loading: register index j is static, address is not
+        for (int64_t sp = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5); sp * U < nseg;
+             sp += (int64_t)gridDim.x * kWarps) {
+            int64_t rot[U][VEC][MR];
+            // rotate while loading: register index j is static, address is not
 #pragma unroll
-                for (int j = 0; j < (MT ? MT : 32); j++) {
+            for (int u = 0; u < U; u++) {
+                const int64_t i = (sp * U + u) * seg_len + lane * VEC;
+                if (i >= n) continue;
+#pragma unroll
+                for (int j = 0; j < MR; j++) {
                     if (!MT && j >= Mv) break;
                     if (j == 0 && !CHECK) continue;
                     int m = r + j;
@@ -46,37 +50,47 @@ __global__ void __launch_bounds__(kThreads) k_extract(const int64_t* __restrict_
                     const int64_t* src = db + (int64_t)m * n + i;
                     if constexpr (VEC == 2) {
                         longlong2 v = __ldcs(reinterpret_cast<const longlong2*>(src));
-                        rot[0][j] = v.x;
-                        rot[1][j] = v.y;
+                        rot[u][0][j] = v.x;
+                        rot[u][1][j] = v.y;
                     } else {
-                        rot[0][j] = __ldcs(src);
-                    }
-                }
-#pragma unroll
-                for (int v = 0; v < VEC; v++) {
-                    int64_t out[MT ? MT : 32];
-                    if (extract_rot<MT>(rot[v], Mv, l, CHECK, out)) f |= 1u << v;
-                    if constexpr (WRITE_D) {
-#pragma unroll
-                        for (int j = 0; j < (MT ? MT : 32); j++) {
-                            if (!MT && j >= Mv) break;
-                            rot[v][j] = out[j];
-                        }
-                    }
-                }
-                if constexpr (WRITE_D) {
-#pragma unroll
-                    for (int j = 0; j < (MT ? MT : 32); j++) {
-                        if (!MT && j >= Mv) break;
-                        int m = r + j;
-                        if (m >= Mv) m -= Mv;
-                        int64_t* dst = ob + (int64_t)m * n + i;
-                        if constexpr (VEC == 2) __stcs(reinterpret_cast<longlong2*>(dst), make_longlong2(rot[0][j], rot[1][j]));
-                        else __stcs(dst, rot[0][j]);
+                        rot[u][0][j] = __ldcs(src);
                     }
                 }
             }
-            if constexpr (CHECK) emit_flags<VEC>(f, lane, seg, wpr, fb, nflag);
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const int64_t seg = sp * U + u;
+                if (seg >= nseg) break;                    // warp-uniform
+                const int64_t i = seg * seg_len + lane * VEC;
+                uint32_t f = 0;
+                if (i < n) {
+#pragma unroll
+                    for (int v = 0; v < VEC; v++) {
+                        int64_t out[MR];
+                        if (extract_rot<MT>(rot[u][v], Mv, l, CHECK, out)) f |= 1u << v;
+                        if constexpr (WRITE_D) {
+#pragma unroll
+                            for (int j = 0; j < MR; j++) {
+                                if (!MT && j >= Mv) break;
+                                rot[u][v][j] = out[j];
+                            }
+                        }
+                    }
+                    if constexpr (WRITE_D) {
+#pragma unroll
+                        for (int j = 0; j < MR; j++) {
+                            if (!MT && j >= Mv) break;
+                            int m = r + j;
+                            if (m >= Mv) m -= Mv;
+                            int64_t* dst = ob + (int64_t)m * n + i;
+                            if constexpr (VEC == 2)
+                                __stcs(reinterpret_cast<longlong2*>(dst), make_longlong2(rot[u][0][j], rot[u][1][j]));
+                            else __stcs(dst, rot[u][0][j]);
+                        }
+                    }
+                }
+                if constexpr (CHECK) emit_flags<VEC>(f, lane, seg, wpr, fb, nflag);
+            }
         }
     }
 }
@@ -95,13 +109,14 @@ dim3 grid_segments(int64_t batch, int64_t nseg) {
 template <int MT, bool WRITE_D, bool CHECK>
 void launch_extract_vec(const int64_t* delta, int64_t* dhat, int M, int l, int r, int64_t batch, int64_t n,
                         uint32_t* flags, unsigned long long* nflag, cudaStream_t s) {
+    constexpr int U = MT ? 2 : 1;      // the generic-M kernel keeps one segment (register budget)
     const bool vec2 = (n % 2 == 0) && aligned(delta, 16) && (!WRITE_D || aligned(dhat, 16));
     if (vec2) {
-        dim3 g = grid_segments(batch, (n + 63) / 64);
-        k_extract<MT, 2, WRITE_D, CHECK><<<g, kThreads, 0, s>>>(delta, dhat, M, l, r, batch, n, flags, nflag);
+        dim3 g = grid_segments(batch, ((n + 63) / 64 + U - 1) / U);
+        k_extract<MT, 2, U, WRITE_D, CHECK><<<g, kThreads, 0, s>>>(delta, dhat, M, l, r, batch, n, flags, nflag);
     } else {
-        dim3 g = grid_segments(batch, (n + 31) / 32);
-        k_extract<MT, 1, WRITE_D, CHECK><<<g, kThreads, 0, s>>>(delta, dhat, M, l, r, batch, n, flags, nflag);
+        dim3 g = grid_segments(batch, ((n + 31) / 32 + U - 1) / U);
+        k_extract<MT, 1, U, WRITE_D, CHECK><<<g, kThreads, 0, s>>>(delta, dhat, M, l, r, batch, n, flags, nflag);
     }
 }
 

@@ -246,6 +246,7 @@ __global__ void __launch_bounds__(kThreads) k_inner(const int64_t* __restrict__ 
 #pragma unroll
         for (int m = 0; m < MR; m++) acc[m] = 0;
         if (vec2) {
+#pragma unroll 4
             for (int64_t i = lo + 2 * threadIdx.x; i < hi; i += 2 * kThreads) {
                 const longlong2 gv = __ldg(reinterpret_cast<const longlong2*>(gb + i));
 #pragma unroll
@@ -257,6 +258,7 @@ __global__ void __launch_bounds__(kThreads) k_inner(const int64_t* __restrict__ 
                 }
             }
         } else {
+#pragma unroll 4
             for (int64_t i = lo + threadIdx.x; i < hi; i += kThreads) {
                 const uint64_t gv = (uint64_t)__ldg(gb + i);
 #pragma unroll

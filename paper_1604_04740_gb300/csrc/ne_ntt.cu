@@ -9,7 +9,7 @@
 // digits of the caller's digit plan (each digit in [-128, 127]; every byte of
 // every word that the plan does not store is checked to be a zero digit).  The
 // circular convolution of one digit plane with the int8 filter is bounded by
-// N * 2^14 in magnitude, far below P / 2 for the prime P = 119 * 2^23 + 1,
+// N * 2^14 = 2^24 in magnitude, below P / 2 for the prime P = 77 * 2^19 + 1,
 // so its residue modulo P determines it exactly.  The words are the
 // shift-and-add of their digits' convolutions in wrapping 64-bit arithmetic,
 // exact whenever the true outputs fit the w = 64 word (the choice of l).
@@ -21,9 +21,11 @@
 // shared-memory table, a padded 32 x 33 shared-memory transpose exchanges the
 // two index digits, and a second 32-point register transform finishes.  The
 // inverse runs the same steps backwards; the 1/N factor is folded into the
-// filter's transform.  Residues stay in [0, 2P) between butterflies (P < 2^30,
-// so sums up to 4P fit 32 bits): twiddle products are Shoup products, the
-// pointwise products Montgomery products.
+// filter's transform.  P < 2^26 leaves room for the five butterfly stages of
+// a 32-point transform to run without any modular reduction: stage t maps
+// residues below 2^(t+1) P to residues below 2^(t+2) P, so a transform takes
+// inputs below 2P to outputs below 64P < 2^32, and only the twiddle products
+// (Shoup) and pointwise products (Montgomery) bring them back below 2P.
 //
 // CTA: persistent over groups.  Warp w < M*S transforms digit s = w % S of
 // stream m = w / S; warp M*S transforms the filter.  After the inverse
@@ -41,15 +43,14 @@ using namespace ne;
 
 namespace ntt {
 
-constexpr uint32_t P = 998244353u;   // 119 * 2^23 + 1, prime
-constexpr uint32_t P2 = 2u * P;
+constexpr uint32_t P = 40370177u;    // 77 * 2^19 + 1, prime
 constexpr uint32_t GEN = 3u;         // a primitive root modulo P
 constexpr int N = 1024;
 constexpr int PAD = 33;              // row stride of the transpose buffers (conflict-free)
 constexpr int BUF = 32 * PAD;        // words per warp buffer
 
-static_assert((uint64_t)4 * P < ((uint64_t)1 << 32), "lazy residues in [0, 4P) must fit 32 bits");
-static_assert((uint64_t)N * 128 * 128 < P / 2, "a digit plane's convolution must be recoverable from its residue");
+static_assert((uint64_t)64 * P < ((uint64_t)1 << 32), "unreduced residues below 64P must fit 32 bits");
+static_assert((uint64_t)N * 128 * 128 <= P / 2, "a digit plane's convolution must be recoverable from its residue");
 static_assert((P - 1) % N == 0, "P must have N-th roots of unity");
 
 __host__ __device__ constexpr uint32_t mulmod(uint32_t a, uint32_t b) { return (uint32_t)((uint64_t)a * b % P); }
@@ -79,6 +80,7 @@ constexpr uint32_t WI = powmod(W, N - 1);          // its inverse
 constexpr uint32_t W32 = powmod(W, 32);            // primitive 32nd root
 constexpr uint32_t W32I = powmod(WI, 32);
 constexpr uint32_t PNEG = neg_inv();
+constexpr uint32_t Q1 = (uint32_t)((((uint64_t)1) << 32) / P);      // Shoup quotient of 1
 constexpr uint32_t R1 = (uint32_t)(((uint64_t)1 << 32) % P);          // 2^32 mod P
 constexpr uint32_t NINV = powmod((uint32_t)N, P - 2);
 // Montgomery product of x with GSCALE = x 2^32 / N mod P, so that a later
@@ -89,10 +91,15 @@ static_assert(powmod(W, N / 2) == P - 1, "W must have order exactly N");
 static_assert(mulmod(W, WI) == 1, "WI must invert W");
 static_assert((uint32_t)(P * (0u - PNEG)) == 1u, "PNEG must be -P^-1 mod 2^32");
 
+// A twiddle and its Shoup quotient, read together (one 8-byte load)
+struct __align__(8) Tw {
+    uint32_t w, q;
+};
+
 // 1024-point twiddles of the four-step form, tw[a * 32 + b] = W^(a b), and
-// their inverses, with Shoup quotients
+// their inverses
 struct Tables {
-    uint32_t tw[N], twq[N], twi[N], twiq[N];
+    Tw tw[N], twi[N];
 };
 
 constexpr Tables make_tables() {
@@ -108,10 +115,10 @@ constexpr Tables make_tables() {
     for (int a = 0; a < 32; a++)
         for (int b = 0; b < 32; b++) {
             const int e = (a * b) % N;
-            t.tw[a * 32 + b] = pows[e];
-            t.twq[a * 32 + b] = shoup(pows[e]);
-            t.twi[a * 32 + b] = powsi[e];
-            t.twiq[a * 32 + b] = shoup(powsi[e]);
+            t.tw[a * 32 + b].w = pows[e];
+            t.tw[a * 32 + b].q = shoup(pows[e]);
+            t.twi[a * 32 + b].w = powsi[e];
+            t.twi[a * 32 + b].q = shoup(powsi[e]);
         }
     return t;
 }
@@ -130,7 +137,6 @@ __device__ __forceinline__ void static_for(F&& f) {
     }
 }
 
-__device__ __forceinline__ uint32_t red2(uint32_t x) { return min(x, x - P2); }   // [0, 4P) -> [0, 2P)
 __device__ __forceinline__ uint32_t red1(uint32_t x) { return min(x, x - P); }    // [0, 2P) -> [0, P)
 
 // x w mod P in [0, 2P) for any 32-bit x and w < P (Shoup)
@@ -146,21 +152,26 @@ __device__ __forceinline__ uint32_t mont(uint32_t a, uint32_t b) {
 }
 
 // In-register 32-point transform, radix 2, decimation in frequency: on entry
-// a[n] (natural order, residues in [0, 2P)); on return a[rev5(k)] holds
-// sum_n w^(n k) a[n] with w = W32 (INV: W32I), residues in [0, 2P).
+// a[n] (natural order, residues below 2P); on return a[rev5(k)] holds
+// sum_n w^(n k) a[n] with w = W32 (INV: W32I) as a residue below 64P.  No
+// reductions: the inputs of stage t are below B = 2^(t+1) P, its sums below
+// 2B, its differences u + B - v in (0, 2B), and the twiddled differences below
+// 2P (Shoup).
 template <bool INV>
 __device__ __forceinline__ void dft32(uint32_t (&a)[32]) {
     static_for<0, 5>([&](auto st) {
-        constexpr int h = 16 >> decltype(st)::value;
+        constexpr int t = decltype(st)::value;
+        constexpr int h = 16 >> t;
+        constexpr uint32_t B = (2u << t) * P;
         static_for<0, 16 / h>([&](auto blk) {
             constexpr int s = decltype(blk)::value * 2 * h;
             static_for<0, h>([&](auto jj) {
                 constexpr int j = decltype(jj)::value;
                 const uint32_t u = a[s + j], v = a[s + j + h];
-                a[s + j] = red2(u + v);
-                const uint32_t d = u + P2 - v;
+                a[s + j] = u + v;
+                const uint32_t d = u + B - v;
                 if constexpr (j == 0) {
-                    a[s + j + h] = red2(d);
+                    a[s + j + h] = d;
                 } else {
                     constexpr uint32_t w = powmod(INV ? W32I : W32, (uint64_t)j * (16 / h));
                     constexpr uint32_t wq = shoup(w);
@@ -171,45 +182,48 @@ __device__ __forceinline__ void dft32(uint32_t (&a)[32]) {
     });
 }
 
-// Forward transform of the warp's 1024 residues.  On entry a[n1] = x[32 n1 +
-// lane]; on return a[rev5(k2)] = X[lane + 32 k2], X[k] = sum_n W^(n k) x[n].
-__device__ __forceinline__ void forward(uint32_t (&a)[32], uint32_t* buf, const uint32_t* tw, const uint32_t* twq,
-                                        int lane) {
-    dft32<false>(a);   // a[rev5(k1)] = sum_n1 W32^(n1 k1) x[32 n1 + lane]
-    static_for<0, 32>([&](auto kk) {
-        constexpr int k1 = decltype(kk)::value;
-        buf[k1 * PAD + lane] = mul_shoup(a[rev5(k1)], tw[k1 * 32 + lane], twq[k1 * 32 + lane]);
-    });
-    __syncwarp();
-    static_for<0, 32>([&](auto nn) {
-        constexpr int n2 = decltype(nn)::value;
-        a[n2] = buf[lane * PAD + n2];
-    });
-    __syncwarp();
-    dft32<false>(a);
+// Forward transform of the warp's 1024 residues (below 2P on entry).  On
+// entry a[n1] = x[32 n1 + lane]; on return a[rev5(k2)] = X[lane + 32 k2] below
+// 64P, X[k] = sum_n W^(n k) x[n].  Both passes share one copy of the code.
+__device__ __forceinline__ void forward(uint32_t (&a)[32], uint32_t* buf, const Tw* tw, int lane) {
+#pragma unroll 1
+    for (int pass = 0; pass < 2; pass++) {
+        dft32<false>(a);   // pass 0: a[rev5(k1)] = sum_n1 W32^(n1 k1) x[32 n1 + lane]
+        if (pass == 1) break;
+        static_for<0, 32>([&](auto kk) {
+            constexpr int k1 = decltype(kk)::value;
+            const Tw t = tw[k1 * 32 + lane];
+            buf[k1 * PAD + lane] = mul_shoup(a[rev5(k1)], t.w, t.q);
+        });
+        __syncwarp();
+        static_for<0, 32>([&](auto nn) {
+            constexpr int n2 = decltype(nn)::value;
+            a[n2] = buf[lane * PAD + n2];
+        });
+        __syncwarp();
+    }
 }
 
-// Inverse transform without the 1/N factor.  On entry a[rev5(k2)] =
-// Y[lane + 32 k2]; on return a[rev5(n1)] = sum_k W^(-n k) Y[k] at n = 32 n1 + lane.
-__device__ __forceinline__ void inverse(uint32_t (&a)[32], uint32_t* buf, const uint32_t* twi, const uint32_t* twiq,
-                                        int lane) {
-    uint32_t b[32];
-    static_for<0, 32>([&](auto kk) {
-        constexpr int k2 = decltype(kk)::value;
-        b[k2] = a[rev5(k2)];
-    });
-    dft32<true>(b);    // b[rev5(n2)] = sum_k2 W32^(-n2 k2) Y[lane + 32 k2]
-    static_for<0, 32>([&](auto nn) {
-        constexpr int n2 = decltype(nn)::value;
-        buf[n2 * PAD + lane] = mul_shoup(b[rev5(n2)], twi[n2 * 32 + lane], twiq[n2 * 32 + lane]);
-    });
-    __syncwarp();
-    static_for<0, 32>([&](auto kk) {
-        constexpr int k1 = decltype(kk)::value;
-        a[k1] = buf[lane * PAD + k1];
-    });
-    __syncwarp();
-    dft32<true>(a);
+// Inverse transform without the 1/N factor.  On entry a[k2] = Y[lane + 32 k2]
+// (natural order, below 2P); on return a[rev5(n1)] = sum_k W^(-n k) Y[k] at
+// n = 32 n1 + lane, below 64P.
+__device__ __forceinline__ void inverse(uint32_t (&a)[32], uint32_t* buf, const Tw* twi, int lane) {
+#pragma unroll 1
+    for (int pass = 0; pass < 2; pass++) {
+        dft32<true>(a);    // pass 0: a[rev5(n2)] = sum_k2 W32^(-n2 k2) Y[lane + 32 k2]
+        if (pass == 1) break;
+        static_for<0, 32>([&](auto nn) {
+            constexpr int n2 = decltype(nn)::value;
+            const Tw t = twi[n2 * 32 + lane];
+            buf[n2 * PAD + lane] = mul_shoup(a[rev5(n2)], t.w, t.q);
+        });
+        __syncwarp();
+        static_for<0, 32>([&](auto kk) {
+            constexpr int k1 = decltype(kk)::value;
+            a[k1] = buf[lane * PAD + k1];
+        });
+        __syncwarp();
+    }
 }
 
 }  // namespace ntt
@@ -224,83 +238,113 @@ struct NttArgs {
     int64_t batch;
     int M, S, MS, l, r, fuse, plain;
     int shift[NE_MAX_DIGITS];
-    uint64_t ns_mask, ns_want;  // bytes of a word that hold no stored digit, and 0x80 in each of them
+    // generic digit split: bytes of a 64-bit word that hold no stored digit, and 0x80 in each
+    uint64_t ns_mask, ns_want;
+    // fast digit split (words of in-range inputs fit 32 bits): the input range
+    // [lo, hi] is checked instead of every word
+    uint32_t off32;
+    int lo, hi;
 };
 
 constexpr size_t ntt_smem_bytes(int MS) {
     return sizeof(uint32_t) * (size_t)(5 * ntt::N + (MS + 1) * ntt::BUF);
 }
 
-template <int MT>
-__global__ void __launch_bounds__(512) k_cconv_ntt(const NttArgs a) {
+// Digit s of the 32 words of this lane (positions 32 n1 + lane) as residues
+// below 2P: FAST forms the words in 32 bits and checks the inputs against the
+// plan's range; otherwise every 64-bit word is checked digit by digit.
+template <bool FAST>
+__device__ __forceinline__ bool load_digits(const NttArgs& a, const int32_t* cm, const int32_t* cp, int sh,
+                                            uint32_t (&v)[32]) {
+    using namespace ntt;
+    if constexpr (FAST) {
+        uint32_t worst = 0;
+        const uint32_t span = (uint32_t)a.hi - (uint32_t)a.lo;
+        const int up = 24 - sh;    // the digit's byte moved to the top, then sign-extended
+#pragma unroll
+        for (int n1 = 0; n1 < 32; n1++) {
+            const int32_t x = __ldg(cm + 32 * n1);
+            worst = max(worst, (uint32_t)x - (uint32_t)a.lo);
+            uint32_t y = (uint32_t)x + a.off32;
+            if (!a.plain) y += (uint32_t)__ldg(cp + 32 * n1) << a.l;
+            const int d = (int32_t)((y ^ 0x80808080u) << up) >> 24;
+            v[n1] = (uint32_t)(d + (int)P);
+        }
+        return worst > span;
+    } else {
+        bool bad = false;
+#pragma unroll
+        for (int n1 = 0; n1 < 32; n1++) {
+            const int32_t x = __ldg(cm + 32 * n1);
+            const int64_t e = a.plain ? (int64_t)x : entangle_word(x, __ldg(cp + 32 * n1), a.l);
+            const uint64_t y = (uint64_t)e + 0x8080808080808080ull;
+            bad |= (y & a.ns_mask) != a.ns_want;
+            const int d = (int)(int8_t)(uint8_t)(((uint32_t)(y >> sh) & 0xffu) ^ 0x80u);
+            v[n1] = (uint32_t)(d + (int)P);
+        }
+        return bad;
+    }
+}
+
+template <int MT, bool FAST>
+__global__ void __launch_bounds__(448, 2) k_cconv_ntt(const NttArgs a) {
     using namespace ntt;
     constexpr int MR = MT ? MT : 16;
     extern __shared__ __align__(16) uint32_t sm[];
-    uint32_t* tw = sm;
-    uint32_t* twq = sm + N;
-    uint32_t* twi = sm + 2 * N;
-    uint32_t* twiq = sm + 3 * N;
+    Tw* tw = reinterpret_cast<Tw*>(sm);
+    Tw* twi = tw + N;
     uint32_t* gm = sm + 4 * N;
     uint32_t* bufs = sm + 5 * N;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int Mv = MT ? MT : a.M;
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
         tw[i] = g_tables.tw[i];
-        twq[i] = g_tables.twq[i];
         twi[i] = g_tables.twi[i];
-        twiq[i] = g_tables.twiq[i];
     }
     __syncthreads();
     uint32_t* buf = bufs + warp * BUF;
+    const bool filter_warp = warp == a.MS;
     const bool digit_warp = warp < a.MS;
     const int m = digit_warp ? warp / a.S : 0;
     const int s = digit_warp ? warp - m * a.S : 0;
     const bool active = digit_warp && !(a.fuse == NE_FUSE_RECOVER && m == a.r);
+    const int mp = m == 0 ? Mv - 1 : m - 1;
     for (int64_t b = blockIdx.x; b < a.batch; b += gridDim.x) {
         uint32_t v[32];
-        if (active) {
-            // Eq. 16 for the 32 positions of this lane, the plan's digit s
-            const int mp = m == 0 ? Mv - 1 : m - 1;
-            const int32_t* cm = a.c + (b * Mv + m) * N + lane;
-            const int32_t* cp = a.c + (b * Mv + mp) * N + lane;
-            const int sh = a.shift[s];
-            bool bad = false;
+        if (active || filter_warp) {
+            if (filter_warp) {
+                const int8_t* gb = a.g + b * N + lane;
 #pragma unroll
-            for (int n1 = 0; n1 < 32; n1++) {
-                const int32_t x = __ldg(cm + 32 * n1);
-                const int64_t e = a.plain ? (int64_t)x : entangle_word(x, __ldg(cp + 32 * n1), a.l);
-                const uint64_t y = (uint64_t)e + 0x8080808080808080ull;
-                bad |= (y & a.ns_mask) != a.ns_want;
-                const int d = (int)(int8_t)(uint8_t)(((uint32_t)(y >> sh) & 0xffu) ^ 0x80u);
-                v[n1] = d < 0 ? (uint32_t)(d + (int)P) : (uint32_t)d;
+                for (int n1 = 0; n1 < 32; n1++) v[n1] = (uint32_t)((int)__ldg(gb + 32 * n1) + (int)P);
+            } else {
+                // Eq. 16 for the 32 positions of this lane, digit s of the plan
+                const bool bad = load_digits<FAST>(a, a.c + (b * Mv + m) * N + lane, a.c + (b * Mv + mp) * N + lane,
+                                                   a.shift[s], v);
+                if (bad && a.status) atomicExch(a.status, (int32_t)NE_ERANGE);
             }
-            if (bad && a.status) atomicExch(a.status, (int32_t)NE_ERANGE);
-            forward(v, buf, tw, twq, lane);
-        } else if (warp == a.MS) {
-            const int8_t* gb = a.g + b * N + lane;
-#pragma unroll
-            for (int n1 = 0; n1 < 32; n1++) {
-                const int d = __ldg(gb + 32 * n1);
-                v[n1] = d < 0 ? (uint32_t)(d + (int)P) : (uint32_t)d;
+            forward(v, buf, tw, lane);
+            if (filter_warp) {
+                // G 2^32 / N mod P, fully reduced, so that the Montgomery products below
+                // multiply the streams' transforms by G / N
+                static_for<0, 32>([&](auto kk) {
+                    constexpr int k2 = decltype(kk)::value;
+                    gm[lane + 32 * k2] = red1(mont(v[rev5(k2)], GSCALE));
+                });
             }
-            forward(v, buf, tw, twq, lane);
-            static_for<0, 32>([&](auto kk) {
-                constexpr int k2 = decltype(kk)::value;
-                gm[lane + 32 * k2] = mont(v[rev5(k2)], GSCALE);
-            });
         }
         __syncthreads();
         if (active) {
+            uint32_t y[32];
             static_for<0, 32>([&](auto kk) {
                 constexpr int k2 = decltype(kk)::value;
-                v[rev5(k2)] = mont(v[rev5(k2)], gm[lane + 32 * k2]);
+                y[k2] = mont(v[rev5(k2)], gm[lane + 32 * k2]);
             });
-            inverse(v, buf, twi, twiq, lane);
-            // the digit plane's convolution, centred into (-P/2, P/2]
+            inverse(y, buf, twi, lane);
+            // the digit plane's convolution: reduce below P, centre into (-P/2, P/2]
             int32_t* res = reinterpret_cast<int32_t*>(buf);
             static_for<0, 32>([&](auto nn) {
                 constexpr int n1 = decltype(nn)::value;
-                const uint32_t x = red1(v[rev5(n1)]);
+                const uint32_t x = red1(mul_shoup(y[rev5(n1)], 1u, Q1));
                 res[32 * n1 + lane] = x > P / 2 ? (int32_t)(x - P) : (int32_t)x;
             });
         }
@@ -351,20 +395,26 @@ __global__ void __launch_bounds__(512) k_cconv_ntt(const NttArgs a) {
     }
 }
 
-template <int MT>
-ne_status launch_ntt(const NttArgs& a, cudaStream_t s) {
+template <int MT, bool FAST>
+ne_status launch_ntt_kernel(const NttArgs& a, cudaStream_t s) {
     const size_t smem = ntt_smem_bytes(a.MS);
     const int threads = 32 * (a.MS + 1);
-    if (cudaFuncSetAttribute(k_cconv_ntt<MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    if (cudaFuncSetAttribute(k_cconv_ntt<MT, FAST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
         return check_launch("ne_cconv_ntt: shared memory");
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cconv_ntt<MT>, threads, smem) != cudaSuccess ||
-        per_sm < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cconv_ntt<MT, FAST>, threads, smem) !=
+            cudaSuccess || per_sm < 1)
         return check_launch("ne_cconv_ntt: occupancy");
     int64_t grid = (int64_t)sm_count() * per_sm;
     if (grid > a.batch) grid = a.batch;
-    k_cconv_ntt<MT><<<(unsigned)grid, threads, smem, s>>>(a);
+    k_cconv_ntt<MT, FAST><<<(unsigned)grid, threads, smem, s>>>(a);
     return check_launch("ne_cconv_ntt");
+}
+
+template <int MT>
+ne_status launch_ntt(const NttArgs& a, bool fast, cudaStream_t s) {
+    return fast ? launch_ntt_kernel<MT, true>(a, s) : launch_ntt_kernel<MT, false>(a, s);
 }
 
 }  // namespace
@@ -410,10 +460,30 @@ extern "C" ne_status ne_cconv_ntt(ne_params p, ne_digits dg, const int32_t* c, c
     }
     a.ns_mask = ~stored;
     a.ns_want = 0x8080808080808080ull & ~stored;
+    // The fast split trusts the digit set only when it is exactly the plan of its
+    // recorded (l, lo, hi) (for the plain operation: one digit at shift 0 and a
+    // range inside [-128, 127]); then in-range inputs form words whose digits are
+    // all in the set and fit 32 bits, and checking the inputs suffices.
+    bool fast = false;
+    if (plain) {
+        fast = dg.S == 1 && dg.shift[0] == 0 && dg.lo <= dg.hi && dg.lo >= -128 && dg.hi <= 127;
+        a.off32 = 0x80808080u;
+    } else if (dg.lo <= dg.hi && dg.l == p.l) {
+        ne_digits ref;
+        FastPlan F;
+        if (ne_plan_digits(dg.l, dg.lo, dg.hi, &ref) == NE_OK && ref.S == dg.S) {
+            fast = true;
+            for (int i = 0; i < dg.S; i++) fast = fast && ref.shift[i] == dg.shift[i];
+        }
+        fast = fast && make_fast_plan(dg, p.l, &F);
+        a.off32 = fast ? F.off : 0u;
+    }
+    a.lo = dg.lo;
+    a.hi = dg.hi;
     switch (p.M) {
-        case 3: return launch_ntt<3>(a, s);
-        case 4: return launch_ntt<4>(a, s);
-        case 5: return launch_ntt<5>(a, s);
-        default: return launch_ntt<0>(a, s);
+        case 3: return launch_ntt<3>(a, fast, s);
+        case 4: return launch_ntt<4>(a, fast, s);
+        case 5: return launch_ntt<5>(a, fast, s);
+        default: return launch_ntt<0>(a, fast, s);
     }
 }

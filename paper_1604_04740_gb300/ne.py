@@ -108,6 +108,9 @@ def _load():
         "ne_batch_run_static": [ctypes.POINTER(ne_job), i32, ne_batch_config, P, P, P, P, P, P, P, P, P, P],
         "ne_copy_regions_h2d": [P, P, P, P, P, i64, P],
         "ne_cconv_ntt": [ne_params, ne_digits, P, P, P, P, P, i64, i64, i32, i32, i32, P, P],
+        "ne_abft_rc_encode": [P, P, P, P, i64, i64, i64, i64, P],
+        "ne_abft_rc_check": [P, P, P, P, P, P, P, P, P, i64, i64, i64, i64, P],
+        "ne_abft_rc_correct": [P, P, P, P, P, i64, i64, i64, P],
         "ne_elementwise": [ne_params, i32, P, P, i64, P, P, P, i64, i64, i32, i32, P],
         "ne_entangle_kernel_self": [i32, P, P, i64, P],
         "ne_outer": [ne_params, P, P, i64, P, P, P, i64, i64, i64, i32, i32, P],
@@ -329,6 +332,57 @@ def ne_cconv_ntt(p: ne_params, dg: ne_digits, c: torch.Tensor, g: torch.Tensor, 
           _ptr(nflag, torch.int64, "nflag", True), batch, N, fuse, r, 1 if plain else 0,
           _ptr(status, torch.int32, "status", True), _stream())
     return out
+
+
+# ---- row/column checksum ABFT of a product (ABFT RC-check) ---------------------------
+
+def ne_abft_rc_encode(A: torch.Tensor, B: torch.Tensor, ac: torch.Tensor | None = None,
+                      br: torch.Tensor | None = None):
+    """A int32 [batch, m, k], B int8 [k, n] -> (ac int64 [batch, k], br int64 [k])."""
+    batch, m, k = A.shape
+    n = B.shape[1]
+    if ac is None:
+        ac = torch.empty((batch, k), dtype=torch.int64, device=A.device)
+    if br is None:
+        br = torch.empty(k, dtype=torch.int64, device=A.device)
+    _call("ne_abft_rc_encode", _ptr(A, torch.int32, "A"), _ptr(B, torch.int8, "B"), _ptr(ac, torch.int64, "ac"),
+          _ptr(br, torch.int64, "br"), batch, m, k, n, _stream())
+    return ac, br
+
+
+def rc_flag_words(batch: int, m: int, n: int):
+    return batch * ((m + 1 + 31) // 32), batch * ((n + 1 + 31) // 32)
+
+
+def ne_abft_rc_check(C: torch.Tensor, A: torch.Tensor, B: torch.Tensor, ac: torch.Tensor, br: torch.Tensor,
+                     work: torch.Tensor | None = None, row_bad: torch.Tensor | None = None,
+                     col_bad: torch.Tensor | None = None, nbad: torch.Tensor | None = None):
+    """C int64 [batch, m, n] -> (work, row_bad, col_bad)."""
+    batch, m, k = A.shape
+    n = B.shape[1]
+    if tuple(C.shape) != (batch, m, n):
+        raise ValueError("C must be [batch, m, n]")
+    if work is None:
+        work = torch.empty((batch, 2 * (m + n + 1)), dtype=torch.int64, device=C.device)
+    rw, cw = rc_flag_words(batch, m, n)
+    if row_bad is None:
+        row_bad = torch.empty(rw, dtype=torch.int32, device=C.device)
+    if col_bad is None:
+        col_bad = torch.empty(cw, dtype=torch.int32, device=C.device)
+    _call("ne_abft_rc_check", _ptr(C, torch.int64, "C"), _ptr(A, torch.int32, "A"), _ptr(B, torch.int8, "B"),
+          _ptr(ac, torch.int64, "ac"), _ptr(br, torch.int64, "br"), _ptr(work, torch.int64, "work"),
+          _ptr(row_bad, torch.int32, "row_bad"), _ptr(col_bad, torch.int32, "col_bad"),
+          _ptr(nbad, torch.int64, "nbad", True), batch, m, k, n, _stream())
+    return work, row_bad, col_bad
+
+
+def ne_abft_rc_correct(C: torch.Tensor, work: torch.Tensor, row_bad: torch.Tensor, col_bad: torch.Tensor,
+                       ncorrected: torch.Tensor | None = None) -> torch.Tensor:
+    batch, m, n = C.shape
+    _call("ne_abft_rc_correct", _ptr(C, torch.int64, "C"), _ptr(work, torch.int64, "work"),
+          _ptr(row_bad, torch.int32, "row_bad"), _ptr(col_bad, torch.int32, "col_bad"),
+          _ptr(ncorrected, torch.int64, "ncorrected", True), batch, m, n, _stream())
+    return C
 
 
 # ---- the other LSB operators of Eq. 2 ----------------------------------------------
