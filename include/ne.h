@@ -172,6 +172,19 @@ ne_status ne_cconv_digits(ne_params p, ne_digits dg, const int8_t* planes, const
                           int64_t* out, uint32_t* flags, uint64_t* nflag,
                           int64_t batch, int64_t N, int32_t fuse, int32_t r, cudaStream_t s);
 
+/* ne_cconv_digits fused with the entanglement in front: the tiles read the
+ * raw streams c (int32 [batch][M][N], 16-byte aligned) and form the words of
+ * Eq. 16 and their digits while loading, so one launch goes from the raw
+ * streams to the extracted outputs.  dg must be the digit plan of its
+ * (l, lo, hi) with words of at most 4 digits (ne_plan_digits); every input
+ * outside [lo, hi] sets *status = NE_ERANGE (device int32, nullable).
+ * plain = 1: the plain operation on the raw streams (dg one digit at shift 0
+ * with a range inside [-128, 127]; NE_FUSE_NONE).  Other arguments as for
+ * ne_cconv_digits. */
+ne_status ne_cconv_entangled(ne_params p, ne_digits dg, const int32_t* c, const int8_t* g, int64_t* out,
+                             uint32_t* flags, uint64_t* nflag, int64_t batch, int64_t N, int32_t fuse,
+                             int32_t r, int32_t plain, int32_t* status, cudaStream_t s);
+
 /* The same batched convolution through an exact number-theoretic transform
  * (the integer-exact form of the frequency-domain convolution of Sec. V),
  * fused from the raw streams to the extracted outputs: every word of Eq. 16

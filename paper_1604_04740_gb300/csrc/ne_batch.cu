@@ -359,6 +359,8 @@ __device__ __noinline__ void run_cconv(const BatchK& k, const DevJob* J, const D
     t.r = J->r;
     t.fuse = J->fuse;
     t.flags_atomic = 1;
+    t.craw = nullptr;     // the batch's digit planes come from its segment entangle
+    t.status = nullptr;
 #pragma unroll
     for (int i = 0; i < NE_MAX_DIGITS; i++) t.shift[i] = J->shift[i];
     const int NB = J->N / cconv::T;

@@ -6,6 +6,7 @@
 #include <cstdlib>
 
 #include "ne_cconv_tile.cuh"
+#include "ne_entangle.cuh"
 
 namespace {
 
@@ -20,9 +21,26 @@ struct CconvArgs {
     int64_t N;
     int M, S, MS, l, r, fuse;
     int shift[NE_MAX_DIGITS];
+    // fused form: raw streams [batch][M][N] instead of planes (see TileArgs)
+    const int32_t* craw;
+    int32_t* status;
+    uint32_t raw_off;
+    int raw_lo, raw_hi, raw_plain;
+    int raw_byte[4];
 };
 
-template <int NTW, int MT>
+__device__ __forceinline__ void raw_fields(const CconvArgs& a, int64_t b, cconv::TileArgs& t) {
+    t.craw = a.craw ? a.craw + b * a.M * a.N : nullptr;
+    t.status = a.status;
+    t.raw_off = a.raw_off;
+    t.raw_lo = a.raw_lo;
+    t.raw_hi = a.raw_hi;
+    t.raw_plain = a.raw_plain;
+#pragma unroll
+    for (int i = 0; i < 4; i++) t.raw_byte[i] = a.raw_byte[i];
+}
+
+template <int NTW, int MT, bool RAW>
 __global__ void __launch_bounds__(cconv::THREADS, (NTW <= 6 ? 4 : (NTW <= 10 ? 3 : 2)))
     k_cconv_digits(CconvArgs a, int64_t b_off) {
     extern __shared__ __align__(128) uint8_t smem[];
@@ -48,14 +66,15 @@ __global__ void __launch_bounds__(cconv::THREADS, (NTW <= 6 ? 4 : (NTW <= 10 ? 3
     t.flags_atomic = 0;
 #pragma unroll
     for (int i = 0; i < NE_MAX_DIGITS; i++) t.shift[i] = a.shift[i];
+    raw_fields(a, b, t);
     const int NB = (int)(N / cconv::T);
     const int p0 = blockIdx.x * cconv::NPB;
-    cconv::tile<NTW, MT>(t, smem, p0, min(cconv::NPB, NB - p0));
+    cconv::tile<NTW, MT, RAW>(t, smem, p0, min(cconv::NPB, NB - p0));
 }
 
 // The hybrid tile (tensor pipe + dp4a pipe) for groups of 9..16 blocks.
-template <int MT, int MSC, int HW, int R>
-__global__ void __launch_bounds__(cconv::hybrid_threads(HW), 2) k_cconv_digits_hybrid(CconvArgs a, int64_t b_off) {
+template <int MT, int MSC, int HW, int R, bool RAW>
+__global__ void __launch_bounds__(cconv::hybrid_threads(HW), RAW ? 3 : 2) k_cconv_digits_hybrid(CconvArgs a, int64_t b_off) {
     extern __shared__ __align__(128) uint8_t smem[];
     const int64_t b = b_off + blockIdx.y;
     const int64_t N = a.N;
@@ -79,10 +98,11 @@ __global__ void __launch_bounds__(cconv::hybrid_threads(HW), 2) k_cconv_digits_h
     t.flags_atomic = 0;
 #pragma unroll
     for (int i = 0; i < NE_MAX_DIGITS; i++) t.shift[i] = a.shift[i];
-    cconv::tile_hybrid<MT, MSC, HW, R>(t, smem);
+    raw_fields(a, b, t);
+    cconv::tile_hybrid<MT, MSC, HW, R, RAW>(t, smem);
 }
 
-template <int MT, int MSC, int HW, int R>
+template <int MT, int MSC, int HW, int R, bool RAW>
 ne_status launch_hybrid(const CconvArgs& a, int64_t batch, cudaStream_t s) {
     if (a.N / cconv::T <= 32 * HW * R / cconv::T) return NE_EINVAL;   // needs a block left for the tensor pipe
     const int smem = cconv::hybrid_smem_bytes(MSC);
@@ -90,14 +110,14 @@ ne_status launch_hybrid(const CconvArgs& a, int64_t batch, cudaStream_t s) {
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-        if (cudaFuncSetAttribute(k_cconv_digits_hybrid<MT, MSC, HW, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if (cudaFuncSetAttribute(k_cconv_digits_hybrid<MT, MSC, HW, R, RAW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  smem) != cudaSuccess)
             return check_launch("ne_cconv_digits: shared-memory attribute");
         attr_set[dev] = true;
     }
     for (int64_t b0 = 0; b0 < batch; b0 += 65535) {
         const int64_t nb = batch - b0 < 65535 ? batch - b0 : 65535;
-        k_cconv_digits_hybrid<MT, MSC, HW, R><<<dim3(1, (unsigned)nb), cconv::hybrid_threads(HW), smem, s>>>(a, b0);
+        k_cconv_digits_hybrid<MT, MSC, HW, R, RAW><<<dim3(1, (unsigned)nb), cconv::hybrid_threads(HW), smem, s>>>(a, b0);
         ne_status st = check_launch("ne_cconv_digits (hybrid)");
         if (st) return st;
     }
@@ -120,27 +140,27 @@ int hybrid_variant(int64_t NB) {
     return v;
 }
 
-template <int MT, int MSC>
+template <int MT, int MSC, bool RAW>
 ne_status launch_hybrid_variant(int var, const CconvArgs& a, int64_t batch, cudaStream_t s) {
     switch (var) {
-        case 22: return launch_hybrid<MT, MSC, 2, 2>(a, batch, s);
-        case 23: return launch_hybrid<MT, MSC, 2, 3>(a, batch, s);
-        case 24: return launch_hybrid<MT, MSC, 2, 4>(a, batch, s);
-        case 25: return launch_hybrid<MT, MSC, 2, 5>(a, batch, s);
-        case 26: return launch_hybrid<MT, MSC, 2, 6>(a, batch, s);
-        case 42: return launch_hybrid<MT, MSC, 4, 2>(a, batch, s);
+        case 22: return launch_hybrid<MT, MSC, 2, 2, RAW>(a, batch, s);
+        case 23: return launch_hybrid<MT, MSC, 2, 3, RAW>(a, batch, s);
+        case 24: return launch_hybrid<MT, MSC, 2, 4, RAW>(a, batch, s);
+        case 25: return launch_hybrid<MT, MSC, 2, 5, RAW>(a, batch, s);
+        case 26: return launch_hybrid<MT, MSC, 2, 6, RAW>(a, batch, s);
+        case 42: return launch_hybrid<MT, MSC, 4, 2, RAW>(a, batch, s);
         default: return NE_EINVAL;
     }
 }
 
-template <int NTW, int MT>
+template <int NTW, int MT, bool RAW>
 ne_status launch(const CconvArgs& a, int64_t batch, cudaStream_t s) {
     const int smem = cconv::smem_bytes(a.MS);
     static bool attr_set[64] = {false};
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-        if (cudaFuncSetAttribute(k_cconv_digits<NTW, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if (cudaFuncSetAttribute(k_cconv_digits<NTW, MT, RAW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  cconv::smem_bytes(16)) != cudaSuccess)
             return check_launch("ne_cconv_digits: shared-memory attribute");
         attr_set[dev] = true;
@@ -149,35 +169,60 @@ ne_status launch(const CconvArgs& a, int64_t batch, cudaStream_t s) {
     for (int64_t b0 = 0; b0 < batch; b0 += 65535) {
         const int64_t nb = batch - b0 < 65535 ? batch - b0 : 65535;
         dim3 grid((NB + cconv::NPB - 1) / cconv::NPB, (unsigned)nb);
-        k_cconv_digits<NTW, MT><<<grid, cconv::THREADS, smem, s>>>(a, b0);
+        k_cconv_digits<NTW, MT, RAW><<<grid, cconv::THREADS, smem, s>>>(a, b0);
         ne_status st = check_launch("ne_cconv_digits");
         if (st) return st;
     }
     return NE_OK;
 }
 
-}  // namespace
+template <bool RAW>
+ne_status dispatch(const CconvArgs& a, int64_t batch, cudaStream_t s) {
+    const int64_t NB = a.N / cconv::T;
+    const int var = hybrid_variant(NB);
+    if (var && NB <= 16) {
+        ne_status hs = NE_EINVAL;
+        if (a.M == 3 && a.MS == 6) hs = launch_hybrid_variant<3, 6, RAW>(var, a, batch, s);
+        else if (a.M == 4 && a.MS == 8) hs = launch_hybrid_variant<4, 8, RAW>(var, a, batch, s);
+        if (hs != NE_EINVAL) return hs;    // NE_EINVAL: this shape stays on the tensor pipe
+    }
+    const int MS = a.MS;
+    // a warp holds at most MS column tiles (16 output blocks x MS planes / 8 / 2)
+    switch (a.M) {
+        case 3:
+            if (MS <= 4) return launch<4, 3, RAW>(a, batch, s);
+            if (MS <= 6) return launch<6, 3, RAW>(a, batch, s);
+            return launch<10, 3, RAW>(a, batch, s);
+        case 4:
+            if (MS <= 4) return launch<4, 4, RAW>(a, batch, s);
+            if (MS <= 8) return launch<8, 4, RAW>(a, batch, s);
+            return launch<12, 4, RAW>(a, batch, s);
+        case 5:
+            if (MS <= 6) return launch<6, 5, RAW>(a, batch, s);
+            if (MS <= 10) return launch<10, 5, RAW>(a, batch, s);
+            return launch<16, 5, RAW>(a, batch, s);
+        default:
+            return launch<16, 0, RAW>(a, batch, s);
+    }
+}
 
-extern "C" ne_status ne_cconv_digits(ne_params p, ne_digits dg, const int8_t* planes, const int8_t* g, int64_t* out,
-                                     uint32_t* flags, uint64_t* nflag, int64_t batch, int64_t N, int32_t fuse,
-                                     int32_t r, cudaStream_t s) {
+ne_status common_args(const ne_params& p, const ne_digits& dg, int64_t batch, int64_t N, int32_t fuse, int32_t r,
+                      const char* who) {
     ne_status st = validate_params(p);
     if (st) return st;
     if ((st = validate_digits(dg))) return st;
-    if (batch < 0) return fail(NE_EINVAL, "ne_cconv_digits: batch < 0");
+    if (batch < 0) return fail(NE_EINVAL, "%s: batch < 0", who);
     if (N < 64 || N % 64 != 0 || N > 65536)
-        return fail(NE_EINVAL, "ne_cconv_digits: N=%lld must be a multiple of 64 in [64, 65536]", (long long)N);
-    if (fuse < NE_FUSE_NONE || fuse > NE_FUSE_RECOVER) return fail(NE_EINVAL, "ne_cconv_digits: fuse=%d", fuse);
-    if (r < 0 || r >= p.M) return fail(NE_EINVAL, "ne_cconv_digits: r=%d", r);
-    const int MS = p.M * dg.S;
-    if (MS > 16) return fail(NE_EINVAL, "ne_cconv_digits: M*S=%d exceeds 16 planes", MS);
-    unsigned long long* nf = reinterpret_cast<unsigned long long*>(nflag);
-    if (nf && cudaMemsetAsync(nf, 0, sizeof(*nf), s) != cudaSuccess) return check_launch("ne_cconv_digits: reset");
-    if (batch == 0) return NE_OK;
-    if (!planes || !g || !out) return fail(NE_EINVAL, "ne_cconv_digits: null pointer");
-    if (!aligned(planes, 16) || !aligned(out, 8)) return fail(NE_EINVAL, "ne_cconv_digits: planes must be 16-byte aligned");
-    CconvArgs a;
-    a.planes = planes;
+        return fail(NE_EINVAL, "%s: N=%lld must be a multiple of 64 in [64, 65536]", who, (long long)N);
+    if (fuse < NE_FUSE_NONE || fuse > NE_FUSE_RECOVER) return fail(NE_EINVAL, "%s: fuse=%d", who, fuse);
+    if (r < 0 || r >= p.M) return fail(NE_EINVAL, "%s: r=%d", who, r);
+    if (p.M * dg.S > 16) return fail(NE_EINVAL, "%s: M*S=%d exceeds 16 planes", who, p.M * dg.S);
+    return NE_OK;
+}
+
+void fill_args(CconvArgs& a, const ne_params& p, const ne_digits& dg, const int8_t* g, int64_t* out, uint32_t* flags,
+               unsigned long long* nf, int64_t N, int32_t fuse, int32_t r) {
+    a.planes = nullptr;
     a.g = g;
     a.out = out;
     a.flags = (fuse == NE_FUSE_EXTRACT_CHECK) ? flags : nullptr;
@@ -185,34 +230,75 @@ extern "C" ne_status ne_cconv_digits(ne_params p, ne_digits dg, const int8_t* pl
     a.N = N;
     a.M = p.M;
     a.S = dg.S;
-    a.MS = MS;
+    a.MS = p.M * dg.S;
     a.l = p.l;
     a.r = r;
     a.fuse = fuse;
     for (int i = 0; i < NE_MAX_DIGITS; i++) a.shift[i] = i < dg.S ? dg.shift[i] : 0;
-    const int64_t NB = N / cconv::T;
-    const int var = hybrid_variant(NB);
-    if (var && NB <= 16) {
-        ne_status hs = NE_EINVAL;
-        if (p.M == 3 && MS == 6) hs = launch_hybrid_variant<3, 6>(var, a, batch, s);
-        else if (p.M == 4 && MS == 8) hs = launch_hybrid_variant<4, 8>(var, a, batch, s);
-        if (hs != NE_EINVAL) return hs;    // NE_EINVAL: this shape stays on the tensor pipe
+    a.craw = nullptr;
+    a.status = nullptr;
+    a.raw_off = 0;
+    a.raw_lo = a.raw_hi = a.raw_plain = 0;
+    for (int i = 0; i < 4; i++) a.raw_byte[i] = 0;
+}
+
+}  // namespace
+
+extern "C" ne_status ne_cconv_digits(ne_params p, ne_digits dg, const int8_t* planes, const int8_t* g, int64_t* out,
+                                     uint32_t* flags, uint64_t* nflag, int64_t batch, int64_t N, int32_t fuse,
+                                     int32_t r, cudaStream_t s) {
+    ne_status st = common_args(p, dg, batch, N, fuse, r, "ne_cconv_digits");
+    if (st) return st;
+    unsigned long long* nf = reinterpret_cast<unsigned long long*>(nflag);
+    if (nf && cudaMemsetAsync(nf, 0, sizeof(*nf), s) != cudaSuccess) return check_launch("ne_cconv_digits: reset");
+    if (batch == 0) return NE_OK;
+    if (!planes || !g || !out) return fail(NE_EINVAL, "ne_cconv_digits: null pointer");
+    if (!aligned(planes, 16) || !aligned(out, 8)) return fail(NE_EINVAL, "ne_cconv_digits: planes must be 16-byte aligned");
+    CconvArgs a;
+    fill_args(a, p, dg, g, out, flags, nf, N, fuse, r);
+    a.planes = planes;
+    return dispatch<false>(a, batch, s);
+}
+
+extern "C" ne_status ne_cconv_entangled(ne_params p, ne_digits dg, const int32_t* c, const int8_t* g, int64_t* out,
+                                        uint32_t* flags, uint64_t* nflag, int64_t batch, int64_t N, int32_t fuse,
+                                        int32_t r, int32_t plain, int32_t* status, cudaStream_t s) {
+    ne_status st = common_args(p, dg, batch, N, fuse, r, "ne_cconv_entangled");
+    if (st) return st;
+    if (plain && fuse != NE_FUSE_NONE) return fail(NE_EINVAL, "ne_cconv_entangled: the plain operation has no extraction");
+    // the digit split in 32 bits needs the plan of a known input range: the
+    // digit set of (l, lo, hi) itself (plain: one digit of values in [-128, 127])
+    uint32_t off = 0;
+    int byte_of[4] = {0, 0, 0, 0};
+    if (plain) {
+        if (!(dg.S == 1 && dg.shift[0] == 0 && dg.lo <= dg.hi && dg.lo >= -128 && dg.hi <= 127))
+            return fail(NE_EINVAL, "ne_cconv_entangled: the plain operation needs one digit and a range in [-128, 127]");
+        off = 0x80u;
+    } else {
+        ne_digits ref;
+        FastPlan F;
+        bool planned = dg.lo <= dg.hi && dg.l == p.l && ne_plan_digits(dg.l, dg.lo, dg.hi, &ref) == NE_OK &&
+                       ref.S == dg.S;
+        for (int i = 0; planned && i < dg.S; i++) planned = ref.shift[i] == dg.shift[i];
+        if (!planned || !make_fast_plan(dg, p.l, &F))
+            return fail(NE_EINVAL, "ne_cconv_entangled: dg must be the plan of (l, lo, hi) with words of at most "
+                                   "4 digits; otherwise entangle with ne_entangle_digits");
+        off = F.off;
+        for (int i = 0; i < 4; i++) byte_of[i] = F.byte_of[i];
     }
-    // a warp holds at most MS column tiles (16 output blocks x MS planes / 8 / 2)
-    switch (p.M) {
-        case 3:
-            if (MS <= 4) return launch<4, 3>(a, batch, s);
-            if (MS <= 6) return launch<6, 3>(a, batch, s);
-            return launch<10, 3>(a, batch, s);
-        case 4:
-            if (MS <= 4) return launch<4, 4>(a, batch, s);
-            if (MS <= 8) return launch<8, 4>(a, batch, s);
-            return launch<12, 4>(a, batch, s);
-        case 5:
-            if (MS <= 6) return launch<6, 5>(a, batch, s);
-            if (MS <= 10) return launch<10, 5>(a, batch, s);
-            return launch<16, 5>(a, batch, s);
-        default:
-            return launch<16, 0>(a, batch, s);
-    }
+    unsigned long long* nf = reinterpret_cast<unsigned long long*>(nflag);
+    if (nf && cudaMemsetAsync(nf, 0, sizeof(*nf), s) != cudaSuccess) return check_launch("ne_cconv_entangled: reset");
+    if (batch == 0) return NE_OK;
+    if (!c || !g || !out) return fail(NE_EINVAL, "ne_cconv_entangled: null pointer");
+    if (!aligned(c, 16) || !aligned(out, 8)) return fail(NE_EINVAL, "ne_cconv_entangled: c must be 16-byte aligned");
+    CconvArgs a;
+    fill_args(a, p, dg, g, out, flags, nf, N, fuse, r);
+    a.craw = c;
+    a.status = status;
+    a.raw_off = off;
+    a.raw_lo = dg.lo;
+    a.raw_hi = dg.hi;
+    a.raw_plain = plain ? 1 : 0;
+    for (int i = 0; i < 4; i++) a.raw_byte[i] = byte_of[i];
+    return dispatch<true>(a, batch, s);
 }

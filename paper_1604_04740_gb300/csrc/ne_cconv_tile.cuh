@@ -22,6 +22,10 @@
 // The epilogue recombines the digits in int64, optionally flips injected
 // fault bits into delta, then extracts/checks per position with the shared
 // device code of the stand-alone extraction kernel.
+// The digit rows come either from digit planes in memory (cp.async) or, for
+// the fused form, straight from the raw int32 streams: Eq. 16 and the digit
+// split are computed while the window is loaded, so the entangled words never
+// reach memory.
 #pragma once
 
 #include "ne_common.cuh"
@@ -59,6 +63,15 @@ struct TileArgs {
     int N, M, S, MS, l, r, fuse;
     int flags_atomic;            // bitmap pre-zeroed: OR in the set bits instead of storing words
     int shift[NE_MAX_DIGITS];
+    // fused form (craw non-null): the raw streams [M][N] and the digit plan's
+    // 32-bit split -- every input is checked against [raw_lo, raw_hi], the word
+    // c_m + 2^l c_{m-1} (c_m alone if raw_plain) plus raw_off holds digit s as
+    // byte raw_byte[s] XOR 0x80; an input out of range sets *status = NE_ERANGE
+    const int32_t* craw;
+    int32_t* status;
+    uint32_t raw_off;
+    int raw_lo, raw_hi, raw_plain;
+    int raw_byte[4];
 };
 
 __device__ __forceinline__ int64_t shl64(int64_t x, int s) { return (int64_t)((uint64_t)x << s); }
@@ -144,9 +157,90 @@ __device__ __forceinline__ void epilogue(const TileArgs& a, const int32_t* stash
     }
 }
 
+// bytes t of four words, XOR 0x80: four consecutive positions of one digit plane
+__device__ __forceinline__ uint32_t pick4(uint32_t y0, uint32_t y1, uint32_t y2, uint32_t y3, uint32_t t) {
+    const uint32_t sel = t | ((t + 4) << 4);
+    return __byte_perm(__byte_perm(y0, y1, sel), __byte_perm(y2, y3, sel), 0x5410) ^ 0x80808080u;
+}
+
+// The digit rows [WB][MS][ROWB] of input blocks (first + blk_rel) mod NB.
+// From planes: 16-byte cp.async copies (a lost stream's rows zero-filled);
+// the caller commits and waits.  Fused: every work item (block, stream,
+// 16 positions) loads 16 inputs of c_m and c_{m-1}, forms the words of
+// Eq. 16 in 32 bits and stores the S digit rows' 16 bytes.
+template <bool RAW>
+__device__ __forceinline__ void load_window(const TileArgs& a, uint8_t* sig, int WB, int first, int NB, int nthr) {
+    const int N = a.N, MS = a.MS;
+    const int tid = threadIdx.x;
+    if constexpr (!RAW) {
+        const uint32_t sig_s = smem_u32(sig);
+        for (int e = tid; e < WB * MS * 4; e += nthr) {
+            const int c16 = e & 3, row = e >> 2;
+            const int blk_rel = row / MS, ms = row - blk_rel * MS;
+            int ab = (first + blk_rel) % NB;
+            if (ab < 0) ab += NB;
+            const int8_t* src = a.planes + (int64_t)ms * N + (int64_t)ab * T + c16 * 16;
+            const bool lost = (a.fuse == NE_FUSE_RECOVER) && (ms / a.S == a.r);
+            cp_async16(sig_s + row * ROWB + c16 * 16, src, lost ? 0 : 16);
+        }
+        return;
+    } else {
+    const int M = a.M, S = a.S;
+    uint32_t worst = 0;
+    for (int e = tid; e < WB * M * 4; e += nthr) {
+        const int c16 = e & 3, rowm = e >> 2;
+        const int blk_rel = rowm / M, m = rowm - blk_rel * M;
+        int ab = (first + blk_rel) % NB;
+        if (ab < 0) ab += NB;
+        uint8_t* dst = sig + (blk_rel * MS + m * S) * ROWB + c16 * 16;
+        if (a.fuse == NE_FUSE_RECOVER && m == a.r) {
+            for (int s = 0; s < S; s++) *reinterpret_cast<uint4*>(dst + s * ROWB) = make_uint4(0u, 0u, 0u, 0u);
+            continue;
+        }
+        const int64_t pos = (int64_t)ab * T + c16 * 16;
+        const int mp = m == 0 ? M - 1 : m - 1;
+        const int4* xm = reinterpret_cast<const int4*>(a.craw + (int64_t)m * N + pos);
+        const int4* xp = reinterpret_cast<const int4*>(a.craw + (int64_t)mp * N + pos);
+        uint32_t y[16];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const int4 v = __ldg(xm + q);
+            y[4 * q] = (uint32_t)v.x;
+            y[4 * q + 1] = (uint32_t)v.y;
+            y[4 * q + 2] = (uint32_t)v.z;
+            y[4 * q + 3] = (uint32_t)v.w;
+        }
+#pragma unroll
+        for (int k = 0; k < 16; k++) {
+            worst = max(worst, y[k] - (uint32_t)a.raw_lo);
+            y[k] += a.raw_off;
+        }
+        if (!a.raw_plain) {
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const int4 v = __ldg(xp + q);
+                y[4 * q] += (uint32_t)v.x << a.l;
+                y[4 * q + 1] += (uint32_t)v.y << a.l;
+                y[4 * q + 2] += (uint32_t)v.z << a.l;
+                y[4 * q + 3] += (uint32_t)v.w << a.l;
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < 4; s++) {
+            if (s >= S) break;
+            const uint32_t t = (uint32_t)a.raw_byte[s];
+            *reinterpret_cast<uint4*>(dst + s * ROWB) =
+                make_uint4(pick4(y[0], y[1], y[2], y[3], t), pick4(y[4], y[5], y[6], y[7], t),
+                           pick4(y[8], y[9], y[10], y[11], t), pick4(y[12], y[13], y[14], y[15], t));
+        }
+    }
+    if (worst > (uint32_t)a.raw_hi - (uint32_t)a.raw_lo && a.status) atomicExch(a.status, (int32_t)NE_ERANGE);
+    }
+}
+
 // The tile of output blocks [p0, p0 + npb) of one group; all 256 threads of
 // the block take part.  smem: smem_bytes(MS) bytes, 128-byte aligned.
-template <int NTW, int MT>
+template <int NTW, int MT, bool RAW = false>
 __device__ __forceinline__ void tile(const TileArgs& a, uint8_t* smem, int p0, int npb) {
     const int MS = a.MS;
     const int N = a.N;
@@ -177,17 +271,8 @@ __device__ __forceinline__ void tile(const TileArgs& a, uint8_t* smem, int p0, i
 
     for (int u0 = 0; u0 < NB; u0 += uch) {
         const int uc = min(uch, NB - u0);
-        // digit planes of input blocks (p0 - (u0 + uch - 1) + blk_rel) mod NB
-        const int nchunks = WB * MS * 4;
-        for (int e = tid; e < nchunks; e += THREADS) {
-            const int c16 = e & 3, row = e >> 2;
-            const int blk_rel = row / MS, ms = row - blk_rel * MS;
-            int ab = (p0 - (u0 + uch - 1) + blk_rel) % NB;
-            if (ab < 0) ab += NB;
-            const int8_t* src = a.planes + (int64_t)ms * N + (int64_t)ab * T + c16 * 16;
-            const bool lost = (a.fuse == NE_FUSE_RECOVER) && (ms / a.S == a.r);
-            cp_async16(sig_s + row * ROWB + c16 * 16, src, lost ? 0 : 16);
-        }
+        // digit rows of input blocks (p0 - (u0 + uch - 1) + blk_rel) mod NB
+        load_window<RAW>(a, sig, WB, p0 - (u0 + uch - 1), NB, THREADS);
         cp_async_commit();
         // g copies: copy rr, byte z holds g[(T (u0 + uch) - (z + rr - PADB)) mod N]
         const int top = T * (u0 + uch);
@@ -272,7 +357,7 @@ __host__ __device__ constexpr int hybrid_smem_bytes(int MS) {
     return WBMAX * MS * ROWB + 4 * GW + 4 * GDP + MS * NPB * SP * 4;
 }
 
-template <int MT, int MSC, int HW, int R>
+template <int MT, int MSC, int HW, int R, bool RAW = false>
 __device__ __forceinline__ void tile_hybrid(const TileArgs& a, uint8_t* smem) {
     constexpr int MS = MSC;
     constexpr int NTHR = hybrid_threads(HW);
@@ -296,14 +381,7 @@ __device__ __forceinline__ void tile_hybrid(const TileArgs& a, uint8_t* smem) {
     const uint32_t sig_s = smem_u32(sig);
 
     // -- loads (every thread) --
-    for (int e = tid; e < WB * MS * 4; e += NTHR) {
-        const int c16 = e & 3, row = e >> 2;
-        const int blk_rel = row / MS, ms = row - blk_rel * MS;
-        int ab = (blk_rel - (uch - 1)) % NB;
-        if (ab < 0) ab += NB;
-        const bool lost = (a.fuse == NE_FUSE_RECOVER) && (ms / a.S == a.r);
-        cp_async16(sig_s + row * ROWB + c16 * 16, a.planes + (int64_t)ms * N + (int64_t)ab * T + c16 * 16, lost ? 0 : 16);
-    }
+    load_window<RAW>(a, sig, WB, -(uch - 1), NB, NTHR);
     cp_async_commit();
     const int top = T * uch;
     for (int e = tid; e < 4 * (GW / 4); e += NTHR) {

@@ -76,6 +76,14 @@ def digits(shifts) -> ne_digits:
     return d
 
 
+def raw_digits(lo: int = -128, hi: int = 127) -> ne_digits:
+    """One digit at shift 0 for raw streams with values in [lo, hi] (the plain
+    operation of the fused kernels)."""
+    d = digits((0,))
+    d.lo, d.hi = lo, hi
+    return d
+
+
 def _load():
     path = _build.LIB
     if not os.path.exists(path) or os.environ.get("NE_REBUILD") == "1":
@@ -107,6 +115,7 @@ def _load():
         "ne_batch_run": [ne_batch_info, P, P, P, P, P, P, P, P, P, P, P],
         "ne_batch_run_static": [ctypes.POINTER(ne_job), i32, ne_batch_config, P, P, P, P, P, P, P, P, P, P],
         "ne_copy_regions_h2d": [P, P, P, P, P, i64, P],
+        "ne_cconv_entangled": [ne_params, ne_digits, P, P, P, P, P, i64, i64, i32, i32, i32, P, P],
         "ne_cconv_ntt": [ne_params, ne_digits, P, P, P, P, P, i64, i64, i32, i32, i32, P, P],
         "ne_abft_rc_encode": [P, P, P, P, i64, i64, i64, i64, P],
         "ne_abft_rc_check": [P, P, P, P, P, P, P, P, P, i64, i64, i64, i64, P],
@@ -314,6 +323,23 @@ def ne_cconv_digits(p: ne_params, dg: ne_digits, planes: torch.Tensor, g: torch.
     _call("ne_cconv_digits", p, dg, _ptr(planes, torch.int8, "planes"), _ptr(g, torch.int8, "g"),
           _ptr(out, torch.int64, "out"), _ptr(flags, torch.int32, "flags", True),
           _ptr(nflag, torch.int64, "nflag", True), batch, N, fuse, r, _stream())
+    return out
+
+
+def ne_cconv_entangled(p: ne_params, dg: ne_digits, c: torch.Tensor, g: torch.Tensor,
+                       out: torch.Tensor | None = None, flags: torch.Tensor | None = None,
+                       nflag: torch.Tensor | None = None, fuse: int = NE_FUSE_EXTRACT_CHECK, r: int = 0,
+                       plain: bool = False, status: torch.Tensor | None = None) -> torch.Tensor:
+    """c int32 [batch, M, N] (raw streams); g int8 [batch, N] -> int64 [batch, M, N] (tensor path, one launch)."""
+    batch, M, N = c.shape
+    if M != p.M or tuple(g.shape) != (batch, N):
+        raise ValueError("c / g shapes")
+    if out is None:
+        out = torch.empty((batch, M, N), dtype=torch.int64, device=c.device)
+    _call("ne_cconv_entangled", p, dg, _ptr(c, torch.int32, "c"), _ptr(g, torch.int8, "g"),
+          _ptr(out, torch.int64, "out"), _ptr(flags, torch.int32, "flags", True),
+          _ptr(nflag, torch.int64, "nflag", True), batch, N, fuse, r, 1 if plain else 0,
+          _ptr(status, torch.int32, "status", True), _stream())
     return out
 
 
