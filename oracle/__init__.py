@@ -61,6 +61,7 @@ def _L():
         lib.or_entangle_kernel_self.argtypes = [i32, p, p, i64]
         lib.or_extract.argtypes = [i32, i32, p, i64, i32, p, p]
         lib.or_inner.argtypes = [p, p, p, i64, i64, i64]
+        lib.or_cconv_at.argtypes = [p, p, i64, i64, p, p, i64, p]
         lib.or_rc_encode.argtypes = [p, p, i64, i64, i64, p, p]
         lib.or_gemm64.argtypes = [p, p, p, i64, i64, i64]
         lib.or_rc_check.argtypes = [p, i64, i64, p, p]
@@ -72,7 +73,7 @@ def _L():
         lib.or_abft_check.argtypes = [i32, p, i64, p]
         lib.or_abft_recover.argtypes = [i32, p, i64, i32]
         for f in ("or_entangle", "or_gemm", "or_cconv", "or_elementwise", "or_entangle_kernel_self",
-                  "or_extract", "or_rc_encode", "or_gemm64", "or_rc_check", "or_rc_correct", "or_inner", "or_outer", "or_permute", "or_cxcorr", "or_abft_encode", "or_abft_check", "or_abft_recover", "or_choose_l"):
+                  "or_extract", "or_cconv_at", "or_rc_encode", "or_gemm64", "or_rc_check", "or_rc_correct", "or_inner", "or_outer", "or_permute", "or_cxcorr", "or_abft_encode", "or_abft_check", "or_abft_recover", "or_choose_l"):
             getattr(lib, f).restype = i32
         _lib = lib
     return _lib
@@ -148,6 +149,19 @@ def cconv(x, g):
     assert g.shape == (B, N)
     y = np.empty_like(x)
     _chk(_L().or_cconv(px, pg, y.ctypes.data, B, S, N), "cconv")
+    return y
+
+
+def cconv_at(x, g, signal, pos):
+    """Selected outputs y[signal[t], pos[t]] of cconv(x, g), one by one (x int64
+    [B, S, N], g int8 [B, N], signal = b * S + s)."""
+    x, px = _arr(x, np.int64)
+    g, pg = _arr(g, np.int8)
+    B, S, N = x.shape
+    sig, ps = _arr(signal, np.int64)
+    pos, pp = _arr(pos, np.int64)
+    y = np.empty(sig.size, np.int64)
+    _chk(_L().or_cconv_at(px, pg, S, N, ps, pp, sig.size, y.ctypes.data), "cconv_at")
     return y
 
 

@@ -244,6 +244,30 @@ static int cconv_one(const int64_t *x, const int8_t *g, int64_t *y, int64_t N) {
 }
 
 /*
+ * Selected outputs of the same circular convolution, one by one: for each of
+ * the count requests (signal index bs of the batched [B][S][N] layout,
+ * position n), y_at[t] = sum_j x[bs][j] g[bs / S][(n - j) mod N].  For
+ * lengths whose full convolution is too long to check output by output.
+ */
+int or_cconv_at(const int64_t *x, const int8_t *g, int64_t S, int64_t N, const int64_t *bs, const int64_t *pos,
+                int64_t count, int64_t *y_at) {
+    if (S < 1 || N < 1 || count < 0) return OR_EINVAL;
+    int err = OR_OK;
+    for (int64_t t = 0; t < count; t++) {
+        const int64_t *xs = x + bs[t] * N;
+        const int8_t *gb = g + (bs[t] / S) * N;
+        i128 acc = 0;
+        for (int64_t j = 0; j < N; j++) {
+            int64_t idx = (int64_t)floor_mod((i128)(pos[t] - j), (i128)N);
+            acc = checked_add(acc, checked_mul((i128)xs[j], (i128)gb[idx], &err), &err);
+            if (!fits_i64(acc)) err = OR_EOVERFLOW;
+        }
+        y_at[t] = low64(acc);
+    }
+    return err;
+}
+
+/*
  * Batched form: x is [B][S][N] (B groups of S signals), g is [B][N] (one
  * kernel per group), y is [B][S][N].  Signal s of group b is convolved with
  * kernel b.

@@ -280,3 +280,19 @@ def test_rc_two_errors_are_detected_not_corrected():
     assert np.flatnonzero(rb).tolist() == [1, 4] and np.flatnonzero(cb).tolist() == [2, 6]
     fixed, done = oracle.rc_correct(bad)
     assert not done and (fixed == bad).all()
+
+
+def test_cconv_at_equals_full_cconv_at_every_requested_output():
+    rng = np.random.default_rng(16)
+    B, S, N = 3, 2, 37
+    x = rng.integers(-(2 ** 20), 2 ** 20, (B, S, N), dtype=np.int64)
+    g = rng.integers(-128, 128, (B, N)).astype(np.int8)
+    full = oracle.cconv(x, g)
+    sig = rng.integers(0, B * S, 50)
+    pos = rng.integers(0, N, 50)
+    assert (oracle.cconv_at(x, g, sig, pos) == full.reshape(B * S, N)[sig, pos]).all()
+    # y[0] of a delta signal is the filter's first entry
+    e = np.zeros((1, 1, 8), np.int64)
+    e[0, 0, 0] = 1
+    gg = np.arange(8, dtype=np.int8).reshape(1, 8)
+    assert oracle.cconv_at(e, gg, [0, 0], [0, 5]).tolist() == [0, 5]
