@@ -43,6 +43,8 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from paper_1604_04740_gb300 import dist as D  # noqa: E402
+
 METRIC = "entangled int GEMM/conv Gop/s & overhead % vs plain, same GB300, bit-exact"
 L2_FLUSH_BYTES = 256 << 20
 L2_NOTE = ("flushed before every timed step: 256 MiB written, then a second 256 MiB buffer read, so the "
@@ -83,13 +85,13 @@ def parse():
 # ---- workload definitions ---------------------------------------------------------
 
 class Workload:
-    def __init__(self, name):
+    def __init__(self, name, seed=0):
         from paper_1604_04740_gb300 import inputs
         self.name = name
         if name in ("cconv", "cconv_ntt"):
             self.G, self.M, self.N = 4096, 3, 1024
-            self.c = inputs.streams(0, (self.G, self.M, self.N))
-            self.g = inputs.operator_int8(0, (self.G, self.N))
+            self.c = inputs.streams(seed, (self.G, self.M, self.N))
+            self.g = inputs.operator_int8(seed, (self.G, self.N))
             self.bound = self.N * 2 ** 14
             self.useful_ops = 2 * self.G * self.M * self.N ** 2
             self.desc = f"batched circular convolution: {self.G} groups x M={self.M} x N={self.N}, int8 filter per group"
@@ -97,15 +99,15 @@ class Workload:
                 self.desc += ", number-theoretic transform"
         elif name == "gemm":
             self.M, self.n = 4, 4096
-            self.c = inputs.streams(0, (self.M, self.n, self.n))
-            self.Gm = inputs.operator_int8(0, (self.n, self.n))
+            self.c = inputs.streams(seed, (self.M, self.n, self.n))
+            self.Gm = inputs.operator_int8(seed, (self.n, self.n))
             self.bound = self.n * 2 ** 14
             self.useful_ops = 2 * self.M * self.n ** 3
             self.desc = f"GEMM: M={self.M} streams of {self.n}x{self.n} int32 times a shared {self.n}x{self.n} int8"
         else:
             self.M, self.n = 3, 64
-            self.c = inputs.streams(0, (self.M, self.n, self.n))
-            self.Gm = inputs.operator_int8(0, (self.n, self.n))
+            self.c = inputs.streams(seed, (self.M, self.n, self.n))
+            self.Gm = inputs.operator_int8(seed, (self.n, self.n))
             self.bound = self.n * 2 ** 14
             self.useful_ops = 2 * self.M * self.n ** 3
             self.desc = f"GEMM: M={self.M} streams of {self.n}x{self.n} times a shared {self.n}x{self.n} int8, int64 CUDA-core form"
@@ -288,7 +290,7 @@ def run_ours(args, rank, world, local_rank):
 
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
-    wl = Workload(args.workload)
+    wl = Workload(args.workload, D.rank_seed(0, rank))
     K, W = args.steps, args.warmup
     flush = L2Flush(torch, dev)
     extras = {}
@@ -416,7 +418,6 @@ def run_ours(args, rank, world, local_rank):
                "parallelism": f"replicas x{world}"}
 
     # --- main timed region ---------------------------------------------------------------
-    import torch.distributed as dist
     try:
         smi_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
     except Exception:
@@ -425,17 +426,13 @@ def run_ours(args, rank, world, local_rank):
     for _ in range(W):
         step(None)
     torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
+    D.barrier()
     torch.cuda.synchronize()
     sampler.start()
     time.sleep(0.15)
     total_ms, inner = timed_steps(torch, step, K, 0, flush, inner=True)
     clocks = sampler.stop()
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = D.max_over_ranks(total_ms, dev)
     ms_per_step = total_ms / K
     value = wl.useful_ops * world / (ms_per_step * 1e-3) / 1e9
     assert int(nflag.item()) == 0, "clean data flagged"
@@ -466,7 +463,7 @@ def run_ours(args, rank, world, local_rank):
         if hybrid:
             # both int8 pipes in the convolution kernel's warp layout (8 tensor + 2 dp4a warps,
             # 3 blocks per SM), swept over the share of the work given to dp4a; the ceiling
-            # is the best split (the kernel gives dp4a 4 of 16 output blocks, a quarter)
+            # is the best split (the kernel gives dp4a 6 of 16 output blocks, 3/8)
             I = 2048
             for num, den in ((0, 1), (1, 8), (1, 4), (3, 8), (1, 2)):
                 idp = (128 * I * num) // (den - num)
@@ -478,8 +475,8 @@ def run_ours(args, rank, world, local_rank):
                 peak_mixed[f"{num}/{den}"] = ops / (e0.elapsed_time(e1) * 1e-3) / 1e12
         peak = max(peak_mixed.values()) if hybrid else peak_mma
         src = ("measured in this run: mma.sync.m16n8k32 s8 register-resident probe (ne_probe_mma_peak)"
-               + ("; the kernel splits each group between the two int8 pipes (12 of 16 blocks on the tensor "
-                  "pipe, 4 on dp4a), so the peak is the best of ne_probe_mixed_peak (both pipes in the "
+               + ("; the kernel splits each group between the two int8 pipes (10 of 16 blocks on the tensor "
+                  "pipe, 6 on dp4a), so the peak is the best of ne_probe_mixed_peak (both pipes in the "
                   "kernel's warp layout) over the dp4a work shares in peak_mixed" if hybrid else "")
                + "; MEASURED_PEAKS.json has no int8 figure and sm_103a has no tcgen05 integer MMA")
         roof = {"bound": "tensor", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "TOP/s",
@@ -837,9 +834,8 @@ def run_batch(args, rank, world, local_rank):
     for _ in range(W):
         b.replay()
     torch.cuda.synchronize()
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
+    D.barrier()
+    torch.cuda.synchronize()
     sampler.start()
     time.sleep(0.15)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -849,12 +845,7 @@ def run_batch(args, rank, world, local_rank):
     e1.record(stream)
     torch.cuda.synchronize()
     clocks = sampler.stop()
-    total_ms = e0.elapsed_time(e1)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = D.max_over_ranks(e0.elapsed_time(e1), dev)
     ms = total_ms / K
     useful = b.useful_ops()
     value = useful * world / (ms * 1e-3) / 1e9
@@ -1011,9 +1002,8 @@ def main():
         return
     if world > 1:
         import torch
-        import torch.distributed as dist
         torch.cuda.set_device(local_rank)
-        dist.init_process_group("nccl")
+        D.init("nccl")
     if args.workload == "batch":
         run_batch(args, rank, world, local_rank)
     elif args.workload == "serve":
@@ -1022,9 +1012,7 @@ def main():
         run_serve(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
-    if world > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
+    D.finish()
 
 
 if __name__ == "__main__":

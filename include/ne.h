@@ -201,6 +201,28 @@ ne_status ne_cconv_ntt(ne_params p, ne_digits dg, const int32_t* c, const int8_t
                        uint32_t* flags, uint64_t* nflag, int64_t batch, int64_t N, int32_t fuse,
                        int32_t r, int32_t plain, int32_t* status, cudaStream_t s);
 
+/* Workspace bytes ne_cconv_ntt_any needs for batch groups of M streams of
+ * length N (-1 for invalid sizes). */
+int64_t ne_cconv_ntt_any_workspace(int32_t M, int64_t N, int64_t batch);
+
+/* The transform convolution for any N in [2, 65536]: the words of Eq. 16
+ * (plain = 1: the raw values) are transformed modulo two primes (77 * 2^19 + 1
+ * and 69 * 2^19 + 1) at length N (a power of two) or at the next power of two
+ * >= 2N - 1 (a linear convolution folded back), and the outputs rebuilt by the
+ * Chinese remainder theorem, then the epilogue of ne_cconv_digits.
+ * cmin, cmax: the range of the stream values; an input outside it sets
+ * *status = NE_ERANGE (device int32, nullable), and the host returns
+ * NE_ERANGE when N * max|c| (2^l + 1) * 128 could leave the two-prime range.
+ * workspace: device, 16-byte aligned, at least ne_cconv_ntt_any_workspace
+ * bytes (caller-owned scratch).  The first call on a device also fills the
+ * library's twiddle tables and synchronises s.  c: int32 [batch][M][N];
+ * g: int8 [batch][N]; out: int64 [batch][M][N]; flags: [batch][ceil(N/32)];
+ * batch <= 65535. */
+ne_status ne_cconv_ntt_any(ne_params p, int32_t cmin, int32_t cmax, const int32_t* c, const int8_t* g,
+                           int64_t* out, uint32_t* flags, uint64_t* nflag, int64_t batch, int64_t N,
+                           int32_t fuse, int32_t r, int32_t plain, int32_t* status, void* workspace,
+                           int64_t workspace_bytes, cudaStream_t s);
+
 /* ------------------------------------------------------------------------ */
 /* Extraction, check and recovery (Eq. 17-20, Eq. 24, Prop. 3)               */
 /* ------------------------------------------------------------------------ */
@@ -408,6 +430,9 @@ typedef struct {
     int32_t order;             /* NE_ORDER_JOB or NE_ORDER_LPT                                */
     int32_t cconv_blocks;      /* outputs per convolution tile, in blocks of 64: 4, 8 or 16   */
     int32_t l_policy;          /* NE_L_BYTE or NE_L_SMALLEST for jobs with l = 0              */
+    int32_t ntt_min_n;         /* convolutions with N >= this (and outputs inside the two-prime
+                                  range) run as exact transforms (ne_cconv_ntt_any's kernels)
+                                  instead of tensor tiles; 0: never                            */
 } ne_batch_config;
 
 typedef struct {               /* what ne_batch_run needs to know on the host                 */
@@ -416,6 +441,11 @@ typedef struct {               /* what ne_batch_run needs to know on the host   
     int64_t workspace_bytes;   /* device workspace the plan occupies                          */
     int64_t mma_ops;           /* int8 operations the tiles issue (2 x multiply-adds)         */
     int64_t useful_ops;        /* 2 x multiply-adds of the operations on the raw streams      */
+    int32_t ntransform;        /* jobs on the transform path                                  */
+    int32_t ntt_max_logL, ntt_max_M, pad;
+    int64_t ntt_table_off;     /* byte offsets of the transform jobs' table and scratch       */
+    int64_t ntt_ws_off;
+    int64_t ntt_units;         /* the largest (M + 1) L of the transform jobs                 */
 } ne_batch_info;
 
 /* Plan a batch: choose l and the digit plan of every job, lay out the digit

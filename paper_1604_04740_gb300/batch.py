@@ -243,6 +243,7 @@ def default_config(**kw) -> ne.ne_batch_config:
     cfg.order = kw.get("order", ne.NE_ORDER_LPT)
     cfg.cconv_blocks = kw.get("cconv_blocks", 16)
     cfg.l_policy = kw.get("l_policy", ne.NE_L_BYTE)
+    cfg.ntt_min_n = kw.get("ntt_min_n", 0)
     return cfg
 
 

@@ -14,6 +14,9 @@
 //     counter and runs a product tile (16 x 64 outputs, all M*S planes) or
 //     a convolution tile (up to 1024 outputs, all planes, ne_cconv_tile.cuh)
 //     with the fused extract/check or fused recovery of its job.
+//   Long convolutions (N >= the plan's ntt_min_n) skip the tiles and run as
+//     exact two-prime transforms (ne_ntt_any.cu) in the launches that follow,
+//     with the same epilogues and the same fault hook.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -22,6 +25,7 @@
 #include "ne_entangle.cuh"
 #include "ne_extract.cuh"
 #include "ne_mma.cuh"
+#include "ne_ntt_any.cuh"
 
 namespace {
 
@@ -48,18 +52,21 @@ struct DevSeg {
 };
 
 struct Layout {
-    int64_t jobs, tiles, segs, planes, total;
+    int64_t jobs, tiles, segs, planes, ntt_table, ntt_ws, total;
 };
 
 int64_t align256(int64_t x) { return (x + 255) & ~(int64_t)255; }
 
-Layout layout(int64_t njobs, int64_t ntiles, int64_t nsegs, int64_t plane_bytes) {
+Layout layout(int64_t njobs, int64_t ntiles, int64_t nsegs, int64_t plane_bytes, int64_t nntt = 0,
+              int64_t ntt_ws_bytes = 0) {
     Layout L;
     L.jobs = 256;
     L.tiles = align256(L.jobs + njobs * (int64_t)sizeof(DevJob));
     L.segs = align256(L.tiles + ntiles * (int64_t)sizeof(DevTile));
     L.planes = align256(L.segs + nsegs * (int64_t)sizeof(DevSeg));
-    L.total = align256(L.planes + plane_bytes);
+    L.ntt_table = align256(L.planes + plane_bytes);
+    L.ntt_ws = align256(L.ntt_table + nntt * (int64_t)sizeof(NJob));
+    L.total = align256(L.ntt_ws + ntt_ws_bytes);
     return L;
 }
 
@@ -460,7 +467,11 @@ extern "C" ne_status ne_batch_plan(const ne_job* jobs, int32_t njobs, ne_batch_c
         return fail(NE_EINVAL, "ne_batch_plan: cconv_blocks=%d", cfg.cconv_blocks);
     if (cfg.l_policy != NE_L_BYTE && cfg.l_policy != NE_L_SMALLEST)
         return fail(NE_EINVAL, "ne_batch_plan: l_policy=%d", cfg.l_policy);
+    if (cfg.ntt_min_n < 0) return fail(NE_EINVAL, "ne_batch_plan: ntt_min_n=%d", cfg.ntt_min_n);
     std::vector<DevJob> dj((size_t)njobs);
+    std::vector<NJob> nj;
+    int64_t ntt_ws = 0, ntt_units = 0;
+    int ntt_max_logL = 0, ntt_max_M = 0;
     std::vector<DevTile> tiles;
     std::vector<DevSeg> segs;
     std::vector<int64_t> cost;
@@ -532,9 +543,43 @@ extern "C" ne_status ne_batch_plan(const ne_job* jobs, int32_t njobs, ne_batch_c
         d.fault_end = j.fault_end;
         d.npos = j.kind == NE_JOB_GEMM ? (int64_t)j.rows * j.k : (int64_t)j.N;
         d.nout = j.kind == NE_JOB_GEMM ? (int64_t)j.rows * j.cols : (int64_t)j.N;
+        flag_words = std::max(flag_words, j.flag_off + (d.nout + 31) / 32);
+        const int32_t cabs = (int32_t)amax;
+        if (j.kind == NE_JOB_CCONV && cfg.ntt_min_n > 0 && j.N >= cfg.ntt_min_n &&
+            ntt_any_exact(j.M, j.plain ? 0 : l, j.N, cabs, j.plain != 0)) {
+            // the exact transform path: no digit planes, segments or tiles
+            NJob t;
+            std::memset(&t, 0, sizeof(t));
+            int lg = 0;
+            t.L = ntt_any_length(j.N, &lg);
+            t.logL = lg;
+            t.c_off = j.c_off;
+            t.g_off = j.op_off;
+            t.out_off = j.out_off;
+            t.flag_off = j.flag_off;
+            t.ws_off = ntt_ws / 4;
+            t.fault_begin = j.fault_begin;
+            t.fault_end = j.fault_end;
+            t.M = j.M;
+            t.N = j.N;
+            t.l = j.plain ? 0 : l;
+            t.r = j.fuse == NE_FUSE_NONE ? 0 : j.r;
+            t.fuse = j.fuse;
+            t.plain = j.plain;
+            t.lo = j.cmin;
+            t.hi = j.cmax;
+            ntt_any_job_constants(t);
+            nj.push_back(t);
+            ntt_ws = align256(ntt_ws + (int64_t)(j.M + 1) * 2 * t.L * 4);
+            ntt_units = std::max(ntt_units, (int64_t)(j.M + 1) * t.L);
+            ntt_max_logL = std::max(ntt_max_logL, lg);
+            ntt_max_M = std::max(ntt_max_M, (int)j.M);
+            d.plane_off = plane_bytes;           // no planes
+            useful += 2LL * j.M * j.N * j.N;
+            continue;
+        }
         d.plane_off = plane_bytes;
         plane_bytes = align256(plane_bytes + (int64_t)d.MS * d.npos);
-        flag_words = std::max(flag_words, j.flag_off + (d.nout + 31) / 32);
         for (int64_t s0 = 0; s0 < d.npos; s0 += SEG) segs.push_back(DevSeg{i, 0, s0, std::min<int64_t>(SEG, d.npos - s0)});
         if (j.kind == NE_JOB_GEMM) {
             const int rt = (j.rows + bgemm::BM - 1) / bgemm::BM, ct = (j.cols + bgemm::BN - 1) / bgemm::BN;
@@ -565,7 +610,8 @@ extern "C" ne_status ne_batch_plan(const ne_job* jobs, int32_t njobs, ne_batch_c
         tiles.swap(sorted);
     }
     if (tiles.size() > 0x7fffffff || segs.size() > 0x7fffffff) return fail(NE_EINVAL, "ne_batch_plan: batch too large");
-    const Layout L = layout(njobs, (int64_t)tiles.size(), (int64_t)segs.size(), plane_bytes);
+    if (nj.size() > 65535) return fail(NE_EINVAL, "ne_batch_plan: more than 65535 transform jobs");
+    const Layout L = layout(njobs, (int64_t)tiles.size(), (int64_t)segs.size(), plane_bytes, (int64_t)nj.size(), ntt_ws);
     info->njobs = njobs;
     info->ntiles = (int32_t)tiles.size();
     info->nsegs = (int32_t)segs.size();
@@ -574,7 +620,19 @@ extern "C" ne_status ne_batch_plan(const ne_job* jobs, int32_t njobs, ne_batch_c
     info->workspace_bytes = L.total;
     info->mma_ops = mma_ops;
     info->useful_ops = useful;
+    info->ntransform = (int32_t)nj.size();
+    info->ntt_max_logL = ntt_max_logL;
+    info->ntt_max_M = ntt_max_M;
+    info->pad = 0;
+    info->ntt_table_off = L.ntt_table;
+    info->ntt_ws_off = L.ntt_ws;
+    info->ntt_units = ntt_units;
     if (!workspace) return NE_OK;
+    if (!nj.empty()) {
+        // the twiddle tables are filled here, outside any stream capture of the runs
+        ne_status st = ntt_any_init_tables(s);
+        if (st) return st;
+    }
     if (workspace_bytes < L.total) return fail(NE_ENOMEM, "ne_batch_plan: workspace %lld < %lld bytes",
                                                (long long)workspace_bytes, (long long)L.total);
     if (!aligned(workspace, 256)) return fail(NE_EINVAL, "ne_batch_plan: workspace must be 256-byte aligned");
@@ -582,9 +640,12 @@ extern "C" ne_status ne_batch_plan(const ne_job* jobs, int32_t njobs, ne_batch_c
     std::memcpy(host.data() + L.jobs, dj.data(), dj.size() * sizeof(DevJob));
     if (!tiles.empty()) std::memcpy(host.data() + L.tiles, tiles.data(), tiles.size() * sizeof(DevTile));
     if (!segs.empty()) std::memcpy(host.data() + L.segs, segs.data(), segs.size() * sizeof(DevSeg));
-    if (cudaMemcpyAsync(workspace, host.data(), host.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)
+    if (cudaMemcpyAsync(workspace, host.data(), host.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
         return check_launch("ne_batch_plan: copy tables");
+    if (!nj.empty() && cudaMemcpyAsync(static_cast<uint8_t*>(workspace) + L.ntt_table, nj.data(),
+                                       nj.size() * sizeof(NJob), cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return check_launch("ne_batch_plan: copy transform jobs");
+    if (cudaStreamSynchronize(s) != cudaSuccess) return check_launch("ne_batch_plan: copy tables");
     return NE_OK;
 }
 
@@ -636,7 +697,25 @@ extern "C" ne_status ne_batch_run(ne_batch_info info, const int32_t* c, const in
     }
     if (info.ntiles > 0) {
         k_batch_op<<<info.grid, THREADS, op_smem_bytes(), s>>>(k);
-        return check_launch("ne_batch_run: operation");
+        ne_status st = check_launch("ne_batch_run: operation");
+        if (st) return st;
+    }
+    if (info.ntransform > 0) {
+        NttAnyArgs a{};
+        a.jobs.table = reinterpret_cast<const NJob*>(ws + info.ntt_table_off);
+        a.jobs.njobs = info.ntransform;
+        a.c = c;
+        a.g = ops;
+        a.out = out;
+        a.flags = flags;
+        a.nflag = reinterpret_cast<unsigned long long*>(nflag);
+        a.flags_atomic = 1;
+        a.status = status;
+        a.ws = reinterpret_cast<uint32_t*>(ws + info.ntt_ws_off);
+        a.fault_pos = fault_pos;
+        a.fault_stream = fault_stream;
+        a.fault_bit = fault_bit;
+        return ntt_any_run(a, info.ntt_max_logL, info.ntt_max_M, info.ntt_units, s);
     }
     return NE_OK;
 }

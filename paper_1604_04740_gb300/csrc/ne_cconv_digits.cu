@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(cconv::THREADS, (NTW <= 6 ? 4 : (NTW <= 10 ? 3
 
 // The hybrid tile (tensor pipe + dp4a pipe) for groups of 9..16 blocks.
 template <int MT, int MSC, int HW, int R, bool RAW>
-__global__ void __launch_bounds__(cconv::hybrid_threads(HW), RAW ? 3 : 2) k_cconv_digits_hybrid(CconvArgs a, int64_t b_off) {
+__global__ void __launch_bounds__(cconv::hybrid_threads(HW), 3) k_cconv_digits_hybrid(CconvArgs a, int64_t b_off) {
     extern __shared__ __align__(128) uint8_t smem[];
     const int64_t b = b_off + blockIdx.y;
     const int64_t N = a.N;
@@ -124,19 +124,21 @@ ne_status launch_hybrid(const CconvArgs& a, int64_t batch, cudaStream_t s) {
     return NE_OK;
 }
 
-// Split of a group between the tensor pipe and the dp4a pipe.  Default:
-// groups of 16 blocks put 4 blocks on 2 dp4a warps (variant 24, the fastest
-// of the splits measured on GB300: 12 % less time than the tensor pipe
-// alone for 4096 x 3 x 1024).  NE_CCONV_HYBRID overrides: "0" tensor pipe
-// only; "HR" H dp4a warps of R outputs per thread (H * R / 2 blocks on
-// dp4a), one of 22..26, 42, for any group of at most 16 blocks.
-int hybrid_variant(int64_t NB) {
+// Split of a group between the tensor pipe and the dp4a pipe.  Default for
+// groups of 16 blocks (the fastest splits measured on GB300 at 3 CTAs per
+// SM, 4096 groups, N = 1024): 6 planes (M = 3, two digits) put 6 blocks on 2
+// dp4a warps (variant 26, 3/8 of the work -- the best split of the two-pipe
+// probe as well); 8 planes put 4 blocks on them (variant 24; 26 would spill).
+// NE_CCONV_HYBRID overrides: "0" tensor pipe only; "HR" H dp4a warps of R
+// outputs per thread (H * R / 2 blocks on dp4a), one of 22..26, 42, for any
+// group of at most 16 blocks.
+int hybrid_variant(int64_t NB, int MS) {
     static int v = -2;
     if (v == -2) {
         const char* e = getenv("NE_CCONV_HYBRID");
         v = e ? atoi(e) : -1;
     }
-    if (v == -1) return NB == 16 ? 24 : 0;
+    if (v == -1) return NB == 16 ? (MS == 6 ? 26 : 24) : 0;
     return v;
 }
 
@@ -179,7 +181,7 @@ ne_status launch(const CconvArgs& a, int64_t batch, cudaStream_t s) {
 template <bool RAW>
 ne_status dispatch(const CconvArgs& a, int64_t batch, cudaStream_t s) {
     const int64_t NB = a.N / cconv::T;
-    const int var = hybrid_variant(NB);
+    const int var = hybrid_variant(NB, a.MS);
     if (var && NB <= 16) {
         ne_status hs = NE_EINVAL;
         if (a.M == 3 && a.MS == 6) hs = launch_hybrid_variant<3, 6, RAW>(var, a, batch, s);

@@ -54,12 +54,14 @@ class ne_job(ctypes.Structure):
 
 
 class ne_batch_config(ctypes.Structure):
-    _fields_ = [(n, ctypes.c_int32) for n in ("ctas_per_sm", "order", "cconv_blocks", "l_policy")]
+    _fields_ = [(n, ctypes.c_int32) for n in ("ctas_per_sm", "order", "cconv_blocks", "l_policy", "ntt_min_n")]
 
 
 class ne_batch_info(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in ("njobs", "ntiles", "nsegs", "grid")] + \
-               [(n, ctypes.c_int64) for n in ("flag_words", "workspace_bytes", "mma_ops", "useful_ops")]
+               [(n, ctypes.c_int64) for n in ("flag_words", "workspace_bytes", "mma_ops", "useful_ops")] + \
+               [(n, ctypes.c_int32) for n in ("ntransform", "ntt_max_logL", "ntt_max_M", "pad")] + \
+               [(n, ctypes.c_int64) for n in ("ntt_table_off", "ntt_ws_off", "ntt_units")]
 
 
 def params(M: int, l: int, w: int = 64) -> ne_params:
@@ -116,6 +118,7 @@ def _load():
         "ne_batch_run_static": [ctypes.POINTER(ne_job), i32, ne_batch_config, P, P, P, P, P, P, P, P, P, P],
         "ne_copy_regions_h2d": [P, P, P, P, P, i64, P],
         "ne_cconv_entangled": [ne_params, ne_digits, P, P, P, P, P, i64, i64, i32, i32, i32, P, P],
+        "ne_cconv_ntt_any": [ne_params, i32, i32, P, P, P, P, P, i64, i64, i32, i32, i32, P, P, i64, P],
         "ne_cconv_ntt": [ne_params, ne_digits, P, P, P, P, P, i64, i64, i32, i32, i32, P, P],
         "ne_abft_rc_encode": [P, P, P, P, i64, i64, i64, i64, P],
         "ne_abft_rc_check": [P, P, P, P, P, P, P, P, P, i64, i64, i64, i64, P],
@@ -131,6 +134,8 @@ def _load():
         f = getattr(lib, name)
         f.argtypes = args
         f.restype = ctypes.c_int
+    lib.ne_cconv_ntt_any_workspace.argtypes = [i32, i64, i64]
+    lib.ne_cconv_ntt_any_workspace.restype = i64
     lib.ne_last_error.restype = ctypes.c_char_p
     lib.ne_version.restype = ctypes.c_char_p
     return lib
@@ -340,6 +345,28 @@ def ne_cconv_entangled(p: ne_params, dg: ne_digits, c: torch.Tensor, g: torch.Te
           _ptr(out, torch.int64, "out"), _ptr(flags, torch.int32, "flags", True),
           _ptr(nflag, torch.int64, "nflag", True), batch, N, fuse, r, 1 if plain else 0,
           _ptr(status, torch.int32, "status", True), _stream())
+    return out
+
+
+def ne_cconv_ntt_any(p: ne_params, c: torch.Tensor, g: torch.Tensor, out: torch.Tensor | None = None,
+                     flags: torch.Tensor | None = None, nflag: torch.Tensor | None = None,
+                     fuse: int = NE_FUSE_EXTRACT_CHECK, r: int = 0, plain: bool = False,
+                     status: torch.Tensor | None = None, cmin: int = -128, cmax: int = 127,
+                     workspace: torch.Tensor | None = None) -> torch.Tensor:
+    """c int32 [batch, M, N] (raw streams, any N in [2, 65536]); g int8 [batch, N] -> int64 [batch, M, N]."""
+    batch, M, N = c.shape
+    if M != p.M or tuple(g.shape) != (batch, N):
+        raise ValueError("c / g shapes")
+    need = int(_lib.ne_cconv_ntt_any_workspace(M, N, batch))
+    if workspace is None:
+        workspace = torch.empty(max(need, 16), dtype=torch.uint8, device=c.device)
+    if out is None:
+        out = torch.empty((batch, M, N), dtype=torch.int64, device=c.device)
+    _call("ne_cconv_ntt_any", p, cmin, cmax, _ptr(c, torch.int32, "c"), _ptr(g, torch.int8, "g"),
+          _ptr(out, torch.int64, "out"), _ptr(flags, torch.int32, "flags", True),
+          _ptr(nflag, torch.int64, "nflag", True), batch, N, fuse, r, 1 if plain else 0,
+          _ptr(status, torch.int32, "status", True), _ptr(workspace, torch.uint8, "workspace"),
+          workspace.numel(), _stream())
     return out
 
 

@@ -81,6 +81,42 @@ def test_batch_matches_oracle_and_flags_exactly_the_faults(mods):
     assert b.faults is not None and int(b.nflag.item()) == total == len(b.faults["pos"])
 
 
+def test_transform_path_matches_oracle_tensor_path_and_graph(mods):
+    # convolutions of N >= 512 leave the tensor tiles for the exact transforms
+    B, ne = mods
+    specs = small_specs(B, ne) + [B.JobSpec(ne.NE_JOB_CCONV, 3, N=4160), B.JobSpec(ne.NE_JOB_CCONV, 5, N=8192),
+                                  B.JobSpec(ne.NE_JOB_CCONV, 4, N=2112, fuse=ne.NE_FUSE_RECOVER, r=0)]
+    b = B.Batch(specs, seed=10, fault_rate=2e-3)
+    b.plan(B.default_config(ntt_min_n=512))
+    assert b.info.ntransform >= 5
+    b.run()
+    torch.cuda.synchronize()
+    assert int(b.status.item()) == 0
+    total = 0
+    for j, s in enumerate(b.specs):
+        dh, fl = oracle_job(b, j, ne)
+        got = b.job_output(j).cpu().numpy().reshape(s.M, -1)
+        assert (got == dh).all(), f"job {j} ({s})"
+        if fl is not None:
+            gf = unpack_flags(b.job_flags(j).cpu().numpy(), 1, s.positions_out)[0]
+            assert (gf == fl).all() and (gf == B.expected_flags(b, j)).all(), f"job {j} flags"
+            total += int(fl.sum())
+    assert int(b.nflag.item()) == total == len(b.faults["pos"])
+    out_t, fl_t = b.out.clone(), b.flags.clone()
+    # the tensor tiles give the same bits
+    b.plan(B.default_config(ntt_min_n=0))
+    b.run()
+    torch.cuda.synchronize()
+    assert torch.equal(b.out, out_t) and torch.equal(b.flags, fl_t)
+    # and so does a graph replay of the transform plan
+    b.plan(B.default_config(ntt_min_n=512))
+    b.capture()
+    b.out.fill_(0)
+    b.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(b.out, out_t) and torch.equal(b.flags, fl_t)
+
+
 def test_batch_equals_each_job_alone_and_direct_results(mods):
     B, ne = mods
     b = B.Batch(small_specs(B, ne), seed=5)
