@@ -879,11 +879,15 @@ def run_batch(args, rank, world, local_rank):
     peak = peak_ops / (p0.elapsed_time(p1) * 1e-3) / 1e12
     run_ms = statistics.median(op_ms)
     achieved = info.mma_ops / (run_ms * 1e-3) / 1e12
-    roof = {"bound": "tensor", "kernel": "ne_batch_run (entangle launch + persistent operation launch)",
+    roof = {"bound": "tensor", "kernel": "ne_batch_run (entangle launch + persistent operation launch"
+                                          + (" + transform launches" if info.ntransform else "") + ")",
             "achieved": achieved, "peak": peak, "unit": "TOP/s", "frac": achieved / peak, "traffic": None,
             "peak_source": "measured in this run: mma.sync.m16n8k32 s8 register-resident probe",
-            "algorithmic": f"{info.mma_ops} int8 ops per run (2 x multiply-adds of all tiles incl. edge padding)",
-            "ms_per_launch": run_ms}
+            "algorithmic": f"{info.mma_ops} int8 ops per run (2 x multiply-adds of all tiles incl. edge padding)"
+                           + (f"; the {info.ntransform} convolutions on the exact-transform path add no tensor "
+                              "work and are not counted, so this fraction understates the tiles' own"
+                              if info.ntransform else ""),
+            "ms_per_launch": run_ms, "transform_jobs": int(info.ntransform)}
     # e2e: inputs from pinned host memory, outputs and flags back, through the graph
     c_host = b.c.cpu().pin_memory()
     ops_host = b.ops.cpu().pin_memory()

@@ -198,14 +198,14 @@ __global__ void __launch_bounds__(256) k_load(const NttAnyArgs a) {
     }
 }
 
-// one butterfly stage of half-span h = L >> (s + 1) over the workspace, for
-// every job with L > LB (forward DIF or inverse DIT)
+// one butterfly stage over the workspace for every job with L > LB: forward
+// DIF with half-span h = L >> (s + 1), inverse DIT with h = LB << s
 template <bool INV>
 __global__ void __launch_bounds__(256) k_stage(const NttAnyArgs a, int s) {
     for (int64_t b = blockIdx.y; b < a.jobs.njobs; b += gridDim.y) {
         const NJob j = job_of(a.jobs, b);
         if (j.L <= LB || s >= j.logL - LOGB) continue;
-        const int h = INV ? (LB << (j.logL - LOGB - 1 - s)) : (j.L >> (s + 1));
+        const int h = INV ? (LB << s) : (j.L >> (s + 1));     // inverse: spans grow, forward: they shrink
         const int64_t half = j.L / 2;
         const int64_t units = (int64_t)(j.M + 1) * 2 * half;
         for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < units; u += (int64_t)gridDim.x * blockDim.x) {
