@@ -49,6 +49,23 @@ def test_mix_equals_alone_and_oracle(mods, rate, lanes, max_batch, budget):
         assert (srv.outputs[rq.idx] == _direct(ne, srv, rq)).all(), f"request {rq.idx} ({rq.spec})"
 
 
+def test_transform_path_in_the_mix_equals_the_tensor_path_alone(mods):
+    # convolutions of N >= 1024 run as exact transforms in the mix; alone they run on tensor tiles
+    B, ne, S = mods
+    specs = B.mixed_jobs(23, 40, mnk=(16, 192), conv=(64, 4096), recover_frac=0.15)
+    specs += S.plain_copy(B.mixed_jobs(24, 6, mnk=(16, 64), conv=(1024, 4096)))
+    srv = S.Server(budget_bytes=256 << 20, lanes=3, max_batch=8, keep_outputs=True, host_pool_elems=1 << 22,
+                   cfg=B.default_config(ntt_min_n=1024))
+    reqs = srv.run(specs, S.poisson_arrivals(4, len(specs), 20000.0), seed=6)
+    assert srv.pool.used == 0 and srv.flagged == 0
+    alone = S.Server(budget_bytes=256 << 20, lanes=1, keep_outputs=True, host_pool_elems=1 << 22)
+    for rq in reqs:
+        alone.outputs.clear()
+        alone.run([rq.spec], np.zeros(1), offsets=[(rq.c_pool, rq.op_pool)])
+        assert (alone.outputs[0] == srv.outputs[rq.idx]).all(), f"request {rq.idx}: transform mix differs"
+        assert (srv.outputs[rq.idx] == _direct(ne, srv, rq)).all(), f"request {rq.idx} ({rq.spec})"
+
+
 def test_plain_path_computes_the_plain_operation(mods):
     B, ne, S = mods
     specs = S.plain_copy(B.mixed_jobs(22, 16, mnk=(16, 192), conv=(64, 4096)))
