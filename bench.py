@@ -76,6 +76,7 @@ def parse():
     ap.add_argument("--jobs", type=int, default=2048, help="jobs of the ragged batch workload")
     ap.add_argument("--no-extras", action="store_true", help="skip overhead, ABFT and CPU-baseline legs")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target length of the CPU-baseline sample")
+    ap.add_argument("--split", action="store_true", help="batch: also time each class of jobs on its own")
     a = ap.parse_args()
     if a.steps is None:
         a.steps = {"cconv": 400, "cconv_ntt": 400, "gemm": 20, "gemm64": 2000, "batch": 10, "serve": 1}[a.workload]
@@ -473,23 +474,23 @@ def run_ours(args, rank, world, local_rank):
         hybrid = wl.name == "cconv" and os.environ.get("NE_CCONV_HYBRID", "") != "0"
         peak_mixed = {}
         if hybrid:
-            # both int8 pipes in the convolution kernel's warp layout (8 tensor + 2 dp4a warps,
+            # both int8 pipes in the convolution kernel's warp layout (8 tensor + 4 dp4a warps,
             # 3 blocks per SM), swept over the share of the work given to dp4a; the ceiling
             # is the best split (the kernel gives dp4a 6 of 16 output blocks, 3/8)
-            I = 2048
+            I, DW = 2048, 4
             for num, den in ((0, 1), (1, 8), (1, 4), (3, 8), (1, 2)):
-                idp = (128 * I * num) // (den - num)
-                ne.ne_probe_mixed_peak(16, (128 * 16 * num) // (den - num), 8, 2, 3)
+                idp = (256 * I * num) // (DW * (den - num))
+                ne.ne_probe_mixed_peak(16, (256 * 16 * num) // (DW * (den - num)), 8, DW, 3)
                 e0.record(stream)
-                ops = ne.ne_probe_mixed_peak(I, idp, 8, 2, 3)
+                ops = ne.ne_probe_mixed_peak(I, idp, 8, DW, 3)
                 e1.record(stream)
                 torch.cuda.synchronize()
                 peak_mixed[f"{num}/{den}"] = ops / (e0.elapsed_time(e1) * 1e-3) / 1e12
         peak = max(peak_mixed.values()) if hybrid else peak_mma
         src = ("measured in this run: mma.sync.m16n8k32 s8 register-resident probe (ne_probe_mma_peak)"
-               + ("; the kernel splits each group between the two int8 pipes (10 of 16 blocks on the tensor "
-                  "pipe, 6 on dp4a), so the peak is the best of ne_probe_mixed_peak (both pipes in the "
-                  "kernel's warp layout) over the dp4a work shares in peak_mixed" if hybrid else "")
+               + ("; the kernel splits each group between the two int8 pipes (10 of 16 blocks on 8 tensor "
+                  "warps, 6 on 4 dp4a warps), so the peak is the best of ne_probe_mixed_peak (both pipes in "
+                  "the kernel's warp layout) over the dp4a work shares in peak_mixed" if hybrid else "")
                + "; MEASURED_PEAKS.json has no int8 figure and sm_103a has no tcgen05 integer MMA")
         roof = {"bound": "tensor", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "TOP/s",
                 "frac": achieved / peak, "traffic": traffic_for(dominant, dom_src), "peak_source": src,
@@ -854,6 +855,42 @@ def gemm_extras(torch, ne, wl, dev, flush, p, dg, planes, Gm, out, ms_step):
                    "abft_rc_encode_and_check_alone": t_rco / K}}
 
 
+def batch_split(B, ne, torch, specs, cfg, dev):
+    """Each class of the batch's jobs as a batch of its own (same configuration):
+    products by size, short convolutions on tiles, long convolutions on the
+    transform path and, for comparison, on tiles."""
+    thr = cfg.ntt_min_n if cfg.ntt_min_n > 0 else 8192
+    gemm = [s for s in specs if s.kind == ne.NE_JOB_GEMM]
+    classes = [("products", gemm, cfg.ntt_min_n)]
+    for lo, hi in ((0, 1e7), (1e7, 1e8), (1e8, 1e13)):
+        classes.append((f"products mnk in [{lo:.0e}, {hi:.0e})",
+                        [s for s in gemm if lo <= s.rows * s.cols * s.k < hi], cfg.ntt_min_n))
+    short = [s for s in specs if s.kind == ne.NE_JOB_CCONV and s.N < thr]
+    long_ = [s for s in specs if s.kind == ne.NE_JOB_CCONV and s.N >= thr]
+    classes += [(f"convolutions N < {thr}", short, cfg.ntt_min_n), (f"convolutions N >= {thr}, transforms", long_, thr),
+                (f"convolutions N >= {thr}, tiles", long_, 0)]
+    out = {}
+    for name, sp, ntt in classes:
+        if not sp:
+            continue
+        bb = B.Batch(sp, seed=0, device=dev)
+        c2 = B.default_config(**{**B.config_dict(cfg), "ntt_min_n": ntt})
+        bb.plan(c2)
+        bb.run()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(3):
+            bb.run()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 3
+        out[name] = {"jobs": len(sp), "ms": ms, "useful_Tops": bb.useful_ops() / ms / 1e9,
+                     "tile_TOPs": bb.info.mma_ops / ms / 1e9, "transform_jobs": int(bb.info.ntransform)}
+        del bb
+    return out
+
+
 def run_batch(args, rank, world, local_rank):
     """The ragged batch: 2048 jobs (M in {3,4,5}; half products m,n,k in
     [32, 2048], half circular convolutions N in [2^8, 2^16]), one bit flip per
@@ -956,6 +993,7 @@ def run_batch(args, rank, world, local_rank):
     e2e = {"value": useful * world / (e2e_ms * 1e-3) / 1e9, "unit": "Gop/s", "ms_per_step": e2e_ms,
            "h2d_bytes_per_step": int(b.c.numel() * 4 + b.ops.numel()),
            "d2h_bytes_per_step": int(b.out.numel() * 8 + b.flags.numel() * 4)}
+    split = batch_split(B, ne, torch, specs, cfg, dev) if args.split else None
     cpu = None
     if not args.no_extras and rank == 0:
         import oracle
@@ -991,11 +1029,15 @@ def run_batch(args, rank, world, local_rank):
                 "data": "synthetic",
                 "config": {"workload": f"ragged batch: {len(specs)} jobs (M in 3..5; half GEMMs m,n,k log-uniform "
                                        f"in [32,2048], half circular convolutions N log-uniform in [2^8,2^16]); "
-                                       "one bit flip per 1e4 output words; one persistent launch under a CUDA graph",
+                                       "one bit flip per 1e4 output words; under a CUDA graph: one entangle launch, "
+                                       "one persistent tile launch and, for the convolutions the autotuner sends to "
+                                       "the exact transforms, the transform launches",
                            "jobs": len(specs), "tiles": info.ntiles, "autotuned": B.config_dict(cfg),
                            "l2": "inputs of several GB, far larger than L2", "parallelism": f"replicas x{world}"},
                 "jobs_per_s": len(specs) * world / (ms * 1e-3), "detection": detection, "roofline": roof,
-                "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": 2 * K,
+                "split_by_job_class": split,
+                "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "gpu_launches": K * (2 + (6 + 2 * max(0, info.ntt_max_logL - 14) if info.ntransform else 0)),
                 "autotune_trials": trials}
         print(json.dumps(line), flush=True)
 

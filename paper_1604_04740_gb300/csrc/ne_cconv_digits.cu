@@ -74,7 +74,8 @@ __global__ void __launch_bounds__(cconv::THREADS, (NTW <= 6 ? 4 : (NTW <= 10 ? 3
 
 // The hybrid tile (tensor pipe + dp4a pipe) for groups of 9..16 blocks.
 template <int MT, int MSC, int HW, int R, bool RAW>
-__global__ void __launch_bounds__(cconv::hybrid_threads(HW), 3) k_cconv_digits_hybrid(CconvArgs a, int64_t b_off) {
+__global__ void __launch_bounds__(cconv::hybrid_threads(HW), cconv::hybrid_threads(HW) <= 384 ? 3 : 2)
+    k_cconv_digits_hybrid(CconvArgs a, int64_t b_off) {
     extern __shared__ __align__(128) uint8_t smem[];
     const int64_t b = b_off + blockIdx.y;
     const int64_t N = a.N;
@@ -125,20 +126,21 @@ ne_status launch_hybrid(const CconvArgs& a, int64_t batch, cudaStream_t s) {
 }
 
 // Split of a group between the tensor pipe and the dp4a pipe.  Default for
-// groups of 16 blocks (the fastest splits measured on GB300 at 3 CTAs per
-// SM, 4096 groups, N = 1024): 6 planes (M = 3, two digits) put 6 blocks on 2
-// dp4a warps (variant 26, 3/8 of the work -- the best split of the two-pipe
-// probe as well); 8 planes put 4 blocks on them (variant 24; 26 would spill).
+// groups of 16 blocks (the fastest splits measured on GB300, 4096 groups,
+// N = 1024): 6 planes (M = 3, two digits) put 6 blocks on 4 dp4a warps of 3
+// outputs per thread (variant 43, 3/8 of the work -- the best split of the
+// two-pipe probe as well; 0.303 ms against 0.319 ms with 2 warps of 6);
+// 8 planes put 4 blocks on 2 warps (variant 24, 0.392 ms; 43: 0.412 ms).
 // NE_CCONV_HYBRID overrides: "0" tensor pipe only; "HR" H dp4a warps of R
-// outputs per thread (H * R / 2 blocks on dp4a), one of 22..26, 42, for any
-// group of at most 16 blocks.
+// outputs per thread (H * R / 2 blocks on dp4a), one of 22..26, 34, 42..44,
+// 52, 62, for any group of at most 16 blocks.
 int hybrid_variant(int64_t NB, int MS) {
     static int v = -2;
     if (v == -2) {
         const char* e = getenv("NE_CCONV_HYBRID");
         v = e ? atoi(e) : -1;
     }
-    if (v == -1) return NB == 16 ? (MS == 6 ? 26 : 24) : 0;
+    if (v == -1) return NB == 16 ? (MS == 6 ? 43 : 24) : 0;
     return v;
 }
 
@@ -151,6 +153,11 @@ ne_status launch_hybrid_variant(int var, const CconvArgs& a, int64_t batch, cuda
         case 25: return launch_hybrid<MT, MSC, 2, 5, RAW>(a, batch, s);
         case 26: return launch_hybrid<MT, MSC, 2, 6, RAW>(a, batch, s);
         case 42: return launch_hybrid<MT, MSC, 4, 2, RAW>(a, batch, s);
+        case 34: return launch_hybrid<MT, MSC, 3, 4, RAW>(a, batch, s);
+        case 43: return launch_hybrid<MT, MSC, 4, 3, RAW>(a, batch, s);
+        case 44: return launch_hybrid<MT, MSC, 4, 4, RAW>(a, batch, s);
+        case 52: return launch_hybrid<MT, MSC, 5, 2, RAW>(a, batch, s);
+        case 62: return launch_hybrid<MT, MSC, 6, 2, RAW>(a, batch, s);
         default: return NE_EINVAL;
     }
 }
