@@ -442,7 +442,8 @@ typedef struct {               /* what ne_batch_run needs to know on the host   
     int64_t mma_ops;           /* int8 operations the tiles issue (2 x multiply-adds)         */
     int64_t useful_ops;        /* 2 x multiply-adds of the operations on the raw streams      */
     int32_t ntransform;        /* jobs on the transform path                                  */
-    int32_t ntt_max_logL, ntt_max_M, pad;
+    int32_t ntt_max_logL, ntt_max_M;
+    int32_t ntt_min_logL;      /* log2 of the shortest transform length among them            */
     int64_t ntt_table_off;     /* byte offsets of the transform jobs' table and scratch       */
     int64_t ntt_ws_off;
     int64_t ntt_units;         /* the largest (M + 1) L of the transform jobs                 */

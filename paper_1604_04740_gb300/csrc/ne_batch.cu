@@ -238,21 +238,26 @@ __device__ __forceinline__ void tile(const TileArgs& a, uint8_t* smem, int row0,
 #pragma unroll
         for (int ks = 0; ks < 2; ks++) {
             const int t0 = 32 * ks;
+            // every unit of a warp has the same column half (units w, w + 8, ...):
+            // its G fragments are loaded once and used by each of its planes
+            uint32_t bf[2][4];
+#pragma unroll
+            for (int nj = 0; nj < 4; nj += 2) {
+                const int n = 32 * (warp & 1) + 8 * (nj + (lane >> 4)) + (lane & 7);
+                ldsm_x4(bf[nj >> 1], Bs_s + (st * BN + n) * RB + t0 + 16 * ((lane >> 3) & 1));
+            }
 #pragma unroll
             for (int i = 0; i < UPW; i++) {
                 const int u = warp + 8 * i;
                 if (u >= 2 * MS) break;
-                const int pl = u >> 1, nh = u & 1;
+                const int pl = u >> 1;
                 if (recover && pl / a.S == a.r) continue;
                 uint32_t af[4];
                 ldsm_x4(af, As_s + ((st * MS + pl) * BM + (lane & 15)) * RB + t0 + 16 * (lane >> 4));
 #pragma unroll
                 for (int nj = 0; nj < 4; nj += 2) {
-                    uint32_t bf[4];
-                    const int n = 32 * nh + 8 * (nj + (lane >> 4)) + (lane & 7);
-                    ldsm_x4(bf, Bs_s + (st * BN + n) * RB + t0 + 16 * ((lane >> 3) & 1));
-                    mma_s8(acc[i][nj], af, bf[0], bf[1]);
-                    mma_s8(acc[i][nj + 1], af, bf[2], bf[3]);
+                    mma_s8(acc[i][nj], af, bf[nj >> 1][0], bf[nj >> 1][1]);
+                    mma_s8(acc[i][nj + 1], af, bf[nj >> 1][2], bf[nj >> 1][3]);
                 }
             }
         }
@@ -471,7 +476,7 @@ extern "C" ne_status ne_batch_plan(const ne_job* jobs, int32_t njobs, ne_batch_c
     std::vector<DevJob> dj((size_t)njobs);
     std::vector<NJob> nj;
     int64_t ntt_ws = 0, ntt_units = 0;
-    int ntt_max_logL = 0, ntt_max_M = 0;
+    int ntt_max_logL = 0, ntt_max_M = 0, ntt_min_logL = 31;
     std::vector<DevTile> tiles;
     std::vector<DevSeg> segs;
     std::vector<int64_t> cost;
@@ -573,6 +578,7 @@ extern "C" ne_status ne_batch_plan(const ne_job* jobs, int32_t njobs, ne_batch_c
             ntt_ws = align256(ntt_ws + (int64_t)(j.M + 1) * 2 * t.L * 4);
             ntt_units = std::max(ntt_units, (int64_t)(j.M + 1) * t.L);
             ntt_max_logL = std::max(ntt_max_logL, lg);
+            ntt_min_logL = std::min(ntt_min_logL, lg);
             ntt_max_M = std::max(ntt_max_M, (int)j.M);
             d.plane_off = plane_bytes;           // no planes
             useful += 2LL * j.M * j.N * j.N;
@@ -623,7 +629,7 @@ extern "C" ne_status ne_batch_plan(const ne_job* jobs, int32_t njobs, ne_batch_c
     info->ntransform = (int32_t)nj.size();
     info->ntt_max_logL = ntt_max_logL;
     info->ntt_max_M = ntt_max_M;
-    info->pad = 0;
+    info->ntt_min_logL = nj.empty() ? 0 : ntt_min_logL;
     info->ntt_table_off = L.ntt_table;
     info->ntt_ws_off = L.ntt_ws;
     info->ntt_units = ntt_units;
@@ -715,7 +721,7 @@ extern "C" ne_status ne_batch_run(ne_batch_info info, const int32_t* c, const in
         a.fault_pos = fault_pos;
         a.fault_stream = fault_stream;
         a.fault_bit = fault_bit;
-        return ntt_any_run(a, info.ntt_max_logL, info.ntt_max_M, info.ntt_units, s);
+        return ntt_any_run(a, info.ntt_min_logL, info.ntt_max_logL, info.ntt_max_M, info.ntt_units, s);
     }
     return NE_OK;
 }

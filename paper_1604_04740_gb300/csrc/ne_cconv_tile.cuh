@@ -348,7 +348,12 @@ __device__ __forceinline__ void tile(const TileArgs& a, uint8_t* smem, int p0, i
 // of the reversed filter per output, from four byte-shifted copies so that
 // every read is aligned and the 32 lanes hit 32 distinct banks.
 __host__ __device__ constexpr int hybrid_threads(int HW) { return THREADS + 32 * HW; }
-constexpr int GDP = 2144;                     // bytes per filter copy: >= 2 * 1024 + 8, = 24 words mod 32
+constexpr int GDP = 2144;                     // bytes per filter copy slot: >= 2 * 1024 + 8 + 68
+constexpr int GDPW = 514;                     // words of a copy the dp4a reads reach: (2 * 1024 + 8) / 4
+// Byte offset of dp4a filter copy rr.  A warp's 32 lanes read through the four
+// copies with 8 consecutive lanes per copy; the extra word offsets 0, 17, 1, 17
+// put the four groups on disjoint sets of 8 banks (with GDP = 24 words mod 32).
+__host__ __device__ constexpr int gdp_off(int rr) { return rr * GDP + 4 * ((rr & 1) ? 17 : (rr == 2 ? 1 : 0)); }
 
 // [digit-plane window + tensor-pipe filter window][dp4a filter copies][stash]:
 // the stash has its own space, so a warp may write its results as soon as it
@@ -397,8 +402,8 @@ __device__ __forceinline__ void tile_hybrid(const TileArgs& a, uint8_t* smem) {
     }
     // dp4a copies: copy rr, byte z holds g[(N + 4 - z - rr) mod N], i.e. the
     // reversed filter at offset y = z + rr - N - 4
-    for (int e = tid; e < 4 * (GDP / 4); e += NTHR) {
-        const int rr = e / (GDP / 4), zw = e - rr * (GDP / 4);
+    for (int e = tid; e < 4 * GDPW; e += NTHR) {
+        const int rr = e / GDPW, zw = e - rr * GDPW;
         uint32_t w = 0;
 #pragma unroll
         for (int k = 0; k < 4; k++) {
@@ -406,7 +411,7 @@ __device__ __forceinline__ void tile_hybrid(const TileArgs& a, uint8_t* smem) {
             if (idx < 0) idx += N;
             w |= (uint32_t)(uint8_t)__ldg(a.g + idx) << (8 * k);
         }
-        *reinterpret_cast<uint32_t*>(gdp + rr * GDP + 4 * zw) = w;
+        *reinterpret_cast<uint32_t*>(gdp + gdp_off(rr) + 4 * zw) = w;
     }
     cp_async_wait<0>();
     __syncthreads();
@@ -466,7 +471,7 @@ __device__ __forceinline__ void tile_hybrid(const TileArgs& a, uint8_t* smem) {
         const int t = tid - THREADS;               // 0 .. DT - 1
         const int i_base = npb * T + t;
         const int rho = (4 - (t & 3)) & 3;         // byte shift of this thread's filter reads
-        const uint32_t gd = smem_u32(gdp) + rho * GDP + N + 4 - rho - i_base;
+        const uint32_t gd = smem_u32(gdp) + gdp_off(rho) + N + 4 - rho - i_base;
         int acc[R][MS];
 #pragma unroll
         for (int r = 0; r < R; r++)

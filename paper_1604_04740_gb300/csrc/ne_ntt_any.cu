@@ -15,15 +15,19 @@
 //
 // Transform.  Radix 2, forward by decimation in frequency (natural order in,
 // bit-reversed out), inverse by decimation in time (bit-reversed in, natural
-// out), so the pointwise products need no reordering.  Stages whose
-// butterflies span more than LB = 2^14 elements run as passes over the
-// workspace (one launch per stage); the remaining 14 stages run in shared
-// memory, one CTA per contiguous block of LB elements.  Twiddles come from a
-// table laid out by stage (entry h + j = the j-th power of the primitive
-// 2h-th root), so the threads of a warp read consecutive entries.  Residues
-// stay below 2P: sums are reduced once per butterfly, differences and
-// twiddle products through Shoup products, pointwise products are Montgomery
-// products with the filter's transform pre-scaled by 2^32 / L.
+// out), so the pointwise products need no reordering.  The G = logL - 14 <= 3
+// stages whose butterflies span more than LB = 2^14 elements run in one pass
+// over the workspace per direction, 2^G elements per thread in registers (the
+// forward pass also forms the words from the inputs).  The 14 stages inside
+// a block of LB elements run in one CTA of 512 threads holding 32 elements
+// each in registers, in three groups of 5, 5 and 4 stages with two exchanges
+// through shared memory; shorter transforms (L < LB) run radix 2 in shared
+// memory.  Twiddles come from a table laid out by stage (entry h + j = the
+// j-th power of the primitive 2h-th root), so the threads of a warp read
+// consecutive entries.  Residues stay below 2P: sums are reduced once per
+// butterfly, differences and twiddle products through Shoup products,
+// pointwise products are Montgomery products with the filter's transform
+// pre-scaled by 2^32 / L.
 #include <mutex>
 
 #include "ne_common.cuh"
@@ -159,90 +163,336 @@ __device__ __forceinline__ uint32_t* plane_ptr(const NttAnyArgs& a, const NJob& 
     return a.ws + j.ws_off + ((int64_t)p * 2 + q) * j.L;
 }
 
-// words of Eq. 16 (or the raw values) and the filter, both primes, zero padded
-__global__ void __launch_bounds__(256) k_load(const NttAnyArgs a) {
+__device__ __forceinline__ Tw twiddle(const Tw* tw, int idx) {
+    const uint2 v = __ldg(reinterpret_cast<const uint2*>(tw) + idx);
+    return Tw{v.x, v.y};
+}
+
+// DIF butterfly (u, v) -> (u + v, (u - v) w); ONE: w = 1.  Inputs and outputs below 2P.
+template <bool ONE = false>
+__device__ __forceinline__ void bf_dif(uint32_t& u, uint32_t& v, Tw w, uint32_t P) {
+    const uint32_t a = u, b = v;
+    u = red2(a + b, P);
+    v = ONE ? red2(a + 2u * P - b, P) : mul_shoup(a + 2u * P - b, w.w, w.q, P);
+}
+
+// DIT butterfly (u, v) -> (u + v w, u - v w); ONE: w = 1.
+template <bool ONE = false>
+__device__ __forceinline__ void bf_dit(uint32_t& u, uint32_t& v, Tw w, uint32_t P) {
+    const uint32_t t = ONE ? v : mul_shoup(v, w.w, w.q, P);
+    const uint32_t a = u;
+    u = red2(a + t, P);
+    v = red2(a + 2u * P - t, P);
+}
+
+// the residue of the word of stream p (Eq. 16, or the raw value) or of the
+// filter (p = M) at position i < N, modulo both primes; *worst tracks the range
+template <bool FILTER>
+__device__ __forceinline__ void load_residues(const NttAnyArgs& a, const NJob& j, int p, int64_t i, uint32_t& r0,
+                                              uint32_t& r1, uint32_t& worst) {
+    if (!FILTER) {
+        const int32_t x = __ldg(a.c + j.c_off + (int64_t)p * j.N + i);
+        worst = max(worst, (uint32_t)x - (uint32_t)j.lo);
+        int64_t e = x;
+        if (!j.plain) {
+            const int mp = p == 0 ? j.M - 1 : p - 1;
+            e = entangle_word(x, __ldg(a.c + j.c_off + (int64_t)mp * j.N + i), j.l);
+        }
+        // |e| < 2^41: shift into [0, 2^42) by a multiple of both primes, then reduce
+        r0 = (uint32_t)((uint64_t)(e + (int64_t)prime(0) * (int64_t)(1 << 22)) % prime(0));
+        r1 = (uint32_t)((uint64_t)(e + (int64_t)prime(1) * (int64_t)(1 << 22)) % prime(1));
+    } else {
+        const int d = __ldg(a.g + j.g_off + i);
+        r0 = (uint32_t)(d + (int)prime(0));
+        r1 = (uint32_t)(d + (int)prime(1));
+    }
+}
+
+// One unit of the forward pass: the 2^G elements base + k Q (Q = L >> G) of
+// plane p, loaded from the inputs, then the G outermost DIF stages (half-spans
+// L/2 .. Q) in registers, both primes.
+template <int G>
+__device__ __forceinline__ void gfwd_unit(const NttAnyArgs& a, const NJob& j, int p, int base, uint32_t& worst) {
+    constexpr int E = 1 << G;
+    const int Q = j.L >> G;
+    uint32_t r[2][E];
+#pragma unroll
+    for (int k = 0; k < E; k++) {
+        const int64_t i = base + (int64_t)k * Q;
+        r[0][k] = r[1][k] = 0;
+        if (i < j.N) {
+            if (p < j.M) load_residues<false>(a, j, p, i, r[0][k], r[1][k], worst);
+            else load_residues<true>(a, j, p, i, r[0][k], r[1][k], worst);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 2; q++) {
+        const uint32_t P = prime(q);
+        const Tw* tw = g_tw[q][0];
+#pragma unroll
+        for (int s = 0; s < G; s++) {
+            const int d = E >> (s + 1);                  // half-span Q d
+#pragma unroll
+            for (int k = 0; k < E; k++) {
+                if (k & d) continue;
+                bf_dif(r[q][k], r[q][k + d], twiddle(tw, Q * d + base + Q * (k & (d - 1))), P);
+            }
+        }
+        uint32_t* x = plane_ptr(a, j, p, q);
+#pragma unroll
+        for (int k = 0; k < E; k++) x[base + (int64_t)k * Q] = r[q][k];
+    }
+}
+
+// The words of Eq. 16 (or the raw values) and the filter, modulo both primes,
+// zero padded to L, with the stages whose butterflies span more than LB
+// elements (G = logL - 14 <= 3 of them) done in the same pass.
+__global__ void __launch_bounds__(256) k_gfwd(const NttAnyArgs a) {
     for (int64_t b = blockIdx.y; b < a.jobs.njobs; b += gridDim.y) {
         const NJob j = job_of(a.jobs, b);
         if (j.L == 0) continue;
-        const int64_t units = (int64_t)(j.M + 1) * j.L;
+        const int G = j.logL > LOGB ? j.logL - LOGB : 0;
+        const int Q = j.L >> G;
+        const int64_t units = (int64_t)(j.M + 1) * Q;
         uint32_t worst = 0;
         for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < units; u += (int64_t)gridDim.x * blockDim.x) {
-            const int p = (int)(u / j.L);
-            const int i = (int)(u - (int64_t)p * j.L);
+            const int p = (int)(u / Q);
+            const int base = (int)(u - (int64_t)p * Q);
             if (p < j.M && j.fuse == NE_FUSE_RECOVER && p == j.r) continue;   // never computed
-            uint32_t r0 = 0, r1 = 0;
-            if (i < j.N) {
-                if (p < j.M) {
-                    const int32_t x = __ldg(a.c + j.c_off + (int64_t)p * j.N + i);
-                    worst = max(worst, (uint32_t)x - (uint32_t)j.lo);
-                    int64_t e = x;
-                    if (!j.plain) {
-                        const int mp = p == 0 ? j.M - 1 : p - 1;
-                        e = entangle_word(x, __ldg(a.c + j.c_off + (int64_t)mp * j.N + i), j.l);
-                    }
-                    // |e| < 2^41: shift into [0, 2^42) by a multiple of both primes, then reduce
-                    const uint64_t shifted0 = (uint64_t)(e + (int64_t)prime(0) * (int64_t)(1 << 22));
-                    const uint64_t shifted1 = (uint64_t)(e + (int64_t)prime(1) * (int64_t)(1 << 22));
-                    r0 = (uint32_t)(shifted0 % prime(0));
-                    r1 = (uint32_t)(shifted1 % prime(1));
-                } else {
-                    const int d = __ldg(a.g + j.g_off + i);
-                    r0 = (uint32_t)(d + (int)prime(0));
-                    r1 = (uint32_t)(d + (int)prime(1));
-                }
+            switch (G) {
+                case 0: gfwd_unit<0>(a, j, p, base, worst); break;
+                case 1: gfwd_unit<1>(a, j, p, base, worst); break;
+                case 2: gfwd_unit<2>(a, j, p, base, worst); break;
+                default: gfwd_unit<3>(a, j, p, base, worst); break;
             }
-            plane_ptr(a, j, p, 0)[i] = r0;
-            plane_ptr(a, j, p, 1)[i] = r1;
         }
         if (worst > (uint32_t)j.hi - (uint32_t)j.lo && a.status) atomicExch(a.status, (int32_t)NE_ERANGE);
     }
 }
 
-// one butterfly stage over the workspace for every job with L > LB: forward
-// DIF with half-span h = L >> (s + 1), inverse DIT with h = LB << s
-template <bool INV>
-__global__ void __launch_bounds__(256) k_stage(const NttAnyArgs a, int s) {
+// The inverse stages spanning more than LB elements (half-spans Q .. L/2,
+// DIT) for the 2^G elements base + k Q of one plane and prime, in registers.
+template <int G>
+__device__ __forceinline__ void ginv_unit(const NttAnyArgs& a, const NJob& j, int p, int q, int base) {
+    constexpr int E = 1 << G;
+    const int Q = j.L >> G;
+    const uint32_t P = prime(q);
+    const Tw* tw = g_tw[q][1];
+    uint32_t* x = plane_ptr(a, j, p, q);
+    uint32_t r[E];
+#pragma unroll
+    for (int k = 0; k < E; k++) r[k] = x[base + (int64_t)k * Q];
+#pragma unroll
+    for (int s = 0; s < G; s++) {
+        const int d = 1 << s;
+#pragma unroll
+        for (int k = 0; k < E; k++) {
+            if (k & d) continue;
+            bf_dit(r[k], r[k + d], twiddle(tw, Q * d + base + Q * (k & (d - 1))), P);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < E; k++) x[base + (int64_t)k * Q] = r[k];
+}
+
+__global__ void __launch_bounds__(256) k_ginv(const NttAnyArgs a) {
     for (int64_t b = blockIdx.y; b < a.jobs.njobs; b += gridDim.y) {
         const NJob j = job_of(a.jobs, b);
-        if (j.L <= LB || s >= j.logL - LOGB) continue;
-        const int h = INV ? (LB << s) : (j.L >> (s + 1));     // inverse: spans grow, forward: they shrink
-        const int64_t half = j.L / 2;
-        const int64_t units = (int64_t)(j.M + 1) * 2 * half;
+        if (j.L <= LB) continue;
+        const int G = j.logL - LOGB;
+        const int64_t units = (int64_t)j.M * 2 * LB;
         for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < units; u += (int64_t)gridDim.x * blockDim.x) {
-            const int pq = (int)(u / half);
-            const int64_t t = u - (int64_t)pq * half;
+            const int pq = (int)(u >> LOGB);
+            const int base = (int)(u & (LB - 1));
             const int p = pq >> 1, q = pq & 1;
-            if (INV && p == j.M) continue;                                  // the filter has no inverse
-            if (p < j.M && j.fuse == NE_FUSE_RECOVER && p == j.r) continue;
-            const uint32_t P = prime(q);
-            uint32_t* x = plane_ptr(a, j, p, q);
-            const int jj = (int)(t & (h - 1));
-            const int64_t i0 = ((t - jj) << 1) + jj, i1 = i0 + h;
-            const Tw w = g_tw[q][INV ? 1 : 0][h + jj];
-            const uint32_t u0 = x[i0], v0 = x[i1];
-            if (!INV) {
-                x[i0] = red2(u0 + v0, P);
-                x[i1] = mul_shoup(u0 + 2u * P - v0, w.w, w.q, P);
-            } else {
-                const uint32_t v = mul_shoup(v0, w.w, w.q, P);
-                x[i0] = red2(u0 + v, P);
-                x[i1] = red2(u0 + 2u * P - v, P);
+            if (j.fuse == NE_FUSE_RECOVER && p == j.r) continue;
+            switch (G) {
+                case 1: ginv_unit<1>(a, j, p, q, base); break;
+                case 2: ginv_unit<2>(a, j, p, q, base); break;
+                default: ginv_unit<3>(a, j, p, q, base); break;
             }
         }
     }
 }
 
-// the stages within one block of B = min(L, LB) elements, in shared memory
-// (forward: half-spans B/2 .. 1; inverse: the pointwise product with the
-// filter first, then half-spans 1 .. B/2)
+// ---- the 14 innermost stages of a block of LB = 2^14 elements ---------------------------------
+//
+// 512 threads hold 32 elements each in registers and run the stages in three
+// groups, exchanging through shared memory between groups: index bits 13..9
+// (element t + 512 k of thread t), bits 8..4 (element 512 hi + 16 k + lo of
+// thread 16 hi + lo) and bits 3..0 (rows 16 g + kk, g = t and t + 512).  The
+// word of element i in shared memory is swz(i), chosen so that each of the
+// three patterns reads and writes 32 distinct banks per warp (the first but
+// for one pair of lanes).
+
+constexpr int RTHREADS = 512;
+__host__ __device__ constexpr int swz(int i) { return i + (i >> 4) + 16 * (i >> 9); }
+constexpr int RSMEM_WORDS = swz(LB - 1) + 1;
+
+// bits 13..9: half-spans 512 d, d = 16 .. 1 (DIF) or 1 .. 16 (DIT)
+template <bool INV>
+__device__ __forceinline__ void stages_hi(uint32_t (&r)[32], const Tw* tw, int t, uint32_t P) {
+#pragma unroll
+    for (int s = 0; s < 5; s++) {
+        const int d = INV ? (1 << s) : (16 >> s);
+#pragma unroll
+        for (int k = 0; k < 32; k++) {
+            if (k & d) continue;
+            const Tw w = twiddle(tw, 512 * d + t + 512 * (k & (d - 1)));
+            if (INV) bf_dit(r[k], r[k + d], w, P);
+            else bf_dif(r[k], r[k + d], w, P);
+        }
+    }
+}
+
+// bits 8..4: half-spans 16 d
+template <bool INV>
+__device__ __forceinline__ void stages_mid(uint32_t (&r)[32], const Tw* tw, int lo, uint32_t P) {
+#pragma unroll
+    for (int s = 0; s < 5; s++) {
+        const int d = INV ? (1 << s) : (16 >> s);
+#pragma unroll
+        for (int k = 0; k < 32; k++) {
+            if (k & d) continue;
+            const Tw w = twiddle(tw, 16 * d + 16 * (k & (d - 1)) + lo);
+            if (INV) bf_dit(r[k], r[k + d], w, P);
+            else bf_dif(r[k], r[k + d], w, P);
+        }
+    }
+}
+
+// bits 3..0 of two rows of 16: half-spans d = 8 .. 1 (DIF) or 1 .. 8 (DIT);
+// the first butterfly of every span has twiddle 1
+template <bool INV>
+__device__ __forceinline__ void stages_lo(uint32_t (&r)[32], const Tw* tw, uint32_t P) {
+#pragma unroll
+    for (int s = 0; s < 4; s++) {
+        const int d = INV ? (1 << s) : (8 >> s);
+#pragma unroll
+        for (int kk = 0; kk < 16; kk++) {
+            if (kk & d) continue;
+            const int jj = kk & (d - 1);
+            if (jj == 0) {
+#pragma unroll
+                for (int row = 0; row < 2; row++) {
+                    if (INV) bf_dit<true>(r[16 * row + kk], r[16 * row + kk + d], Tw{1u, 0u}, P);
+                    else bf_dif<true>(r[16 * row + kk], r[16 * row + kk + d], Tw{1u, 0u}, P);
+                }
+            } else {
+                const Tw w = twiddle(tw, d + jj);
+#pragma unroll
+                for (int row = 0; row < 2; row++) {
+                    if (INV) bf_dit(r[16 * row + kk], r[16 * row + kk + d], w, P);
+                    else bf_dif(r[16 * row + kk], r[16 * row + kk + d], w, P);
+                }
+            }
+        }
+    }
+}
+
+// Forward (DIF, natural order in, bit-reversed out; the filter plane scaled by
+// 2^32 / L, fully reduced) or inverse (pointwise product with the filter's
+// transform, then DIT) of every LB-block of the jobs with L >= LB.
+template <bool INV>
+__global__ void __launch_bounds__(RTHREADS, 2) k_block_r(const NttAnyArgs a) {
+    extern __shared__ uint32_t sx[];
+    const int t = threadIdx.x;
+    const int hi = t >> 4, lo = t & 15;
+    for (int64_t b = blockIdx.y; b < a.jobs.njobs; b += gridDim.y) {
+        const NJob j = job_of(a.jobs, b);
+        if (j.L < LB) continue;
+        const int nblk = j.L >> LOGB;
+        const int planes = INV ? j.M : j.M + 1;
+        for (int unit = blockIdx.x; unit < planes * 2 * nblk; unit += gridDim.x) {
+            const int blk = unit % nblk, pq = unit / nblk;
+            const int p = pq >> 1, q = pq & 1;
+            if (p < j.M && j.fuse == NE_FUSE_RECOVER && p == j.r) continue;
+            const uint32_t P = prime(q);
+            const Tw* tw = g_tw[q][INV ? 1 : 0];
+            uint32_t* x = plane_ptr(a, j, p, q) + (int64_t)blk * LB;
+            uint32_t r[32];
+            if (!INV) {
+#pragma unroll
+                for (int k = 0; k < 32; k++) r[k] = x[t + 512 * k];
+                stages_hi<false>(r, tw, t, P);
+#pragma unroll
+                for (int k = 0; k < 32; k++) sx[swz(t + 512 * k)] = r[k];
+                __syncthreads();
+#pragma unroll
+                for (int k = 0; k < 32; k++) r[k] = sx[swz(512 * hi + 16 * k + lo)];
+                stages_mid<false>(r, tw, lo, P);
+#pragma unroll
+                for (int k = 0; k < 32; k++) sx[swz(512 * hi + 16 * k + lo)] = r[k];
+                __syncthreads();
+#pragma unroll
+                for (int row = 0; row < 2; row++)
+#pragma unroll
+                    for (int kk = 0; kk < 16; kk++) r[16 * row + kk] = sx[swz(16 * (t + 512 * row) + kk)];
+                stages_lo<false>(r, tw, P);
+                if (p == j.M) {
+                    // a Montgomery product with the scaled filter transform multiplies by G / L
+                    const uint32_t pneg = neg_inv(P), gs = q ? j.gscale[1] : j.gscale[0];
+#pragma unroll
+                    for (int k = 0; k < 32; k++) r[k] = red1(mont(r[k], gs, P, pneg), P);
+                }
+#pragma unroll
+                for (int row = 0; row < 2; row++) {
+                    uint4* dst = reinterpret_cast<uint4*>(x + 16 * (t + 512 * row));
+#pragma unroll
+                    for (int v = 0; v < 4; v++)
+                        dst[v] = make_uint4(r[16 * row + 4 * v], r[16 * row + 4 * v + 1], r[16 * row + 4 * v + 2],
+                                            r[16 * row + 4 * v + 3]);
+                }
+            } else {
+                const uint32_t* gm = plane_ptr(a, j, j.M, q) + (int64_t)blk * LB;
+                const uint32_t pneg = neg_inv(P);
+#pragma unroll
+                for (int row = 0; row < 2; row++) {
+                    const uint4* src = reinterpret_cast<const uint4*>(x + 16 * (t + 512 * row));
+                    const uint4* gsrc = reinterpret_cast<const uint4*>(gm + 16 * (t + 512 * row));
+#pragma unroll
+                    for (int v = 0; v < 4; v++) {
+                        const uint4 xv = src[v], gv = __ldg(gsrc + v);
+                        r[16 * row + 4 * v] = mont(xv.x, gv.x, P, pneg);
+                        r[16 * row + 4 * v + 1] = mont(xv.y, gv.y, P, pneg);
+                        r[16 * row + 4 * v + 2] = mont(xv.z, gv.z, P, pneg);
+                        r[16 * row + 4 * v + 3] = mont(xv.w, gv.w, P, pneg);
+                    }
+                }
+                stages_lo<true>(r, tw, P);
+#pragma unroll
+                for (int row = 0; row < 2; row++)
+#pragma unroll
+                    for (int kk = 0; kk < 16; kk++) sx[swz(16 * (t + 512 * row) + kk)] = r[16 * row + kk];
+                __syncthreads();
+#pragma unroll
+                for (int k = 0; k < 32; k++) r[k] = sx[swz(512 * hi + 16 * k + lo)];
+                stages_mid<true>(r, tw, lo, P);
+#pragma unroll
+                for (int k = 0; k < 32; k++) sx[swz(512 * hi + 16 * k + lo)] = r[k];
+                __syncthreads();
+#pragma unroll
+                for (int k = 0; k < 32; k++) r[k] = sx[swz(t + 512 * k)];
+                stages_hi<true>(r, tw, t, P);
+#pragma unroll
+                for (int k = 0; k < 32; k++) x[t + 512 * k] = r[k];
+            }
+            __syncthreads();        // the next unit reuses sx
+        }
+    }
+}
+
+// all stages of a job with L < LB, radix 2 in shared memory (forward:
+// half-spans L/2 .. 1; inverse: the pointwise product with the filter first,
+// then half-spans 1 .. L/2)
 template <bool INV>
 __global__ void __launch_bounds__(BTHREADS) k_block(const NttAnyArgs a) {
     extern __shared__ uint32_t sx[];
     for (int64_t b = blockIdx.y; b < a.jobs.njobs; b += gridDim.y) {
         const NJob j = job_of(a.jobs, b);
-        if (j.L == 0) continue;
-        const int B = j.L < LB ? j.L : LB;
-        const int nblk = j.L / B;
+        if (j.L == 0 || j.L >= LB) continue;
+        const int B = j.L;
+        const int nblk = 1;
         const int planes = INV ? j.M : j.M + 1;
         for (int unit = blockIdx.x; unit < planes * 2 * nblk; unit += gridDim.x) {
             const int blk = unit % nblk, pq = unit / nblk;
@@ -281,7 +531,7 @@ __global__ void __launch_bounds__(BTHREADS) k_block(const NttAnyArgs a) {
                 // the filter's transform times 2^32 / L, fully reduced: a Montgomery
                 // product with it multiplies by G / L
                 const uint32_t pneg = neg_inv(P);
-                const uint32_t gs = j.gscale[q];
+                const uint32_t gs = q ? j.gscale[1] : j.gscale[0];
                 for (int i = threadIdx.x; i < B; i += blockDim.x) x[i] = red1(mont(sx[i], gs, P, pneg), P);
             } else {
                 for (int i = threadIdx.x; i < B; i += blockDim.x) x[i] = sx[i];
@@ -399,7 +649,8 @@ void ntt_any_job_constants(NJob& j) {
     }
 }
 
-ne_status ntt_any_run(NttAnyArgs& a, int max_logL, int max_M, int64_t max_units_load, cudaStream_t s) {
+ne_status ntt_any_run(NttAnyArgs& a, int min_logL, int max_logL, int max_M, int64_t max_units_load,
+                      cudaStream_t s) {
     ne_status st = ntt_any_init_tables(s);
     if (st) return st;
     const uint32_t inv = ntt2::powmod(ntt2::prime(0) % ntt2::prime(1), ntt2::prime(1) - 2, ntt2::prime(1));
@@ -415,33 +666,44 @@ ne_status ntt_any_run(NttAnyArgs& a, int max_logL, int max_M, int64_t max_units_
         if (want < 1) want = 1;
         return (unsigned)want;
     };
-    ntt2::k_load<<<dim3(gx_for(max_units_load, 256), gy), 256, 0, s>>>(a);
-    if ((st = check_launch("ne_cconv_ntt_any: load"))) return st;
-    const int gstages = max_logL > ntt2::LOGB ? max_logL - ntt2::LOGB : 0;
-    const int64_t half_units = (int64_t)(max_M + 1) * 2 * ((int64_t)1 << (max_logL - 1));
-    for (int sidx = 0; sidx < gstages; sidx++) {
-        ntt2::k_stage<false><<<dim3(gx_for(half_units, 256), gy), 256, 0, s>>>(a, sidx);
-        if ((st = check_launch("ne_cconv_ntt_any: stage"))) return st;
-    }
-    const int B = max_logL < ntt2::LOGB ? (1 << max_logL) : ntt2::LB;
-    const size_t smem = (size_t)B * sizeof(uint32_t);
-    static bool attr[64][2];
+    ntt2::k_gfwd<<<dim3(gx_for(max_units_load, 256), gy), 256, 0, s>>>(a);
+    if ((st = check_launch("ne_cconv_ntt_any: load and outer forward stages"))) return st;
+    static bool attr[64];
     int dev = 0;
     cudaGetDevice(&dev);
-    if (dev >= 0 && dev < 64 && !attr[dev][0]) {
-        cudaFuncSetAttribute(ntt2::k_block<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ntt2::LB * 4);
-        cudaFuncSetAttribute(ntt2::k_block<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ntt2::LB * 4);
-        attr[dev][0] = true;
+    if (dev >= 0 && dev < 64 && !attr[dev]) {
+        cudaFuncSetAttribute(ntt2::k_block<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ntt2::LB / 2 * 4);
+        cudaFuncSetAttribute(ntt2::k_block<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ntt2::LB / 2 * 4);
+        cudaFuncSetAttribute(ntt2::k_block_r<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             ntt2::RSMEM_WORDS * 4);
+        cudaFuncSetAttribute(ntt2::k_block_r<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             ntt2::RSMEM_WORDS * 4);
+        attr[dev] = true;
     }
-    const int nblk = (1 << max_logL) / B;
-    const int fwd_units = (max_M + 1) * 2 * nblk, inv_units = max_M * 2 * nblk;
-    ntt2::k_block<false><<<dim3((unsigned)fwd_units, gy), ntt2::BTHREADS, smem, s>>>(a);
-    if ((st = check_launch("ne_cconv_ntt_any: forward blocks"))) return st;
-    ntt2::k_block<true><<<dim3((unsigned)inv_units, gy), ntt2::BTHREADS, smem, s>>>(a);
-    if ((st = check_launch("ne_cconv_ntt_any: inverse blocks"))) return st;
-    for (int sidx = 0; sidx < gstages; sidx++) {
-        ntt2::k_stage<true><<<dim3(gx_for(half_units, 256), gy), 256, 0, s>>>(a, sidx);
-        if ((st = check_launch("ne_cconv_ntt_any: stage"))) return st;
+    // jobs with L >= LB: register-resident blocks of LB; shorter jobs: one block of L
+    const bool big = max_logL >= ntt2::LOGB, small = min_logL < ntt2::LOGB;
+    const int nblk = big ? (1 << max_logL) / ntt2::LB : 1;
+    const int small_logL = max_logL < ntt2::LOGB ? max_logL : ntt2::LOGB - 1;
+    const size_t rsmem = (size_t)ntt2::RSMEM_WORDS * 4, smem = ((size_t)1 << small_logL) * 4;
+    if (big) {
+        ntt2::k_block_r<false><<<dim3((unsigned)((max_M + 1) * 2 * nblk), gy), ntt2::RTHREADS, rsmem, s>>>(a);
+        if ((st = check_launch("ne_cconv_ntt_any: forward blocks"))) return st;
+    }
+    if (small) {
+        ntt2::k_block<false><<<dim3((unsigned)((max_M + 1) * 2), gy), ntt2::BTHREADS, smem, s>>>(a);
+        if ((st = check_launch("ne_cconv_ntt_any: forward blocks"))) return st;
+    }
+    if (big) {
+        ntt2::k_block_r<true><<<dim3((unsigned)(max_M * 2 * nblk), gy), ntt2::RTHREADS, rsmem, s>>>(a);
+        if ((st = check_launch("ne_cconv_ntt_any: inverse blocks"))) return st;
+    }
+    if (small) {
+        ntt2::k_block<true><<<dim3((unsigned)(max_M * 2), gy), ntt2::BTHREADS, smem, s>>>(a);
+        if ((st = check_launch("ne_cconv_ntt_any: inverse blocks"))) return st;
+    }
+    if (max_logL > ntt2::LOGB) {
+        ntt2::k_ginv<<<dim3(gx_for((int64_t)max_M * 2 * ntt2::LB, 256), gy), 256, 0, s>>>(a);
+        if ((st = check_launch("ne_cconv_ntt_any: outer inverse stages"))) return st;
     }
     const int64_t maxN = (int64_t)1 << max_logL;
     const unsigned fx = gx_for(maxN, 256);
@@ -531,5 +793,5 @@ extern "C" ne_status ne_cconv_ntt_any(ne_params p, int32_t cmin, int32_t cmax, c
     a.fault_pos = nullptr;
     a.fault_stream = nullptr;
     a.fault_bit = nullptr;
-    return ntt_any_run(a, lg, p.M, (int64_t)(p.M + 1) * j.L, s);
+    return ntt_any_run(a, lg, lg, p.M, (int64_t)(p.M + 1) * j.L, s);
 }

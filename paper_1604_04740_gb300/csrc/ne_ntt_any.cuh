@@ -53,7 +53,9 @@ bool ntt_any_exact(int M, int l, int64_t N, int32_t cmax_abs, bool plain);
 void ntt_any_job_constants(NJob& j);
 // twiddle tables (once per device; synchronises s the first time)
 ne_status ntt_any_init_tables(cudaStream_t s);
-// the launches for a set of jobs: max_logL / max_M bound every job's L and M
-ne_status ntt_any_run(NttAnyArgs& a, int max_logL, int max_M, int64_t max_units_load, cudaStream_t s);
+// the launches for a set of jobs: min_logL .. max_logL and max_M bound every
+// job's L and M
+ne_status ntt_any_run(NttAnyArgs& a, int min_logL, int max_logL, int max_M, int64_t max_units_load,
+                      cudaStream_t s);
 
 }  // namespace ne
