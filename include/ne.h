@@ -426,7 +426,7 @@ typedef struct {
 } ne_job;
 
 typedef struct {
-    int32_t ctas_per_sm;       /* resident blocks per SM of the persistent launch (1..4)      */
+    int32_t ctas_per_sm;       /* resident blocks per SM of the convolution-tile launch (1..4) */
     int32_t order;             /* NE_ORDER_JOB or NE_ORDER_LPT                                */
     int32_t cconv_blocks;      /* outputs per convolution tile, in blocks of 64: 4, 8 or 16   */
     int32_t l_policy;          /* NE_L_BYTE or NE_L_SMALLEST for jobs with l = 0              */
@@ -436,7 +436,9 @@ typedef struct {
 } ne_batch_config;
 
 typedef struct {               /* what ne_batch_run needs to know on the host                 */
-    int32_t njobs, ntiles, nsegs, grid;
+    int32_t njobs, ntiles, nsegs, grid;   /* grid: CTAs of the convolution-tile launch  */
+    int32_t ngemm_tiles;       /* the first ngemm_tiles tiles are products (their own launch) */
+    int32_t gemm_grid;         /* CTAs of the product-tile launch                             */
     int64_t flag_words;        /* total check-bitmap words (for clearing)                     */
     int64_t workspace_bytes;   /* device workspace the plan occupies                          */
     int64_t mma_ops;           /* int8 operations the tiles issue (2 x multiply-adds)         */

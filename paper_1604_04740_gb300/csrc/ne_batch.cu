@@ -8,12 +8,13 @@
 //   ne_batch_plan (host): per job l (Eq. 13/14 from the job's bound) and the
 //     digit plan; digit-plane arena layout; entangle segments; operation
 //     tiles (ordered by cost when asked); tables copied to the workspace.
-//   ne_batch_run (device, graph-capturable): clear the tile counter and the
+//   ne_batch_run (device, graph-capturable): clear the tile counters and the
 //     flag bitmaps; one launch entangles every segment into digit planes;
-//     ONE persistent launch: each CTA takes the next tile from an atomic
-//     counter and runs a product tile (16 x 64 outputs, all M*S planes) or
-//     a convolution tile (up to 1024 outputs, all planes, ne_cconv_tile.cuh)
-//     with the fused extract/check or fused recovery of its job.
+//     two persistent launches, one over the product tiles (16 x 64 outputs,
+//     all M*S planes; 3 CTAs per SM) and one over the convolution tiles (up
+//     to 1024 outputs, all planes, ne_cconv_tile.cuh): each CTA takes the
+//     next tile of its list from an atomic counter and runs it with the fused
+//     extract/check or fused recovery of its job.
 //   Long convolutions (N >= the plan's ntt_min_n) skip the tiles and run as
 //     exact two-prime transforms (ne_ntt_any.cu) in the launches that follow,
 //     with the same epilogues and the same fault hook.
@@ -71,16 +72,26 @@ Layout layout(int64_t njobs, int64_t ntiles, int64_t nsegs, int64_t plane_bytes,
 }
 
 // ---- the product tile: 16 x 64 outputs of every digit plane, 8 warps -------------------
+//
+// Shared memory holds 128-byte k-rows of the digit-plane tiles and of the
+// transposed G tile, unpadded; the 16-byte chunk c of row r sits at chunk
+// c ^ sw(r).  sw takes 8 distinct values on every aligned group of 8 rows (the
+// rows of one ldmatrix phase) and on rows 4 nb + q for 8 consecutive nb (the
+// rows the lanes of a warp write when they store their transposed 4 x 4 blocks
+// of G), so neither the fragment loads nor the G stores have bank conflicts.
 
 namespace bgemm {
 
-constexpr int BM = 16, BN = 64, BK = 64, STAGES = 3, RB = 80, SB = 68;
+constexpr int BM = 16, BN = 64, BK = 128, STAGES = 2, RB = 128, SB = 72;
+constexpr int CTAS = 3;            // resident CTAs per SM of the product launch
 constexpr int UPW = 3;            // (plane, column half) units per warp: 2 * MS_MAX / 8, rounded up
 
 __host__ __device__ constexpr int smem_bytes(int MS) {
     return (STAGES * (MS * BM * RB + BN * RB)) > (MS * BM * SB * 4) ? (STAGES * (MS * BM * RB + BN * RB))
                                                                     : (MS * BM * SB * 4);
 }
+
+__device__ __forceinline__ int sw(int r) { return ((r >> 2) ^ r) & 7; }
 
 __device__ __forceinline__ void transpose4x4(const uint32_t (&r)[4], uint32_t (&c)[4]) {
     const uint32_t t0 = __byte_perm(r[0], r[1], 0x5140);
@@ -184,29 +195,40 @@ __device__ __forceinline__ void tile(const TileArgs& a, uint8_t* smem, int row0,
 
     auto load_A = [&](int stage, int kt) {
         const int k0 = kt * BK;
-        for (int e = tid; e < MS * BM * 4; e += THREADS) {
-            const int c16 = e & 3, r = (e >> 2) % BM, pl = (e >> 2) / BM;
+        for (int e = tid; e < MS * BM * 8; e += THREADS) {
+            const int c16 = e & 7, r = (e >> 3) % BM, pl = (e >> 3) / BM;
             const int gi = row0 + r, gk = k0 + 16 * c16;
             const bool ok = gi < rows && gk < K && !(recover && pl / a.S == a.r);
             const int8_t* src = a.planes + ((int64_t)pl * rows + (ok ? gi : 0)) * K + (ok ? gk : 0);
-            cp_async16(As_s + ((stage * MS + pl) * BM + r) * RB + 16 * c16, src, ok ? 16 : 0);
+            cp_async16(As_s + ((stage * MS + pl) * BM + r) * RB + 16 * (c16 ^ sw(r)), src, ok ? 16 : 0);
         }
     };
-    // G: one 4 x 4 byte block per thread and stage
-    const int nb = tid % (BN / 4), kb = tid / (BN / 4);
-    auto load_G = [&](int kt, uint32_t (&reg)[4]) {
+    // G: two 4 x 4 byte blocks per thread and stage; a warp covers 8 column
+    // blocks x 4 k blocks
+    const int nb = (lane & 7) + 8 * (warp & 1), kb0 = (lane >> 3) + 4 * (warp >> 1);
+    auto load_G = [&](int kt, uint32_t (&reg)[2][4]) {
         const int gn = col0 + 4 * nb;
 #pragma unroll
-        for (int q = 0; q < 4; q++) {
-            const int gk = kt * BK + 4 * kb + q;
-            reg[q] = (gk < K && gn < cols) ? __ldg(reinterpret_cast<const uint32_t*>(a.G + (int64_t)gk * cols + gn)) : 0u;
-        }
-    };
-    auto store_G = [&](int stage, const uint32_t (&reg)[4]) {
-        uint32_t c[4];
-        transpose4x4(reg, c);
+        for (int hb = 0; hb < 2; hb++)
 #pragma unroll
-        for (int q = 0; q < 4; q++) *reinterpret_cast<uint32_t*>(Bs + (stage * BN + 4 * nb + q) * RB + 4 * kb) = c[q];
+            for (int q = 0; q < 4; q++) {
+                const int gk = kt * BK + 4 * (kb0 + 16 * hb) + q;
+                reg[hb][q] = (gk < K && gn < cols)
+                                 ? __ldg(reinterpret_cast<const uint32_t*>(a.G + (int64_t)gk * cols + gn)) : 0u;
+            }
+    };
+    auto store_G = [&](int stage, const uint32_t (&reg)[2][4]) {
+#pragma unroll
+        for (int hb = 0; hb < 2; hb++) {
+            const int kb = kb0 + 16 * hb;
+            uint32_t c[4];
+            transpose4x4(reg[hb], c);
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const int n = 4 * nb + q;
+                *reinterpret_cast<uint32_t*>(Bs + (stage * BN + n) * RB + 16 * ((kb >> 2) ^ sw(n)) + 4 * (kb & 3)) = c[q];
+            }
+        }
     };
 
     int acc[UPW][4][4];
@@ -215,7 +237,7 @@ __device__ __forceinline__ void tile(const TileArgs& a, uint8_t* smem, int row0,
 #pragma unroll
         for (int j = 0; j < 4; j++) acc[i][j][0] = acc[i][j][1] = acc[i][j][2] = acc[i][j][3] = 0;
 
-    uint32_t greg[4];
+    uint32_t greg[2][4];
 #pragma unroll
     for (int st = 0; st < STAGES - 1; st++) {
         if (st < KT) {
@@ -225,6 +247,9 @@ __device__ __forceinline__ void tile(const TileArgs& a, uint8_t* smem, int row0,
         }
         cp_async_commit();
     }
+    // lane offsets of the fragment loads: A rows lane & 15 at chunk 2 ks + (lane >> 4);
+    // G rows n(nj) at chunk 2 ks + ((lane >> 3) & 1)
+    const int ar = lane & 15, ac = lane >> 4, bc = (lane >> 3) & 1;
     for (int kt = 0; kt < KT; kt++) {
         cp_async_wait<STAGES - 2>();
         __syncthreads();
@@ -236,15 +261,15 @@ __device__ __forceinline__ void tile(const TileArgs& a, uint8_t* smem, int row0,
         cp_async_commit();
         const int st = kt % STAGES;
 #pragma unroll
-        for (int ks = 0; ks < 2; ks++) {
-            const int t0 = 32 * ks;
+        for (int ks = 0; ks < BK / 32; ks++) {
+            if (kt * BK + 32 * ks >= K) break;      // k is a multiple of 16: the rest of the tile is padding
             // every unit of a warp has the same column half (units w, w + 8, ...):
             // its G fragments are loaded once and used by each of its planes
             uint32_t bf[2][4];
 #pragma unroll
             for (int nj = 0; nj < 4; nj += 2) {
                 const int n = 32 * (warp & 1) + 8 * (nj + (lane >> 4)) + (lane & 7);
-                ldsm_x4(bf[nj >> 1], Bs_s + (st * BN + n) * RB + t0 + 16 * ((lane >> 3) & 1));
+                ldsm_x4(bf[nj >> 1], Bs_s + (st * BN + n) * RB + 16 * ((2 * ks + bc) ^ sw(n)));
             }
 #pragma unroll
             for (int i = 0; i < UPW; i++) {
@@ -253,7 +278,7 @@ __device__ __forceinline__ void tile(const TileArgs& a, uint8_t* smem, int row0,
                 const int pl = u >> 1;
                 if (recover && pl / a.S == a.r) continue;
                 uint32_t af[4];
-                ldsm_x4(af, As_s + ((st * MS + pl) * BM + (lane & 15)) * RB + t0 + 16 * (lane >> 4));
+                ldsm_x4(af, As_s + ((st * MS + pl) * BM + ar) * RB + 16 * ((2 * ks + ac) ^ sw(ar)));
 #pragma unroll
                 for (int nj = 0; nj < 4; nj += 2) {
                     mma_s8(acc[i][nj], af, bf[nj >> 1][0], bf[nj >> 1][1]);
@@ -276,8 +301,9 @@ __device__ __forceinline__ void tile(const TileArgs& a, uint8_t* smem, int row0,
 #pragma unroll
         for (int nj = 0; nj < 4; nj++)
 #pragma unroll
-            for (int h = 0; h < 4; h++)
-                stash[(pl * BM + gq + 8 * (h >> 1)) * SB + 32 * nh + 8 * nj + 2 * tq + (h & 1)] = acc[i][nj][h];
+            for (int h = 0; h < 4; h += 2)
+                *reinterpret_cast<int2*>(stash + (pl * BM + gq + 8 * (h >> 1)) * SB + 32 * nh + 8 * nj + 2 * tq) =
+                    make_int2(acc[i][nj][h], acc[i][nj][h + 1]);
     }
     __syncthreads();
     epilogue<MT>(a, stash, row0, col0);
@@ -291,9 +317,9 @@ struct BatchK {
     const DevJob* jobs;
     const DevTile* tiles;
     const DevSeg* segs;
-    int32_t* counter;
+    int32_t* counter;            // [0]: product tiles taken, [1]: convolution tiles taken
     int8_t* planes;
-    int ntiles, nsegs;
+    int ngemm, ntiles, nsegs;    // tiles [0, ngemm) are products, [ngemm, ntiles) convolutions
     const int32_t* c;
     const int8_t* ops;
     int64_t* out;
@@ -353,7 +379,7 @@ __device__ __forceinline__ void fill_common(const BatchK& k, const DevJob* J, in
     }
 }
 
-__device__ __noinline__ void run_cconv(const BatchK& k, const DevJob* J, const DevTile& tl, uint8_t* smem) {
+__device__ __forceinline__ void run_cconv(const BatchK& k, const DevJob* J, const DevTile& tl, uint8_t* smem) {
     cconv::TileArgs t;
     t.planes = k.planes + J->plane_off;
     t.g = k.ops + J->op_off;
@@ -385,7 +411,7 @@ __device__ __noinline__ void run_cconv(const BatchK& k, const DevJob* J, const D
     }
 }
 
-__device__ __noinline__ void run_gemm(const BatchK& k, const DevJob* J, const DevTile& tl, uint8_t* smem) {
+__device__ __forceinline__ void run_gemm(const BatchK& k, const DevJob* J, const DevTile& tl, uint8_t* smem) {
     bgemm::TileArgs t;
     t.planes = k.planes + J->plane_off;
     t.G = k.ops + J->op_off;
@@ -413,7 +439,9 @@ __device__ __noinline__ void run_gemm(const BatchK& k, const DevJob* J, const De
     }
 }
 
-__global__ void __launch_bounds__(THREADS, 2) k_batch_op(BatchK k) {
+// the product tiles, 3 CTAs per SM: while one CTA fills its pipeline or runs
+// its epilogue, the others keep the tensor pipe busy
+__global__ void __launch_bounds__(THREADS, bgemm::CTAS) k_batch_gemm(BatchK k) {
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ int s_tile;
     for (;;) {
@@ -421,11 +449,24 @@ __global__ void __launch_bounds__(THREADS, 2) k_batch_op(BatchK k) {
         __syncthreads();
         const int t = s_tile;
         __syncthreads();
+        if (t >= k.ngemm) break;
+        const DevTile tl = k.tiles[t];
+        run_gemm(k, k.jobs + tl.job, tl, smem);
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(THREADS, 2) k_batch_cconv(BatchK k) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    __shared__ int s_tile;
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = k.ngemm + atomicAdd(k.counter + 1, 1);
+        __syncthreads();
+        const int t = s_tile;
+        __syncthreads();
         if (t >= k.ntiles) break;
         const DevTile tl = k.tiles[t];
-        const DevJob* J = k.jobs + tl.job;
-        if (tl.kind == NE_JOB_CCONV) run_cconv(k, J, tl, smem);
-        else run_gemm(k, J, tl, smem);
+        run_cconv(k, k.jobs + tl.job, tl, smem);
         __syncthreads();
     }
 }
@@ -457,9 +498,7 @@ ne_status plain_digits(int32_t lo, int32_t hi, ne_digits* dg) {
     return NE_OK;
 }
 
-constexpr int op_smem_bytes() {
-    return cconv::smem_bytes(MS_MAX) > bgemm::smem_bytes(MS_MAX) ? cconv::smem_bytes(MS_MAX) : bgemm::smem_bytes(MS_MAX);
-}
+
 
 }  // namespace
 
@@ -607,19 +646,30 @@ extern "C" ne_status ne_batch_plan(const ne_job* jobs, int32_t njobs, ne_batch_c
             useful += 2LL * j.M * j.N * j.N;
         }
     }
-    if (cfg.order == NE_ORDER_LPT) {
+    {
+        // the product tiles first (their own launch), then the convolution
+        // tiles; within each list job order, or the most costly first
+        const bool lpt = cfg.order == NE_ORDER_LPT;
         std::vector<size_t> idx(tiles.size());
         for (size_t t = 0; t < idx.size(); t++) idx[t] = t;
-        std::stable_sort(idx.begin(), idx.end(), [&](size_t x, size_t y) { return cost[x] > cost[y]; });
+        std::stable_sort(idx.begin(), idx.end(), [&](size_t x, size_t y) {
+            const bool gx = tiles[x].kind == NE_JOB_GEMM, gy = tiles[y].kind == NE_JOB_GEMM;
+            if (gx != gy) return gx;
+            return lpt && cost[x] > cost[y];
+        });
         std::vector<DevTile> sorted(tiles.size());
         for (size_t t = 0; t < idx.size(); t++) sorted[t] = tiles[idx[t]];
         tiles.swap(sorted);
     }
+    int64_t ngemm = 0;
+    while (ngemm < (int64_t)tiles.size() && tiles[(size_t)ngemm].kind == NE_JOB_GEMM) ngemm++;
     if (tiles.size() > 0x7fffffff || segs.size() > 0x7fffffff) return fail(NE_EINVAL, "ne_batch_plan: batch too large");
     if (nj.size() > 65535) return fail(NE_EINVAL, "ne_batch_plan: more than 65535 transform jobs");
     const Layout L = layout(njobs, (int64_t)tiles.size(), (int64_t)segs.size(), plane_bytes, (int64_t)nj.size(), ntt_ws);
     info->njobs = njobs;
     info->ntiles = (int32_t)tiles.size();
+    info->ngemm_tiles = (int32_t)ngemm;
+    info->gemm_grid = sm_count() * bgemm::CTAS;
     info->nsegs = (int32_t)segs.size();
     info->grid = sm_count() * cfg.ctas_per_sm;
     info->flag_words = flag_words;
@@ -658,7 +708,9 @@ extern "C" ne_status ne_batch_plan(const ne_job* jobs, int32_t njobs, ne_batch_c
 extern "C" ne_status ne_batch_run(ne_batch_info info, const int32_t* c, const int8_t* ops, int64_t* out, uint32_t* flags,
                                   uint64_t* nflag, const int64_t* fault_pos, const int32_t* fault_stream,
                                   const int32_t* fault_bit, void* workspace, int32_t* status, cudaStream_t s) {
-    if (!workspace || info.njobs < 0 || info.ntiles < 0 || info.grid < 1) return fail(NE_EINVAL, "ne_batch_run: bad plan");
+    if (!workspace || info.njobs < 0 || info.ntiles < 0 || info.grid < 1 || info.ngemm_tiles < 0 ||
+        info.ngemm_tiles > info.ntiles || (info.ngemm_tiles > 0 && info.gemm_grid < 1))
+        return fail(NE_EINVAL, "ne_batch_run: bad plan");
     if (info.njobs == 0) return NE_OK;
     if (!c || !ops || !out) return fail(NE_EINVAL, "ne_batch_run: null pointer");
     if ((fault_pos || fault_stream || fault_bit) && !(fault_pos && fault_stream && fault_bit))
@@ -672,6 +724,7 @@ extern "C" ne_status ne_batch_run(ne_batch_info info, const int32_t* c, const in
     k.segs = reinterpret_cast<const DevSeg*>(ws + L.segs);
     k.counter = reinterpret_cast<int32_t*>(ws);
     k.planes = reinterpret_cast<int8_t*>(ws + L.planes);
+    k.ngemm = info.ngemm_tiles;
     k.ntiles = info.ntiles;
     k.nsegs = info.nsegs;
     k.c = c;
@@ -683,7 +736,7 @@ extern "C" ne_status ne_batch_run(ne_batch_info info, const int32_t* c, const in
     k.fault_stream = fault_stream;
     k.fault_bit = fault_bit;
     k.status = status;
-    if (cudaMemsetAsync(k.counter, 0, sizeof(int32_t), s) != cudaSuccess) return check_launch("ne_batch_run: counter");
+    if (cudaMemsetAsync(k.counter, 0, 2 * sizeof(int32_t), s) != cudaSuccess) return check_launch("ne_batch_run: counters");
     if (flags && info.flag_words > 0 && cudaMemsetAsync(flags, 0, (size_t)info.flag_words * 4, s) != cudaSuccess)
         return check_launch("ne_batch_run: flags");
     if (nflag && cudaMemsetAsync(nflag, 0, sizeof(uint64_t), s) != cudaSuccess) return check_launch("ne_batch_run: count");
@@ -691,7 +744,10 @@ extern "C" ne_status ne_batch_run(ne_batch_info info, const int32_t* c, const in
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-        if (cudaFuncSetAttribute(k_batch_op, cudaFuncAttributeMaxDynamicSharedMemorySize, op_smem_bytes()) != cudaSuccess)
+        if (cudaFuncSetAttribute(k_batch_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 bgemm::smem_bytes(MS_MAX)) != cudaSuccess ||
+            cudaFuncSetAttribute(k_batch_cconv, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 cconv::smem_bytes(MS_MAX)) != cudaSuccess)
             return check_launch("ne_batch_run: shared-memory attribute");
         attr_set[dev] = true;
     }
@@ -701,9 +757,14 @@ extern "C" ne_status ne_batch_run(ne_batch_info info, const int32_t* c, const in
         ne_status st = check_launch("ne_batch_run: entangle");
         if (st) return st;
     }
-    if (info.ntiles > 0) {
-        k_batch_op<<<info.grid, THREADS, op_smem_bytes(), s>>>(k);
-        ne_status st = check_launch("ne_batch_run: operation");
+    if (info.ngemm_tiles > 0) {
+        k_batch_gemm<<<info.gemm_grid, THREADS, bgemm::smem_bytes(MS_MAX), s>>>(k);
+        ne_status st = check_launch("ne_batch_run: product tiles");
+        if (st) return st;
+    }
+    if (info.ntiles > info.ngemm_tiles) {
+        k_batch_cconv<<<info.grid, THREADS, cconv::smem_bytes(MS_MAX), s>>>(k);
+        ne_status st = check_launch("ne_batch_run: convolution tiles");
         if (st) return st;
     }
     if (info.ntransform > 0) {

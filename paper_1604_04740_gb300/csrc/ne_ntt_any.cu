@@ -321,12 +321,12 @@ __global__ void __launch_bounds__(256) k_ginv(const NttAnyArgs a) {
 // groups, exchanging through shared memory between groups: index bits 13..9
 // (element t + 512 k of thread t), bits 8..4 (element 512 hi + 16 k + lo of
 // thread 16 hi + lo) and bits 3..0 (rows 16 g + kk, g = t and t + 512).  The
-// word of element i in shared memory is swz(i), chosen so that each of the
-// three patterns reads and writes 32 distinct banks per warp (the first but
-// for one pair of lanes).
+// word of element i in shared memory is swz(i) = i + i / 32 (one pad word per
+// 32), with which each of the three patterns reads and writes 32 distinct
+// banks per warp, and every address is a per-thread base plus a constant.
 
 constexpr int RTHREADS = 512;
-__host__ __device__ constexpr int swz(int i) { return i + (i >> 4) + 16 * (i >> 9); }
+__host__ __device__ constexpr int swz(int i) { return i + (i >> 5); }
 constexpr int RSMEM_WORDS = swz(LB - 1) + 1;
 
 // bits 13..9: half-spans 512 d, d = 16 .. 1 (DIF) or 1 .. 16 (DIT)

@@ -58,7 +58,7 @@ class ne_batch_config(ctypes.Structure):
 
 
 class ne_batch_info(ctypes.Structure):
-    _fields_ = [(n, ctypes.c_int32) for n in ("njobs", "ntiles", "nsegs", "grid")] + \
+    _fields_ = [(n, ctypes.c_int32) for n in ("njobs", "ntiles", "nsegs", "grid", "ngemm_tiles", "gemm_grid")] + \
                [(n, ctypes.c_int64) for n in ("flag_words", "workspace_bytes", "mma_ops", "useful_ops")] + \
                [(n, ctypes.c_int32) for n in ("ntransform", "ntt_max_logL", "ntt_max_M", "ntt_min_logL")] + \
                [(n, ctypes.c_int64) for n in ("ntt_table_off", "ntt_ws_off", "ntt_units")]
