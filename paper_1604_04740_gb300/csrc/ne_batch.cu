@@ -84,11 +84,14 @@ namespace bgemm {
 
 constexpr int BM = 16, BN = 64, BK = 128, STAGES = 2, RB = 128, SB = 72;
 constexpr int CTAS = 3;            // resident CTAs per SM of the product launch
+constexpr int FCAP = 64;           // faults of one tile kept in shared memory
 constexpr int UPW = 3;            // (plane, column half) units per warp: 2 * MS_MAX / 8, rounded up
 
+// the pipeline, or after the main loop the stash and the tile's fault list
 __host__ __device__ constexpr int smem_bytes(int MS) {
-    return (STAGES * (MS * BM * RB + BN * RB)) > (MS * BM * SB * 4) ? (STAGES * (MS * BM * RB + BN * RB))
-                                                                    : (MS * BM * SB * 4);
+    return (STAGES * (MS * BM * RB + BN * RB)) > (MS * BM * SB * 4 + 4 * FCAP + 32)
+               ? (STAGES * (MS * BM * RB + BN * RB))
+               : (MS * BM * SB * 4 + 4 * FCAP + 32);
 }
 
 __device__ __forceinline__ int sw(int r) { return ((r >> 2) ^ r) & 7; }
@@ -118,19 +121,78 @@ struct TileArgs {
     int shift[NE_MAX_DIGITS];
 };
 
-template <int MT>
-__device__ __forceinline__ void epilogue(const TileArgs& a, const int32_t* stash, int row0, int col0) {
+// first index in [0, n) with pos[index] >= key (pos sorted ascending), by the
+// 32 lanes of a warp together: each round probes 32 points of the interval
+// left and keeps the part between the last probe below key and the first at
+// or above it
+__device__ __forceinline__ int64_t warp_lower_bound(const int64_t* pos, int64_t n, int64_t key) {
+    const int lane = threadIdx.x & 31;
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        const int64_t len = hi - lo;
+        const int64_t p = lo + len * (lane + 1) / 33;           // nondecreasing in lane, in [lo, hi)
+        const unsigned below = __ballot_sync(0xffffffffu, pos[p] < key);
+        const int c = __popc(below);                             // a prefix of the lanes
+        const int64_t p_last = __shfl_sync(0xffffffffu, p, c > 0 ? c - 1 : 0);
+        const int64_t p_next = __shfl_sync(0xffffffffu, p, c < 32 ? c : 31);
+        if (c > 0) lo = p_last + 1;
+        if (c < 32) hi = p_next;
+    }
+    return lo;
+}
+
+// The faults of a tile: the first warp locates the job's faults in the
+// tile's row band, keeps those inside its columns as (local index, stream,
+// bit) and returns their count, or -1 when there are more than FCAP (then
+// every position scans the band).
+__device__ __forceinline__ int tile_faults(const TileArgs& a, int row0, int col0, int32_t* list, int* count,
+                                           int64_t* band) {
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        const int64_t f0 = warp_lower_bound(a.fault_pos, a.nfault, (int64_t)row0 * a.cols + col0);
+        const int64_t f1 = warp_lower_bound(a.fault_pos, a.nfault, (int64_t)(row0 + BM - 1) * a.cols + col0 + BN);
+        int n = 0;
+        for (int64_t f = f0 + lane; f - lane < f1; f += 32) {
+            bool keep = false;
+            int32_t e = 0;
+            if (f < f1) {
+                const int64_t pos = a.fault_pos[f];
+                const int i = (int)(pos / a.cols), j = (int)(pos - (int64_t)i * a.cols);
+                keep = j >= col0 && j < col0 + BN;
+                e = (((i - row0) * BN + (j - col0)) << 16) | (a.fault_stream[f] << 8) | a.fault_bit[f];
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, keep);
+            const int at = n + __popc(m & ((1u << lane) - 1));
+            if (keep && at < FCAP) list[at] = e;
+            n += __popc(m);
+        }
+        if (lane == 0) {
+            *count = n <= FCAP ? n : -1;
+            band[0] = f0;
+            band[1] = f1;
+        }
+    }
+    __syncthreads();
+    return *count;
+}
+
+// LT: the job's l when it is 8 or 16 (then every shift below is a constant;
+// with two digits at shifts 0 and l, as the byte-aligned plans of int8-valued
+// streams have, the recombination is one shift-add), else 0
+template <int MT, int LT>
+__device__ __forceinline__ void epilogue(const TileArgs& a, const int32_t* stash, int row0, int col0, uint8_t* spare) {
     const int M = MT ? MT : a.M;
+    const int l = LT ? LT : a.l;
+    const bool two = LT && a.S == 2 && a.shift[0] == 0 && a.shift[1] == LT;
     const int S = a.S;
     const int lane = threadIdx.x & 31;
     const bool check = (a.fuse == NE_FUSE_EXTRACT_CHECK);
     const bool need_r = (a.fuse != NE_FUSE_RECOVER);
     const int64_t plane = (int64_t)a.rows * a.cols;
-    int64_t f0 = 0, f1 = 0;
-    if (a.nfault > 0) {
-        f0 = cconv::lower_bound(a.fault_pos, a.nfault, (int64_t)row0 * a.cols + col0);
-        f1 = cconv::lower_bound(a.fault_pos, a.nfault, (int64_t)(row0 + BM - 1) * a.cols + col0 + BN);
-    }
+    int32_t* flist = reinterpret_cast<int32_t*>(spare);
+    int64_t* band = reinterpret_cast<int64_t*>(spare + 4 * FCAP);
+    int* fcount = reinterpret_cast<int*>(spare + 4 * FCAP + 16);
+    const int nf = a.nfault > 0 ? tile_faults(a, row0, col0, flist, fcount, band) : 0;
     for (int base = threadIdx.x & ~31; base < BM * BN; base += THREADS) {
         const int idx = base + lane;
         const int i = idx / BN, j = idx % BN;
@@ -146,11 +208,22 @@ __device__ __forceinline__ void epilogue(const TileArgs& a, const int32_t* stash
             if (m >= M) m -= M;
             int64_t v = 0;
             if (jj > 0 || need_r) {
+                if (two) {
+                    v = (int64_t)sp[2 * m * BM * SB] + (int64_t)((uint64_t)(int64_t)sp[(2 * m + 1) * BM * SB] << LT);
+                } else {
 #pragma unroll
-                for (int s = 0; s < NE_MAX_DIGITS; s++)
-                    if (s < S) v += cconv::shl64(sp[(m * S + s) * BM * SB], a.shift[s]);
-                for (int64_t f = f0; f < f1; f++)
-                    if (a.fault_pos[f] == pos && a.fault_stream[f] == m) v ^= (int64_t)(1ull << a.fault_bit[f]);
+                    for (int s = 0; s < NE_MAX_DIGITS; s++)
+                        if (s < S) v += cconv::shl64(sp[(m * S + s) * BM * SB], a.shift[s]);
+                }
+                if (nf > 0) {
+                    for (int f = 0; f < nf; f++) {
+                        const int32_t e = flist[f];
+                        if ((e >> 16) == idx && ((e >> 8) & 0xff) == m) v ^= (int64_t)(1ull << (e & 0xff));
+                    }
+                } else if (nf < 0) {
+                    for (int64_t f = band[0]; f < band[1]; f++)
+                        if (a.fault_pos[f] == pos && a.fault_stream[f] == m) v ^= (int64_t)(1ull << a.fault_bit[f]);
+                }
             }
             rot[jj] = v;
         }
@@ -166,7 +239,7 @@ __device__ __forceinline__ void epilogue(const TileArgs& a, const int32_t* stash
             }
             continue;
         }
-        flag = extract_rot<MT>(rot, M, a.l, check, res);
+        flag = extract_rot<MT>(rot, M, l, check, res);
 #pragma unroll
         for (int jj = 0; jj < (MT ? MT : 32); jj++) {
             if (!MT && jj >= M) break;
@@ -306,7 +379,10 @@ __device__ __forceinline__ void tile(const TileArgs& a, uint8_t* smem, int row0,
                     make_int2(acc[i][nj][h], acc[i][nj][h + 1]);
     }
     __syncthreads();
-    epilogue<MT>(a, stash, row0, col0);
+    uint8_t* spare = smem + MS * BM * SB * 4;
+    if (a.l == 16) epilogue<MT, 16>(a, stash, row0, col0, spare);
+    else if (a.l == 8) epilogue<MT, 8>(a, stash, row0, col0, spare);
+    else epilogue<MT, 0>(a, stash, row0, col0, spare);
 }
 
 }  // namespace bgemm
