@@ -891,6 +891,18 @@ def batch_split(B, ne, torch, specs, cfg, dev):
     return out
 
 
+def batch_launches(info):
+    """Kernel launches of one ne_batch_run: the segment entangle, the product-
+    and convolution-tile launches, and for transform jobs the forward pass, the
+    block transforms (register-resident for L >= 2^14, radix 2 below), the
+    outer inverse pass and one final launch per M of 3, 4, 5."""
+    n = int(info.nsegs > 0) + int(info.ngemm_tiles > 0) + int(info.ntiles > info.ngemm_tiles)
+    if info.ntransform:
+        big, small = info.ntt_max_logL >= 14, info.ntt_min_logL < 14
+        n += 1 + 2 * int(big) + 2 * int(small) + int(info.ntt_max_logL > 14) + 3
+    return n
+
+
 def run_batch(args, rank, world, local_rank):
     """The ragged batch: 2048 jobs (M in {3,4,5}; half products m,n,k in
     [32, 2048], half circular convolutions N in [2^8, 2^16]), one bit flip per
@@ -964,7 +976,7 @@ def run_batch(args, rank, world, local_rank):
     peak = peak_ops / (p0.elapsed_time(p1) * 1e-3) / 1e12
     run_ms = statistics.median(op_ms)
     achieved = info.mma_ops / (run_ms * 1e-3) / 1e12
-    roof = {"bound": "tensor", "kernel": "ne_batch_run (entangle launch + persistent operation launch"
+    roof = {"bound": "tensor", "kernel": "ne_batch_run (entangle launch + persistent product-tile and convolution-tile launches"
                                           + (" + transform launches" if info.ntransform else "") + ")",
             "achieved": achieved, "peak": peak, "unit": "TOP/s", "frac": achieved / peak, "traffic": None,
             "peak_source": "measured in this run: mma.sync.m16n8k32 s8 register-resident probe",
@@ -1030,14 +1042,15 @@ def run_batch(args, rank, world, local_rank):
                 "config": {"workload": f"ragged batch: {len(specs)} jobs (M in 3..5; half GEMMs m,n,k log-uniform "
                                        f"in [32,2048], half circular convolutions N log-uniform in [2^8,2^16]); "
                                        "one bit flip per 1e4 output words; under a CUDA graph: one entangle launch, "
-                                       "one persistent tile launch and, for the convolutions the autotuner sends to "
-                                       "the exact transforms, the transform launches",
+                                       "one persistent launch over the product tiles, one over the convolution "
+                                       "tiles and, for the convolutions the autotuner sends to the exact "
+                                       "transforms, the transform launches",
                            "jobs": len(specs), "tiles": info.ntiles, "autotuned": B.config_dict(cfg),
                            "l2": "inputs of several GB, far larger than L2", "parallelism": f"replicas x{world}"},
                 "jobs_per_s": len(specs) * world / (ms * 1e-3), "detection": detection, "roofline": roof,
                 "split_by_job_class": split,
                 "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-                "gpu_launches": K * (2 + (6 + 2 * max(0, info.ntt_max_logL - 14) if info.ntransform else 0)),
+                "gpu_launches": K * batch_launches(info),
                 "autotune_trials": trials}
         print(json.dumps(line), flush=True)
 
@@ -1054,9 +1067,9 @@ def run_serve(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     rates = [1000, 2000, 5000, 10000, 20000, 50000]
-    # convolutions of N >= 8192 on the exact-transform path (the batch autotuner's choice for this mix)
+    # convolutions of N >= 4096 on the exact-transform path (the batch autotuner's choice for this mix)
     srv = S.Server(budget_bytes=100 * 10 ** 9, lanes=4, max_batch=256, device=dev, host_pool_elems=1 << 27,
-                   cfg=B.default_config(ntt_min_n=8192))
+                   cfg=B.default_config(ntt_min_n=4096))
     # warm-up: the library, the allocator pool, both job kinds, both convolution paths and
     # every kernel the mix can reach (lazy module loading would otherwise charge the first rate)
     srv.run(B.mixed_jobs(99, 32, conv=(256, 65536)), np.zeros(32))
@@ -1079,7 +1092,7 @@ def run_serve(args, rank, world, local_rank):
                 "config": {"workload": f"serving: Poisson arrivals at {rates} jobs/s, {args.jobs} requests per rate "
                                        "from the ragged-batch distribution, 1% lose one stream, 100 GB HBM budget, "
                                        "continuous batching on 4 CUDA-stream lanes (max 256 requests per micro-batch), "
-                                       "convolutions of N >= 8192 as exact transforms",
+                                       "convolutions of N >= 4096 as exact transforms",
                            "value_is": "useful Gop/s at the highest rate", "results": "device-resident"},
                 "serving": out, "roofline": None, "cpu_baseline": None,
                 "e2e": {"value": top["useful_Gop_s"] * world, "unit": "Gop/s",

@@ -24,6 +24,7 @@ from __future__ import annotations
 
 import bisect
 import dataclasses
+import gc
 import time
 
 import numpy as np
@@ -217,6 +218,18 @@ class Server:
                 co, oo = int(rng_c[i] % np.uint64(span_c + 1)), int(rng_c[i] % np.uint64(span_o + 1))
             reqs.append(Request(i, s, float(arrivals[i]), c_pool=co, op_pool=oo))
         T = _Table(specs, [rq.c_pool for rq in reqs], [rq.op_pool for rq in reqs])
+        # no cyclic garbage collection inside the loop: a full collection can
+        # stall the host for tens of milliseconds, which shows up as latency
+        gc_on = gc.isenabled()
+        gc.collect()
+        gc.disable()
+        try:
+            return self._loop(T, reqs, arrivals, n, timeout_s)
+        finally:
+            if gc_on:
+                gc.enable()
+
+    def _loop(self, T, reqs, arrivals, n, timeout_s):
         inflight = []
         free_lanes = list(range(len(self.streams)))
         head = nxt = done = 0          # requests [head, nxt) have arrived and wait for admission
