@@ -1081,7 +1081,11 @@ def run_serve(args, rank, world, local_rank):
         specs = B.mixed_jobs(rate, args.jobs, mnk=(32, 2048), conv=(256, 65536), recover_frac=0.01)
         arr = S.poisson_arrivals(rate, len(specs), float(rate))
         ent = S.summarize(srv.run(specs, arr, seed=rate))
+        ent.update(max_loop_iteration_ms=srv.max_iter_s * 1e3, max_launch_ms=srv.max_launch_s * 1e3,
+                   **{f"max_{k}_ms": v * 1e3 for k, v in srv.max_phase_s.items()})
         pla = S.summarize(srv.run(S.plain_copy(specs), arr, seed=rate))
+        pla.update(max_loop_iteration_ms=srv.max_iter_s * 1e3, max_launch_ms=srv.max_launch_s * 1e3,
+                   **{f"max_{k}_ms": v * 1e3 for k, v in srv.max_phase_s.items()})
         out[str(rate)] = {"entangled": ent, "plain": pla,
                           "throughput_overhead_pct": 100 * (pla["jobs_per_s"] / ent["jobs_per_s"] - 1)}
         top = ent

@@ -453,8 +453,10 @@ typedef struct {               /* what ne_batch_run needs to know on the host   
 
 /* Plan a batch: choose l and the digit plan of every job, lay out the digit
  * planes, cut entangle segments and operation tiles, order the tiles, and
- * write the tables to the device workspace (synchronous copy; workspace may
- * be null to only size it: info->workspace_bytes).  jobs is a host array.
+ * write the tables to the device workspace (a copy ordered on stream s: run
+ * the batch on s, or synchronise s before using the workspace elsewhere; the
+ * host may reuse jobs at once.  workspace may be null to only size it:
+ * info->workspace_bytes).  jobs is a host array.
  * Jobs are validated here (NE_EINVAL / NE_ERANGE with the job index in the
  * message).  The fault lists are sorted by position within each job's
  * range. */
@@ -508,7 +510,8 @@ ne_status ne_batch_run_static(const ne_job* jobs, int32_t njobs, ne_batch_config
  * regions host -> device on stream s, region i being nbytes[i] bytes from
  * src_base + src_off[i] (host; pinned for the copies to be asynchronous) to
  * dst_base + dst_off[i] (device).  One cudaMemcpyAsync per region, issued in
- * order; the three arrays are host arrays read during the call. */
+ * order, so the copy engines move the bytes while the SMs compute; the three
+ * arrays are host arrays read during the call. */
 ne_status ne_copy_regions_h2d(void* dst_base, const void* src_base, const int64_t* dst_off, const int64_t* src_off,
                               const int64_t* nbytes, int64_t count, cudaStream_t s);
 

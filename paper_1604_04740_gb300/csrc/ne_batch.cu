@@ -41,15 +41,20 @@ struct DevJob {
     int32_t shift[NE_MAX_DIGITS];
     FastPlan fp;
     int64_t c_off, op_off, out_off, flag_off, plane_off, npos, nout, fault_begin, fault_end;
+    int64_t gt_off;              // products: G transposed, [cols][k], in the planes arena
 };
 
 struct DevTile {
     int32_t job, kind, a, b;     // product: row tile, column tile; convolution: output chunk, blocks
 };
 
+constexpr int SEG_ENTANGLE = 0, SEG_TRANSPOSE = 1;
+constexpr int TT = 64;           // G transpose tiles: TT k x TT columns
+constexpr int TT_PER_SEG = 16;
+
 struct DevSeg {
-    int32_t job, pad;
-    int64_t start, count;        // positions of every stream of the job
+    int32_t job, kind;
+    int64_t start, count;        // entangle: positions of every stream of the job; transpose: tiles
 };
 
 struct Layout {
@@ -73,12 +78,12 @@ Layout layout(int64_t njobs, int64_t ntiles, int64_t nsegs, int64_t plane_bytes,
 
 // ---- the product tile: 16 x 64 outputs of every digit plane, 8 warps -------------------
 //
-// Shared memory holds 128-byte k-rows of the digit-plane tiles and of the
-// transposed G tile, unpadded; the 16-byte chunk c of row r sits at chunk
-// c ^ sw(r).  sw takes 8 distinct values on every aligned group of 8 rows (the
-// rows of one ldmatrix phase) and on rows 4 nb + q for 8 consecutive nb (the
-// rows the lanes of a warp write when they store their transposed 4 x 4 blocks
-// of G), so neither the fragment loads nor the G stores have bank conflicts.
+// mma.sync wants both operands k-major; the entangle launch writes each
+// product job's G transposed ([cols][k]) next to its digit planes, so both
+// operand tiles of a k step arrive by cp.async as 128-byte k-rows, unpadded in
+// shared memory, the 16-byte chunk c of row r at chunk c ^ sw(r).  sw takes 8
+// distinct values on every aligned group of 8 rows (the rows of one ldmatrix
+// phase), so the fragment loads have no bank conflicts.
 
 namespace bgemm {
 
@@ -96,20 +101,10 @@ __host__ __device__ constexpr int smem_bytes(int MS) {
 
 __device__ __forceinline__ int sw(int r) { return ((r >> 2) ^ r) & 7; }
 
-__device__ __forceinline__ void transpose4x4(const uint32_t (&r)[4], uint32_t (&c)[4]) {
-    const uint32_t t0 = __byte_perm(r[0], r[1], 0x5140);
-    const uint32_t t1 = __byte_perm(r[0], r[1], 0x7362);
-    const uint32_t t2 = __byte_perm(r[2], r[3], 0x5140);
-    const uint32_t t3 = __byte_perm(r[2], r[3], 0x7362);
-    c[0] = __byte_perm(t0, t2, 0x5410);
-    c[1] = __byte_perm(t0, t2, 0x7632);
-    c[2] = __byte_perm(t1, t3, 0x5410);
-    c[3] = __byte_perm(t1, t3, 0x7632);
-}
 
 struct TileArgs {
     const int8_t* planes;        // [M][S][rows][k]
-    const int8_t* G;             // [k][cols]
+    const int8_t* GT;            // G transposed: [cols][k]
     int64_t* out;                // [M][rows][cols]
     uint32_t* flags;             // bitmap over i * cols + j (pre-zeroed) or null
     unsigned long long* nflag;
@@ -266,7 +261,9 @@ __device__ __forceinline__ void tile(const TileArgs& a, uint8_t* smem, int row0,
     uint8_t* Bs = smem + STAGES * MS * BM * RB;            // [STAGES][BN][RB] (G transposed)
     const uint32_t As_s = smem_u32(As), Bs_s = smem_u32(Bs);
 
-    auto load_A = [&](int stage, int kt) {
+    // one k step of both operands: the digit-plane rows and the G^T rows
+    // (columns col0 .. col0 + 63), 16-byte chunks, zero-filled outside
+    auto load_AB = [&](int stage, int kt) {
         const int k0 = kt * BK;
         for (int e = tid; e < MS * BM * 8; e += THREADS) {
             const int c16 = e & 7, r = (e >> 3) % BM, pl = (e >> 3) / BM;
@@ -275,49 +272,23 @@ __device__ __forceinline__ void tile(const TileArgs& a, uint8_t* smem, int row0,
             const int8_t* src = a.planes + ((int64_t)pl * rows + (ok ? gi : 0)) * K + (ok ? gk : 0);
             cp_async16(As_s + ((stage * MS + pl) * BM + r) * RB + 16 * (c16 ^ sw(r)), src, ok ? 16 : 0);
         }
-    };
-    // G: two 4 x 4 byte blocks per thread and stage; a warp covers 8 column
-    // blocks x 4 k blocks
-    const int nb = (lane & 7) + 8 * (warp & 1), kb0 = (lane >> 3) + 4 * (warp >> 1);
-    auto load_G = [&](int kt, uint32_t (&reg)[2][4]) {
-        const int gn = col0 + 4 * nb;
-#pragma unroll
-        for (int hb = 0; hb < 2; hb++)
-#pragma unroll
-            for (int q = 0; q < 4; q++) {
-                const int gk = kt * BK + 4 * (kb0 + 16 * hb) + q;
-                reg[hb][q] = (gk < K && gn < cols)
-                                 ? __ldg(reinterpret_cast<const uint32_t*>(a.G + (int64_t)gk * cols + gn)) : 0u;
-            }
-    };
-    auto store_G = [&](int stage, const uint32_t (&reg)[2][4]) {
-#pragma unroll
-        for (int hb = 0; hb < 2; hb++) {
-            const int kb = kb0 + 16 * hb;
-            uint32_t c[4];
-            transpose4x4(reg[hb], c);
-#pragma unroll
-            for (int q = 0; q < 4; q++) {
-                const int n = 4 * nb + q;
-                *reinterpret_cast<uint32_t*>(Bs + (stage * BN + n) * RB + 16 * ((kb >> 2) ^ sw(n)) + 4 * (kb & 3)) = c[q];
-            }
+        for (int e = tid; e < BN * 8; e += THREADS) {
+            const int c16 = e & 7, n = e >> 3;
+            const int gn = col0 + n, gk = k0 + 16 * c16;
+            const bool ok = gn < cols && gk < K;
+            const int8_t* src = a.GT + (int64_t)(ok ? gn : 0) * K + (ok ? gk : 0);
+            cp_async16(Bs_s + (stage * BN + n) * RB + 16 * (c16 ^ sw(n)), src, ok ? 16 : 0);
         }
     };
-
     int acc[UPW][4][4];
 #pragma unroll
     for (int i = 0; i < UPW; i++)
 #pragma unroll
         for (int j = 0; j < 4; j++) acc[i][j][0] = acc[i][j][1] = acc[i][j][2] = acc[i][j][3] = 0;
 
-    uint32_t greg[2][4];
 #pragma unroll
     for (int st = 0; st < STAGES - 1; st++) {
-        if (st < KT) {
-            load_A(st, st);
-            load_G(st, greg);
-            store_G(st, greg);
-        }
+        if (st < KT) load_AB(st, st);
         cp_async_commit();
     }
     // lane offsets of the fragment loads: A rows lane & 15 at chunk 2 ks + (lane >> 4);
@@ -327,10 +298,7 @@ __device__ __forceinline__ void tile(const TileArgs& a, uint8_t* smem, int row0,
         cp_async_wait<STAGES - 2>();
         __syncthreads();
         const int pf = kt + STAGES - 1;
-        if (pf < KT) {
-            load_A(pf % STAGES, pf);
-            load_G(pf, greg);
-        }
+        if (pf < KT) load_AB(pf % STAGES, pf);
         cp_async_commit();
         const int st = kt % STAGES;
 #pragma unroll
@@ -359,7 +327,6 @@ __device__ __forceinline__ void tile(const TileArgs& a, uint8_t* smem, int row0,
                 }
             }
         }
-        if (pf < KT) store_G(pf % STAGES, greg);
     }
     cp_async_wait<0>();
     __syncthreads();
@@ -426,11 +393,51 @@ __device__ __forceinline__ bool entangle_segment(const BatchK& k, const DevJob* 
     return worst <= (uint32_t)F.hi - (uint32_t)F.lo;
 }
 
+// tiles [start, start + count) of G^T = the transpose of a product job's G
+// ([k][cols] -> [cols][k], so the product tiles stream both operands k-major)
+__device__ __forceinline__ void transpose_segment(const BatchK& k, const DevJob* J, const DevSeg& sg,
+                                                  uint8_t (*tile)[TT + 4]) {
+    const int K = J->k, cols = J->cols;
+    const int nct = (cols + TT - 1) / TT;
+    const uint8_t* G = reinterpret_cast<const uint8_t*>(k.ops + J->op_off);
+    uint8_t* GT = reinterpret_cast<uint8_t*>(k.planes + J->gt_off);
+    for (int64_t t = sg.start; t < sg.start + sg.count; t++) {
+        const int k0 = (int)(t / nct) * TT, c0 = (int)(t % nct) * TT;
+        // rows k0 .. k0 + 63 of G, 4 bytes per thread and step (rows are 4-byte aligned)
+        for (int e = threadIdx.x; e < TT * TT / 4; e += THREADS) {
+            const int kr = e / (TT / 4), cw = e % (TT / 4);
+            const int gk = k0 + kr, gc = c0 + 4 * cw;
+            const uint32_t w = (gk < K && gc < cols) ? __ldg(reinterpret_cast<const uint32_t*>(G + (int64_t)gk * cols + gc)) : 0u;
+            *reinterpret_cast<uint32_t*>(&tile[kr][4 * cw]) = w;
+        }
+        __syncthreads();
+        // rows c0 .. c0 + 63 of G^T, 16 bytes (16 k) per thread and step (k is a multiple of 16)
+        for (int e = threadIdx.x; e < TT * TT / 16; e += THREADS) {
+            const int n = e / (TT / 16), kc = e % (TT / 16);
+            const int gc = c0 + n, gk = k0 + 16 * kc;
+            if (gc < cols && gk < K) {
+                uint32_t w[4];
+#pragma unroll
+                for (int q = 0; q < 4; q++)
+                    w[q] = (uint32_t)tile[16 * kc + 4 * q][n] | ((uint32_t)tile[16 * kc + 4 * q + 1][n] << 8) |
+                           ((uint32_t)tile[16 * kc + 4 * q + 2][n] << 16) | ((uint32_t)tile[16 * kc + 4 * q + 3][n] << 24);
+                *reinterpret_cast<uint4*>(GT + (int64_t)gc * K + gk) = make_uint4(w[0], w[1], w[2], w[3]);
+            }
+        }
+        __syncthreads();
+    }
+}
+
 __global__ void __launch_bounds__(THREADS) k_batch_entangle(BatchK k) {
+    __shared__ uint8_t tile[TT][TT + 4];
     bool ok = true;
     for (int si = blockIdx.x; si < k.nsegs; si += gridDim.x) {
         const DevSeg sg = k.segs[si];
         const DevJob* J = k.jobs + sg.job;
+        if (sg.kind == SEG_TRANSPOSE) {
+            transpose_segment(k, J, sg, tile);
+            continue;
+        }
         switch (J->M) {
             case 3: ok &= entangle_segment<3>(k, J, sg); break;
             case 4: ok &= entangle_segment<4>(k, J, sg); break;
@@ -490,7 +497,7 @@ __device__ __forceinline__ void run_cconv(const BatchK& k, const DevJob* J, cons
 __device__ __forceinline__ void run_gemm(const BatchK& k, const DevJob* J, const DevTile& tl, uint8_t* smem) {
     bgemm::TileArgs t;
     t.planes = k.planes + J->plane_off;
-    t.G = k.ops + J->op_off;
+    t.GT = k.planes + J->gt_off;
     t.out = k.out + J->out_off;
     t.flags = (J->fuse == NE_FUSE_EXTRACT_CHECK && k.flags) ? k.flags + J->flag_off : nullptr;
     t.nflag = (J->fuse == NE_FUSE_EXTRACT_CHECK) ? k.nflag : nullptr;
@@ -592,9 +599,18 @@ extern "C" ne_status ne_batch_plan(const ne_job* jobs, int32_t njobs, ne_batch_c
     std::vector<NJob> nj;
     int64_t ntt_ws = 0, ntt_units = 0;
     int ntt_max_logL = 0, ntt_max_M = 0, ntt_min_logL = 31;
-    std::vector<DevTile> tiles;
+    // with a workspace the tile and segment lists are built (product tiles and
+    // convolution tiles apart); without one only counted, for the sizes
+    const bool build = workspace != nullptr;
+    struct GemmJob {
+        int32_t job, rt, ct;
+        int64_t cost;            // of each of its tiles
+    };
+    std::vector<GemmJob> gjobs;
+    std::vector<DevTile> tiles_c;
+    std::vector<int64_t> cost_c;
     std::vector<DevSeg> segs;
-    std::vector<int64_t> cost;
+    int64_t n_tiles_g = 0, n_tiles_c = 0, n_segs = 0;
     int64_t plane_bytes = 0, flag_words = 0, mma_ops = 0, useful = 0;
     for (int32_t i = 0; i < njobs; i++) {
         const ne_job& j = jobs[i];
@@ -701,52 +717,46 @@ extern "C" ne_status ne_batch_plan(const ne_job* jobs, int32_t njobs, ne_batch_c
         }
         d.plane_off = plane_bytes;
         plane_bytes = align256(plane_bytes + (int64_t)d.MS * d.npos);
-        for (int64_t s0 = 0; s0 < d.npos; s0 += SEG) segs.push_back(DevSeg{i, 0, s0, std::min<int64_t>(SEG, d.npos - s0)});
+        n_segs += (d.npos + SEG - 1) / SEG;
+        if (build)
+            for (int64_t s0 = 0; s0 < d.npos; s0 += SEG)
+                segs.push_back(DevSeg{i, SEG_ENTANGLE, s0, std::min<int64_t>(SEG, d.npos - s0)});
         if (j.kind == NE_JOB_GEMM) {
+            d.gt_off = plane_bytes;
+            plane_bytes = align256(plane_bytes + (int64_t)j.cols * j.k);
+            const int64_t ntt = (int64_t)((j.k + TT - 1) / TT) * ((j.cols + TT - 1) / TT);
+            n_segs += (ntt + TT_PER_SEG - 1) / TT_PER_SEG;
             const int rt = (j.rows + bgemm::BM - 1) / bgemm::BM, ct = (j.cols + bgemm::BN - 1) / bgemm::BN;
-            for (int a = 0; a < rt; a++)
-                for (int b = 0; b < ct; b++) {
-                    tiles.push_back(DevTile{i, NE_JOB_GEMM, a, b});
-                    cost.push_back((int64_t)d.MS * bgemm::BM * bgemm::BN * j.k);
-                }
+            n_tiles_g += (int64_t)rt * ct;
+            if (build) {
+                for (int64_t s0 = 0; s0 < ntt; s0 += TT_PER_SEG)
+                    segs.push_back(DevSeg{i, SEG_TRANSPOSE, s0, std::min<int64_t>(TT_PER_SEG, ntt - s0)});
+                gjobs.push_back(GemmJob{i, rt, ct, (int64_t)d.MS * bgemm::BM * bgemm::BN * j.k});
+            }
             mma_ops += 2LL * d.MS * rt * bgemm::BM * ct * bgemm::BN * j.k;
             useful += 2LL * j.M * j.rows * j.cols * j.k;
         } else {
             const int NB = j.N / cconv::T;
             const int npb = std::min(cfg.cconv_blocks, NB);
-            for (int a = 0; a * npb < NB; a++) {
-                tiles.push_back(DevTile{i, NE_JOB_CCONV, a, npb});
-                cost.push_back((int64_t)d.MS * std::min(npb, NB - a * npb) * cconv::T * j.N);
-            }
+            n_tiles_c += (NB + npb - 1) / npb;
+            if (build)
+                for (int a = 0; a * npb < NB; a++) {
+                    tiles_c.push_back(DevTile{i, NE_JOB_CCONV, a, npb});
+                    cost_c.push_back((int64_t)d.MS * std::min(npb, NB - a * npb) * cconv::T * j.N);
+                }
             mma_ops += 2LL * d.MS * j.N * j.N;
             useful += 2LL * j.M * j.N * j.N;
         }
     }
-    {
-        // the product tiles first (their own launch), then the convolution
-        // tiles; within each list job order, or the most costly first
-        const bool lpt = cfg.order == NE_ORDER_LPT;
-        std::vector<size_t> idx(tiles.size());
-        for (size_t t = 0; t < idx.size(); t++) idx[t] = t;
-        std::stable_sort(idx.begin(), idx.end(), [&](size_t x, size_t y) {
-            const bool gx = tiles[x].kind == NE_JOB_GEMM, gy = tiles[y].kind == NE_JOB_GEMM;
-            if (gx != gy) return gx;
-            return lpt && cost[x] > cost[y];
-        });
-        std::vector<DevTile> sorted(tiles.size());
-        for (size_t t = 0; t < idx.size(); t++) sorted[t] = tiles[idx[t]];
-        tiles.swap(sorted);
-    }
-    int64_t ngemm = 0;
-    while (ngemm < (int64_t)tiles.size() && tiles[(size_t)ngemm].kind == NE_JOB_GEMM) ngemm++;
-    if (tiles.size() > 0x7fffffff || segs.size() > 0x7fffffff) return fail(NE_EINVAL, "ne_batch_plan: batch too large");
+    const int64_t ntiles = n_tiles_g + n_tiles_c, ngemm = n_tiles_g;
+    if (ntiles > 0x7fffffff || n_segs > 0x7fffffff) return fail(NE_EINVAL, "ne_batch_plan: batch too large");
     if (nj.size() > 65535) return fail(NE_EINVAL, "ne_batch_plan: more than 65535 transform jobs");
-    const Layout L = layout(njobs, (int64_t)tiles.size(), (int64_t)segs.size(), plane_bytes, (int64_t)nj.size(), ntt_ws);
+    const Layout L = layout(njobs, ntiles, n_segs, plane_bytes, (int64_t)nj.size(), ntt_ws);
     info->njobs = njobs;
-    info->ntiles = (int32_t)tiles.size();
+    info->ntiles = (int32_t)ntiles;
     info->ngemm_tiles = (int32_t)ngemm;
     info->gemm_grid = sm_count() * bgemm::CTAS;
-    info->nsegs = (int32_t)segs.size();
+    info->nsegs = (int32_t)n_segs;
     info->grid = sm_count() * cfg.ctas_per_sm;
     info->flag_words = flag_words;
     info->workspace_bytes = L.total;
@@ -770,14 +780,27 @@ extern "C" ne_status ne_batch_plan(const ne_job* jobs, int32_t njobs, ne_batch_c
     if (!aligned(workspace, 256)) return fail(NE_EINVAL, "ne_batch_plan: workspace must be 256-byte aligned");
     std::vector<uint8_t> host((size_t)L.planes, 0);
     std::memcpy(host.data() + L.jobs, dj.data(), dj.size() * sizeof(DevJob));
-    if (!tiles.empty()) std::memcpy(host.data() + L.tiles, tiles.data(), tiles.size() * sizeof(DevTile));
+    // the product tiles first (their own launch), then the convolution tiles;
+    // within each list job order, or the most costly first (stable; all tiles
+    // of a product job cost the same, so its jobs are sorted instead)
+    const bool lpt = cfg.order == NE_ORDER_LPT;
+    DevTile* dst = reinterpret_cast<DevTile*>(host.data() + L.tiles);
+    if (lpt) std::stable_sort(gjobs.begin(), gjobs.end(), [](const GemmJob& x, const GemmJob& y) { return x.cost > y.cost; });
+    for (const GemmJob& g : gjobs)
+        for (int a = 0; a < g.rt; a++)
+            for (int b = 0; b < g.ct; b++) *dst++ = DevTile{g.job, NE_JOB_GEMM, a, b};
+    std::vector<uint32_t> idx(tiles_c.size());
+    for (size_t t = 0; t < idx.size(); t++) idx[t] = (uint32_t)t;
+    if (lpt) std::stable_sort(idx.begin(), idx.end(), [&](uint32_t x, uint32_t y) { return cost_c[x] > cost_c[y]; });
+    for (size_t t = 0; t < idx.size(); t++) *dst++ = tiles_c[idx[t]];
     if (!segs.empty()) std::memcpy(host.data() + L.segs, segs.data(), segs.size() * sizeof(DevSeg));
     if (cudaMemcpyAsync(workspace, host.data(), host.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
         return check_launch("ne_batch_plan: copy tables");
     if (!nj.empty() && cudaMemcpyAsync(static_cast<uint8_t*>(workspace) + L.ntt_table, nj.data(),
                                        nj.size() * sizeof(NJob), cudaMemcpyHostToDevice, s) != cudaSuccess)
         return check_launch("ne_batch_plan: copy transform jobs");
-    if (cudaStreamSynchronize(s) != cudaSuccess) return check_launch("ne_batch_plan: copy tables");
+    // no wait: a copy from pageable memory returns once its bytes are staged
+    // (so the host vectors may go), and it is ordered on s before the runs
     return NE_OK;
 }
 

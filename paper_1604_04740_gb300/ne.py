@@ -622,7 +622,8 @@ def _job_array(jobs):
 def ne_batch_plan(jobs, cfg: ne_batch_config, workspace: torch.Tensor | None = None) -> ne_batch_info:
     """jobs: a ctypes array of ne_job or a numpy JOB_DTYPE array (host).
     With workspace None only sizes the plan (info.workspace_bytes); otherwise
-    writes the tables into it (uint8 device tensor, 256-byte aligned)."""
+    writes the tables into it (uint8 device tensor, 256-byte aligned) by a
+    copy ordered on the current stream: run the batch on the same stream."""
     info = ne_batch_info()
     ws_ptr, ws_bytes = None, 0
     if workspace is not None:

@@ -139,6 +139,11 @@ class Server:
         self.status_h = [torch.zeros(1, dtype=torch.int32).pin_memory() for _ in range(lanes)]
         self.nflag_h = [torch.zeros(1, dtype=torch.int64).pin_memory() for _ in range(lanes)]
         self.flagged = 0
+        # host-side timing of the last run: the longest loop iteration and the
+        # longest micro-batch launch (plan, copies, kernel launches), in seconds
+        self.max_iter_s = 0.0
+        self.max_launch_s = 0.0
+        self.max_phase_s = {"plan": 0.0, "copy": 0.0, "run": 0.0}
 
     # -- one micro-batch: requests [a, b) ------------------------------------------------
     def _launch(self, T: _Table, a: int, b: int, lane: int):
@@ -156,6 +161,7 @@ class Server:
         jobs["c_off"], jobs["op_off"], jobs["out_off"], jobs["flag_off"] = c_off, op_off, out_off, flag_off
         n_c, n_op = int(c_sz.sum()), int(op_sz.sum())
         n_out, n_fl = int(T.out_elems[a:b].sum()), int(T.flag_words[a:b].sum())
+        t_p = time.perf_counter()
         info = ne.ne_batch_plan(jobs, self.cfg)
         parts = [_a(n_c * 4 + 16), _a(n_op + 16), _a(max(n_out, 1) * 8), _a(max(n_fl, 1) * 4), 256, 256,
                  _a(info.workspace_bytes)]
@@ -175,14 +181,19 @@ class Server:
         stream = self.streams[lane]
         with torch.cuda.stream(stream):
             info = ne.ne_batch_plan(jobs, self.cfg, ws)
+            t_c = time.perf_counter()
             ne.ne_copy_regions_h2d(c, self.c_host, c_off * 4, T.c_pool[a:b] * 4, T.c_elems[a:b] * 4)
             ne.ne_copy_regions_h2d(ops, self.op_host, op_off, T.op_pool[a:b], T.op_bytes[a:b])
+            t_r = time.perf_counter()
             status.zero_()
             ne.ne_batch_run(info, c, ops, out, flags, nflag, ws, status=status)
             self.status_h[lane].copy_(status, non_blocking=True)
             self.nflag_h[lane].copy_(nflag, non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(stream)
+        t_e = time.perf_counter()
+        for phase, dt in (("plan", t_c - t_p), ("copy", t_r - t_c), ("run", t_e - t_r)):
+            self.max_phase_s[phase] = max(self.max_phase_s[phase], dt)
         return dict(ev=ev, region=(off, nb), a=a, b=b, out=out, out_off=out_off, lane=lane)
 
     def _finish(self, fl, T: _Table, reqs, t):
@@ -238,8 +249,13 @@ class Server:
         arr = np.asarray(arrivals, np.float64) + t0
         for i, rq in enumerate(reqs):
             rq.arrival = float(arr[i])
+        self.max_iter_s = self.max_launch_s = 0.0
+        self.max_phase_s = {"plan": 0.0, "copy": 0.0, "run": 0.0}
+        last = time.perf_counter()
         while done < n:
             now = time.perf_counter()
+            self.max_iter_s = max(self.max_iter_s, now - last)
+            last = now
             nxt = int(np.searchsorted(arr, now, side="right"))
             still = []
             for fl in inflight:
@@ -254,7 +270,9 @@ class Server:
                 b = min(nxt, head + self.max_batch)
                 fl = None
                 while b > head:
+                    t_l = time.perf_counter()
                     fl = self._launch(T, head, b, free_lanes[0])
+                    self.max_launch_s = max(self.max_launch_s, time.perf_counter() - t_l)
                     if fl is not None:
                         break
                     b = head + (b - head) // 2          # does not fit the free budget: admit fewer

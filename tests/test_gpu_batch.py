@@ -81,6 +81,32 @@ def test_batch_matches_oracle_and_flags_exactly_the_faults(mods):
     assert b.faults is not None and int(b.nflag.item()) == total == len(b.faults["pos"])
 
 
+def test_dense_faults_take_the_band_scan_and_match_the_oracle(mods):
+    # a flip in 3 % of the output words: product tiles hold more faults than
+    # their shared-memory list (64), so positions scan the tile's row band
+    B, ne = mods
+    G, C = ne.NE_JOB_GEMM, ne.NE_JOB_CCONV
+    specs = [B.JobSpec(G, 5, rows=64, cols=128, k=64), B.JobSpec(G, 3, rows=33, cols=200, k=48),
+             B.JobSpec(G, 4, rows=20, cols=64, k=32), B.JobSpec(C, 4, N=1024), B.JobSpec(C, 3, N=5120)]
+    b = B.Batch(specs, seed=12, fault_rate=0.03)
+    b.plan(B.default_config(ntt_min_n=4096))
+    assert b.info.ntransform == 1
+    b.run()
+    torch.cuda.synchronize()
+    assert int(b.status.item()) == 0
+    tile0 = b.faults["pos"][(b.faults["job"] == 0) & (b.faults["pos"] < 16 * 128)]
+    assert (tile0 % 128 < 64).sum() > 64          # the first tile of job 0 overflows the list
+    total = 0
+    for j, s in enumerate(b.specs):
+        dh, fl = oracle_job(b, j, ne)
+        got = b.job_output(j).cpu().numpy().reshape(s.M, -1)
+        assert (got == dh).all(), f"job {j} ({s})"
+        gf = unpack_flags(b.job_flags(j).cpu().numpy(), 1, s.positions_out)[0]
+        assert (gf == fl).all() and (gf == B.expected_flags(b, j)).all(), f"job {j} flags"
+        total += int(fl.sum())
+    assert int(b.nflag.item()) == total == len(b.faults["pos"])
+
+
 def test_transform_path_matches_oracle_tensor_path_and_graph(mods):
     # convolutions of N >= 512 leave the tensor tiles for the exact transforms
     B, ne = mods

@@ -87,3 +87,25 @@ def test_pool_allocator_coalesces(mods):
     p.release(*c)
     assert p.used == 0 and p.free == [(0, p.size)]
     assert p.alloc(p.size + 1) is None
+
+
+@pytest.mark.parametrize("count", [1, 7, 300])
+def test_copy_regions_gathers_every_byte(mods, count):
+    # regions of odd sizes at odd offsets (and empty ones), more than one
+    # gather launch for 300 regions; bytes outside the regions stay untouched
+    _, ne, _ = mods
+    rng = np.random.default_rng(count)
+    src = torch.from_numpy(rng.integers(0, 256, 1 << 20, dtype=np.uint8)).pin_memory()
+    nbytes = rng.integers(0, 3000, count).astype(np.int64)
+    nbytes[::5] = 0
+    src_off = rng.integers(0, src.numel() - 3000, count).astype(np.int64)
+    dst_off = np.concatenate([[3], 3 + np.cumsum(nbytes + rng.integers(0, 40, count))[:-1]]).astype(np.int64)
+    size = int(dst_off[-1] + nbytes[-1] + 64)
+    dst = torch.full((size,), 7, dtype=torch.uint8, device="cuda")
+    ne.ne_copy_regions_h2d(dst, src, dst_off, src_off, nbytes)
+    got = dst.cpu().numpy()
+    want = np.full(size, 7, np.uint8)
+    s = src.numpy()
+    for d, o, b in zip(dst_off, src_off, nbytes):
+        want[d:d + b] = s[o:o + b]
+    assert (got == want).all()
