@@ -383,19 +383,21 @@ ne_status ne_abft_recover(int32_t M, int64_t* d, int64_t batch, int64_t n, int32
                           cudaStream_t s);
 
 /* ------------------------------------------------------------------------ */
-/* Ragged batches: many independent jobs in one persistent launch            */
+/* Ragged batches: many independent jobs in a few persistent launches       */
 /* ------------------------------------------------------------------------ */
 /*
  * Sec. IV notes that long streams and large products are processed as many
  * independent blocks; the entanglement of every block is independent.  A
  * batch runs any mix of such jobs -- products and circular convolutions,
  * with their own M, l and sizes -- through the same digit-plane tensor path:
- * one launch entangles every job into digit planes, then ONE persistent
- * launch walks a tile list covering all jobs (an atomic tile counter), each
- * tile running the operation with the fused extract/check (or fused
- * recovery) of its job.  Both launches read only device memory prepared by
- * ne_batch_plan, so ne_batch_run can be captured in a CUDA graph and
- * replayed.
+ * one launch entangles every job into digit planes (and writes each
+ * product's operand transposed), then one persistent launch walks the
+ * product tiles and one the convolution tiles (an atomic tile counter each),
+ * each tile running the operation with the fused extract/check (or fused
+ * recovery) of its job; convolutions at or above the plan's ntt_min_n run
+ * as exact transforms in the launches that follow.  Every launch reads only
+ * device memory prepared by ne_batch_plan, so ne_batch_run can be captured
+ * in a CUDA graph and replayed.
  */
 #define NE_JOB_GEMM  0
 #define NE_JOB_CCONV 1

@@ -1,7 +1,8 @@
-"""GPU tests of the ragged batch runner (one persistent launch over mixed
-product/convolution jobs): parity with the oracle, detection of exactly the
-injected faults, batch-versus-alone equality, every tuner configuration,
-CUDA-graph replay, and fused recovery of lost streams."""
+"""GPU tests of the ragged batch runner (persistent launches over mixed
+product/convolution jobs, long convolutions on transforms): parity with the
+oracle, detection of exactly the injected faults (sparse and dense),
+batch-versus-alone equality, every tuner configuration, CUDA-graph replay,
+and fused recovery of lost streams."""
 import numpy as np
 import pytest
 
