@@ -350,7 +350,10 @@ __global__ void __launch_bounds__(448, 2) k_cconv_ntt(const NttArgs a) {
         }
         __syncthreads();
         // recombine the digits of every stream and extract, 32 positions per warp
+        // (l = 16 with the two digits at shifts 0 and 16, the byte-aligned plan of
+        // int8-valued streams, with every shift a constant)
         const int32_t* resall = reinterpret_cast<const int32_t*>(bufs);
+        const bool l16 = a.l == 16 && a.S == 2 && a.shift[0] == 0 && a.shift[1] == 16;
         for (int base = warp * 32; base < N; base += blockDim.x) {
             const int i = base + lane;
             int64_t rot[MR];
@@ -361,15 +364,21 @@ __global__ void __launch_bounds__(448, 2) k_cconv_ntt(const NttArgs a) {
                 if (mm >= Mv) mm -= Mv;
                 uint64_t w = 0;
                 if (!(a.fuse == NE_FUSE_RECOVER && j == 0)) {
-                    for (int ss = 0; ss < a.S; ss++)
-                        w += (uint64_t)(int64_t)resall[(mm * a.S + ss) * BUF + i] << a.shift[ss];
+                    if (l16) {
+                        w = (uint64_t)(int64_t)resall[2 * mm * BUF + i] +
+                            ((uint64_t)(int64_t)resall[(2 * mm + 1) * BUF + i] << 16);
+                    } else {
+                        for (int ss = 0; ss < a.S; ss++)
+                            w += (uint64_t)(int64_t)resall[(mm * a.S + ss) * BUF + i] << a.shift[ss];
+                    }
                 }
                 rot[j] = (int64_t)w;
             }
             uint32_t f = 0;
             if (a.fuse != NE_FUSE_NONE) {
                 int64_t o[MR];
-                f = extract_rot<MT>(rot, Mv, a.l, a.fuse == NE_FUSE_EXTRACT_CHECK, o) ? 1u : 0u;
+                const bool chk = a.fuse == NE_FUSE_EXTRACT_CHECK;
+                f = (l16 ? extract_rot<MT>(rot, Mv, 16, chk, o) : extract_rot<MT>(rot, Mv, a.l, chk, o)) ? 1u : 0u;
 #pragma unroll
                 for (int j = 0; j < MR; j++) {
                     if (!MT && j >= Mv) break;

@@ -606,7 +606,11 @@ __global__ void __launch_bounds__(256) k_final(const NttAnyArgs a) {
             if (valid) {
                 if (j.fuse != NE_FUSE_NONE) {
                     int64_t o[MR];
-                    flag = extract_rot<MT>(rot, Mv, j.l, j.fuse == NE_FUSE_EXTRACT_CHECK, o);
+                    // constant shifts for the byte-aligned l of int8-valued streams
+                    const bool chk = j.fuse == NE_FUSE_EXTRACT_CHECK;
+                    flag = j.l == 16  ? extract_rot<MT>(rot, Mv, 16, chk, o)
+                           : j.l == 8 ? extract_rot<MT>(rot, Mv, 8, chk, o)
+                                      : extract_rot<MT>(rot, Mv, j.l, chk, o);
 #pragma unroll
                     for (int jj = 0; jj < MR; jj++) {
                         if (!MT && jj >= Mv) break;
