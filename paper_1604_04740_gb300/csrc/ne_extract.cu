@@ -19,8 +19,8 @@ constexpr int kWarps = kThreads / 32;
 
 // U segments per warp and iteration: all their loads are issued before any
 // arithmetic, so a warp keeps U * M * 32 * VEC words in flight.
-template <int MT, int VEC, int U, bool WRITE_D, bool CHECK>
-__global__ void __launch_bounds__(kThreads) k_extract(const int64_t* __restrict__ delta, int64_t* __restrict__ dhat,
+template <int MT, int VEC, int U, bool WRITE_D, bool CHECK, int TH = kThreads>
+__global__ void __launch_bounds__(TH) k_extract(const int64_t* __restrict__ delta, int64_t* __restrict__ dhat,
                                                       int M, int l, int r, int64_t batch, int64_t n,
                                                       uint32_t* __restrict__ flags, unsigned long long* nflag) {
     constexpr int MR = MT ? MT : 32;
@@ -33,8 +33,8 @@ __global__ void __launch_bounds__(kThreads) k_extract(const int64_t* __restrict_
         const int64_t* db = delta + b * Mv * n;
         int64_t* ob = dhat + b * Mv * n;
         uint32_t* fb = flags ? flags + b * wpr : nullptr;
-        for (int64_t sp = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5); sp * U < nseg;
-             sp += (int64_t)gridDim.x * kWarps) {
+        for (int64_t sp = (int64_t)blockIdx.x * (TH / 32) + (threadIdx.x >> 5); sp * U < nseg;
+             sp += (int64_t)gridDim.x * (TH / 32)) {
             int64_t rot[U][VEC][MR];
             // rotate while loading: register index j is static, address is not
 #pragma unroll
@@ -95,10 +95,10 @@ __global__ void __launch_bounds__(kThreads) k_extract(const int64_t* __restrict_
     }
 }
 
-dim3 grid_segments(int64_t batch, int64_t nseg) {
+dim3 grid_segments(int64_t batch, int64_t nseg, int threads = kThreads) {
     int64_t gy = batch < 65535 ? batch : 65535;
-    int64_t want = (int64_t)wave_blocks(kThreads, 4);
-    int64_t gx = (nseg + kWarps - 1) / kWarps;
+    int64_t want = (int64_t)wave_blocks(threads, 4);
+    int64_t gx = (nseg + threads / 32 - 1) / (threads / 32);
     int64_t cap = want / gy;
     if (cap < 1) cap = 1;
     if (gx > cap) gx = cap;
@@ -111,6 +111,15 @@ void launch_extract_vec(const int64_t* delta, int64_t* dhat, int M, int l, int r
                         uint32_t* flags, unsigned long long* nflag, cudaStream_t s) {
     constexpr int U = MT ? 2 : 1;      // the generic-M kernel keeps one segment (register budget)
     const bool vec2 = (n % 2 == 0) && aligned(delta, 16) && (!WRITE_D || aligned(dhat, 16));
+    if constexpr (MT != 0 && !WRITE_D) {
+        if (vec2) {
+            // the read-only check: four segments per warp in flight (no stores
+            // to overlap with), 128-thread blocks
+            dim3 g = grid_segments(batch, ((n + 63) / 64 + 3) / 4, 128);
+            k_extract<MT, 2, 4, WRITE_D, CHECK, 128><<<g, 128, 0, s>>>(delta, dhat, M, l, r, batch, n, flags, nflag);
+            return;
+        }
+    }
     if (vec2) {
         dim3 g = grid_segments(batch, ((n + 63) / 64 + U - 1) / U);
         k_extract<MT, 2, U, WRITE_D, CHECK><<<g, kThreads, 0, s>>>(delta, dhat, M, l, r, batch, n, flags, nflag);
