@@ -78,9 +78,13 @@ OPS = ("add", "sub", "mul", "outer", "inner", "permute")
 @pytest.mark.parametrize("op", OPS)
 @pytest.mark.parametrize("M", [3, 4, 5, 6])
 @pytest.mark.parametrize("n,shared", [(1000, False), (999, False), (64, True)])
-def test_lsb_operator_matches_oracle(ne, op, M, n, shared):
+@pytest.mark.parametrize("lchoice", ["smallest", "16"])
+def test_lsb_operator_matches_oracle(ne, op, M, n, shared, lchoice):
+    # l = 16 (valid for M <= 4) takes the kernels compiled for that l
     B, k = 3, (10 if n % 2 == 0 else 7)
-    l = oracle.choose_l(M, 64, bound(op, n), oracle.POLICY_SMALLEST)[0]
+    if lchoice == "16" and (M - 1) * 16 >= 64:
+        pytest.skip("l = 16 needs (M - 1) l < 64")
+    l = oracle.choose_l(M, 64, bound(op, n), oracle.POLICY_SMALLEST)[0] if lchoice == "smallest" else 16
     p = ne.params(M, l)
     c = inputs.streams(5 + M, (B, M, n))
     g = operand(op, B, n, k, 11 * M + n, shared)
