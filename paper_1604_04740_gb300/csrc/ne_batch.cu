@@ -51,6 +51,7 @@ struct DevTile {
 constexpr int SEG_ENTANGLE = 0, SEG_TRANSPOSE = 1;
 constexpr int TT = 64;           // G transpose tiles: TT k x TT columns
 constexpr int TT_PER_SEG = 16;
+constexpr int TT_ROUND = 4;      // transpose tiles loaded together
 
 struct DevSeg {
     int32_t job, kind;
@@ -394,34 +395,55 @@ __device__ __forceinline__ bool entangle_segment(const BatchK& k, const DevJob* 
 }
 
 // tiles [start, start + count) of G^T = the transpose of a product job's G
-// ([k][cols] -> [cols][k], so the product tiles stream both operands k-major)
+// ([k][cols] -> [cols][k], so the product tiles stream both operands k-major),
+// TT_ROUND tiles per round so that each thread has 4 TT_ROUND loads in flight
 __device__ __forceinline__ void transpose_segment(const BatchK& k, const DevJob* J, const DevSeg& sg,
-                                                  uint8_t (*tile)[TT + 4]) {
+                                                  uint8_t (*tile)[TT][TT + 4]) {
     const int K = J->k, cols = J->cols;
     const int nct = (cols + TT - 1) / TT;
     const uint8_t* G = reinterpret_cast<const uint8_t*>(k.ops + J->op_off);
     uint8_t* GT = reinterpret_cast<uint8_t*>(k.planes + J->gt_off);
-    for (int64_t t = sg.start; t < sg.start + sg.count; t++) {
-        const int k0 = (int)(t / nct) * TT, c0 = (int)(t % nct) * TT;
+    for (int64_t t0 = sg.start; t0 < sg.start + sg.count; t0 += TT_ROUND) {
+        const int nt = (int)min((int64_t)TT_ROUND, sg.start + sg.count - t0);
         // rows k0 .. k0 + 63 of G, 4 bytes per thread and step (rows are 4-byte aligned)
-        for (int e = threadIdx.x; e < TT * TT / 4; e += THREADS) {
-            const int kr = e / (TT / 4), cw = e % (TT / 4);
-            const int gk = k0 + kr, gc = c0 + 4 * cw;
-            const uint32_t w = (gk < K && gc < cols) ? __ldg(reinterpret_cast<const uint32_t*>(G + (int64_t)gk * cols + gc)) : 0u;
-            *reinterpret_cast<uint32_t*>(&tile[kr][4 * cw]) = w;
+        uint32_t w[TT_ROUND][TT * TT / 4 / THREADS];
+#pragma unroll
+        for (int h = 0; h < TT_ROUND; h++) {
+            const int64_t t = t0 + h;
+            const int k0 = (int)(t / nct) * TT, c0 = (int)(t % nct) * TT;
+#pragma unroll
+            for (int i = 0; i < TT * TT / 4 / THREADS; i++) {
+                const int e = threadIdx.x + i * THREADS;
+                const int kr = e / (TT / 4), cw = e % (TT / 4);
+                const int gk = k0 + kr, gc = c0 + 4 * cw;
+                w[h][i] = (h < nt && gk < K && gc < cols)
+                              ? __ldg(reinterpret_cast<const uint32_t*>(G + (int64_t)gk * cols + gc)) : 0u;
+            }
         }
+#pragma unroll
+        for (int h = 0; h < TT_ROUND; h++)
+#pragma unroll
+            for (int i = 0; i < TT * TT / 4 / THREADS; i++) {
+                const int e = threadIdx.x + i * THREADS;
+                *reinterpret_cast<uint32_t*>(&tile[h][e / (TT / 4)][4 * (e % (TT / 4))]) = w[h][i];
+            }
         __syncthreads();
         // rows c0 .. c0 + 63 of G^T, 16 bytes (16 k) per thread and step (k is a multiple of 16)
-        for (int e = threadIdx.x; e < TT * TT / 16; e += THREADS) {
-            const int n = e / (TT / 16), kc = e % (TT / 16);
-            const int gc = c0 + n, gk = k0 + 16 * kc;
-            if (gc < cols && gk < K) {
-                uint32_t w[4];
+        for (int h = 0; h < nt; h++) {
+            const int64_t t = t0 + h;
+            const int k0 = (int)(t / nct) * TT, c0 = (int)(t % nct) * TT;
+            for (int e = threadIdx.x; e < TT * TT / 16; e += THREADS) {
+                const int n = e / (TT / 16), kc = e % (TT / 16);
+                const int gc = c0 + n, gk = k0 + 16 * kc;
+                if (gc < cols && gk < K) {
+                    uint32_t o[4];
 #pragma unroll
-                for (int q = 0; q < 4; q++)
-                    w[q] = (uint32_t)tile[16 * kc + 4 * q][n] | ((uint32_t)tile[16 * kc + 4 * q + 1][n] << 8) |
-                           ((uint32_t)tile[16 * kc + 4 * q + 2][n] << 16) | ((uint32_t)tile[16 * kc + 4 * q + 3][n] << 24);
-                *reinterpret_cast<uint4*>(GT + (int64_t)gc * K + gk) = make_uint4(w[0], w[1], w[2], w[3]);
+                    for (int q = 0; q < 4; q++)
+                        o[q] = (uint32_t)tile[h][16 * kc + 4 * q][n] | ((uint32_t)tile[h][16 * kc + 4 * q + 1][n] << 8) |
+                               ((uint32_t)tile[h][16 * kc + 4 * q + 2][n] << 16) |
+                               ((uint32_t)tile[h][16 * kc + 4 * q + 3][n] << 24);
+                    *reinterpret_cast<uint4*>(GT + (int64_t)gc * K + gk) = make_uint4(o[0], o[1], o[2], o[3]);
+                }
             }
         }
         __syncthreads();
@@ -429,7 +451,7 @@ __device__ __forceinline__ void transpose_segment(const BatchK& k, const DevJob*
 }
 
 __global__ void __launch_bounds__(THREADS) k_batch_entangle(BatchK k) {
-    __shared__ uint8_t tile[TT][TT + 4];
+    __shared__ uint8_t tile[TT_ROUND][TT][TT + 4];
     bool ok = true;
     for (int si = blockIdx.x; si < k.nsegs; si += gridDim.x) {
         const DevSeg sg = k.segs[si];
