@@ -895,11 +895,11 @@ def batch_launches(info):
     """Kernel launches of one ne_batch_run: the segment entangle, the product-
     and convolution-tile launches, and for transform jobs the forward pass, the
     block transforms (register-resident for L >= 2^14, radix 2 below), the
-    outer inverse pass and one final launch per M of 3, 4, 5."""
+    outer inverse pass and the final pass (a second one for M > 5)."""
     n = int(info.nsegs > 0) + int(info.ngemm_tiles > 0) + int(info.ntiles > info.ngemm_tiles)
     if info.ntransform:
         big, small = info.ntt_max_logL >= 14, info.ntt_min_logL < 14
-        n += 1 + 2 * int(big) + 2 * int(small) + int(info.ntt_max_logL > 14) + 3
+        n += 1 + 2 * int(big) + 2 * int(small) + int(info.ntt_max_logL > 14) + 1 + int(info.ntt_max_M > 5)
     return n
 
 

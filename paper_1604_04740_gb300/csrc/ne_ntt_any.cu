@@ -552,17 +552,15 @@ __device__ __forceinline__ int64_t fault_lower_bound(const int64_t* pos, int64_t
     return lo;
 }
 
-// fold, CRT, extraction / check / faults, 32 positions per warp
+// fold, CRT, extraction / check / faults of one job, 32 positions per warp
 template <int MT>
-__global__ void __launch_bounds__(256) k_final(const NttAnyArgs a) {
+__device__ __forceinline__ void final_job(const NttAnyArgs& a, const NJob& j) {
     constexpr int MR = MT ? MT : 16;
     const int lane = threadIdx.x & 31;
     const uint32_t P1 = prime(0), P2 = prime(1);
     const uint32_t inv = a.crt_inv, invq = a.crt_invq;           // P1^-1 mod P2 and its Shoup quotient
     const uint64_t PP = (uint64_t)P1 * P2;
-    for (int64_t b = blockIdx.y; b < a.jobs.njobs; b += gridDim.y) {
-        const NJob j = job_of(a.jobs, b);
-        if (j.L == 0 || (MT && j.M != MT) || (!MT && a.jobs.table && j.M <= 5)) continue;
+    {
         const int Mv = MT ? MT : j.M;
         const bool folded = j.L != j.N;
         for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) & ~31ll; base < j.N;
@@ -642,6 +640,30 @@ __global__ void __launch_bounds__(256) k_final(const NttAnyArgs a) {
     }
 }
 
+// MT = 3, 4, 5: the jobs with that M; MT = 0: the jobs with M > 5
+template <int MT>
+__global__ void __launch_bounds__(256) k_final(const NttAnyArgs a) {
+    for (int64_t b = blockIdx.y; b < a.jobs.njobs; b += gridDim.y) {
+        const NJob j = job_of(a.jobs, b);
+        if (j.L == 0 || (MT ? j.M != MT : j.M <= 5)) continue;
+        final_job<MT>(a, j);
+    }
+}
+
+// a table of jobs with M in 3 .. 5, each on the code for its M (one launch)
+__global__ void __launch_bounds__(256) k_final_mixed(const NttAnyArgs a) {
+    for (int64_t b = blockIdx.y; b < a.jobs.njobs; b += gridDim.y) {
+        const NJob j = job_of(a.jobs, b);
+        if (j.L == 0) continue;
+        switch (j.M) {
+            case 3: final_job<3>(a, j); break;
+            case 4: final_job<4>(a, j); break;
+            case 5: final_job<5>(a, j); break;
+            default: break;            // M > 5: k_final<0>
+        }
+    }
+}
+
 }  // namespace ntt2
 
 void ntt_any_job_constants(NJob& j) {
@@ -712,10 +734,8 @@ ne_status ntt_any_run(NttAnyArgs& a, int min_logL, int max_logL, int max_M, int6
     const int64_t maxN = (int64_t)1 << max_logL;
     const unsigned fx = gx_for(maxN, 256);
     if (a.jobs.table) {
-        // a table may mix M: one specialised launch per M (each skips the other jobs)
-        ntt2::k_final<3><<<dim3(fx, gy), 256, 0, s>>>(a);
-        ntt2::k_final<4><<<dim3(fx, gy), 256, 0, s>>>(a);
-        ntt2::k_final<5><<<dim3(fx, gy), 256, 0, s>>>(a);
+        // a table may mix M: one launch for M in 3 .. 5, another for larger M
+        ntt2::k_final_mixed<<<dim3(fx, gy), 256, 0, s>>>(a);
         if (max_M > 5) ntt2::k_final<0><<<dim3(fx, gy), 256, 0, s>>>(a);
         return check_launch("ne_cconv_ntt_any: final");
     }

@@ -34,7 +34,8 @@ def host(t):
 # powers of two (cyclic transforms) and other lengths (linear, folded), with
 # and without passes outside shared memory (transform lengths above 2^14)
 @pytest.mark.parametrize("M,N,B", [(3, 2, 3), (3, 3, 2), (4, 64, 5), (3, 100, 4), (5, 1000, 2), (3, 1024, 3),
-                                   (4, 4096, 2), (3, 5000, 2), (3, 8192, 1), (4, 9000, 1)])
+                                   (4, 4096, 2), (3, 5000, 2), (3, 8192, 1), (4, 9000, 1),
+                                   (8, 3000, 2), (6, 20000, 1)])
 def test_ntt_any_matches_oracle(ne, M, N, B):
     l = oracle.choose_l(M, 64, N * 2 ** 14, oracle.POLICY_BYTE)[0]
     p = ne.params(M, l)
