@@ -495,7 +495,8 @@ ne_status ne_batch_run(ne_batch_info info, const int32_t* c, const int8_t* ops, 
  *  - The first call on a device looks up the array's device address (one
  *    runtime query with that device current); make that first call before
  *    any stream capture.
- *  - The planning copies the tables synchronously with respect to the host.
+ *  - The planning's table copy is ordered on s, before the run; consecutive
+ *    calls on one stream therefore never see each other's tables.
  *  - All calls share the one array: calls whose work overlaps on the GPU
  *    (other streams, other host threads) overwrite each other's scratch and
  *    race.  The array keeps the last call's contents; everything a run needs
