@@ -480,19 +480,27 @@ __device__ __forceinline__ void tile_hybrid(const TileArgs& a, uint8_t* smem) {
         for (int jb = 0; jb < NB; jb++) {
             const int blk_rel = (jb + uch - 1) % NB;     // where input block jb sits in the window
             const uint32_t srow = sig_s + blk_rel * MS * ROWB;
+            // 8 input positions per step: the digit-plane words are the same for
+            // every lane (one 8-byte broadcast load per plane), the filter words
+            // per lane and output
 #pragma unroll 2
-            for (int jj = 0; jj < T; jj += 4) {
+            for (int jj = 0; jj < T; jj += 8) {
                 const int j = jb * T + jj;
-                uint32_t s[MS];
+                uint2 s[MS];
 #pragma unroll
-                for (int ms = 0; ms < MS; ms++) s[ms] = lds32(srow + ms * ROWB + jj);
-                uint32_t gw[R];
+                for (int ms = 0; ms < MS; ms++) s[ms] = lds64(srow + ms * ROWB + jj);
+                uint32_t gw[2][R];
 #pragma unroll
-                for (int r = 0; r < R; r++) gw[r] = lds32(gd + j - DT * r);
+                for (int h = 0; h < 2; h++)
+#pragma unroll
+                    for (int r = 0; r < R; r++) gw[h][r] = lds32(gd + j + 4 * h - DT * r);
 #pragma unroll
                 for (int r = 0; r < R; r++)
 #pragma unroll
-                    for (int ms = 0; ms < MS; ms++) acc[r][ms] = __dp4a((int)s[ms], (int)gw[r], acc[r][ms]);
+                    for (int ms = 0; ms < MS; ms++) {
+                        acc[r][ms] = __dp4a((int)s[ms].x, (int)gw[0][r], acc[r][ms]);
+                        acc[r][ms] = __dp4a((int)s[ms].y, (int)gw[1][r], acc[r][ms]);
+                    }
             }
         }
 #pragma unroll
