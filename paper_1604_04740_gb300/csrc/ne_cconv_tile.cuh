@@ -388,30 +388,34 @@ __device__ __forceinline__ void tile_hybrid(const TileArgs& a, uint8_t* smem) {
     // -- loads (every thread) --
     load_window<RAW>(a, sig, WB, -(uch - 1), NB, NTHR);
     cp_async_commit();
-    const int top = T * uch;
-    for (int e = tid; e < 4 * (GW / 4); e += NTHR) {
-        const int rr = e / (GW / 4), zw = e - rr * (GW / 4);
+    // the filter, staged once in the stash's space (free until the stash is
+    // written): 4-byte loads instead of a global byte load per copied byte
+    uint8_t* gs = reinterpret_cast<uint8_t*>(stash);
+    for (int e = tid; e < N / 4; e += NTHR)
+        *reinterpret_cast<uint32_t*>(gs + 4 * e) = __ldg(reinterpret_cast<const uint32_t*>(a.g) + e);
+    __syncthreads();
+    // the word of filter bytes g[(v - k) mod N], k = 0..3 (v reduced once)
+    auto gword = [&](int v) {
+        while (v < 0) v += N;
+        while (v >= N) v -= N;
         uint32_t w = 0;
 #pragma unroll
         for (int k = 0; k < 4; k++) {
-            int idx = (top - (4 * zw + k + rr - PADB)) % N;
-            if (idx < 0) idx += N;
-            w |= (uint32_t)(uint8_t)__ldg(a.g + idx) << (8 * k);
+            const int idx = v - k < 0 ? v - k + N : v - k;
+            w |= (uint32_t)gs[idx] << (8 * k);
         }
-        *reinterpret_cast<uint32_t*>(gcp + rr * GW + 4 * zw) = w;
+        return w;
+    };
+    const int top = T * uch;
+    for (int e = tid; e < 4 * (GW / 4); e += NTHR) {
+        const int rr = e / (GW / 4), zw = e - rr * (GW / 4);
+        *reinterpret_cast<uint32_t*>(gcp + rr * GW + 4 * zw) = gword(top - (4 * zw + rr - PADB));
     }
     // dp4a copies: copy rr, byte z holds g[(N + 4 - z - rr) mod N], i.e. the
     // reversed filter at offset y = z + rr - N - 4
     for (int e = tid; e < 4 * GDPW; e += NTHR) {
         const int rr = e / GDPW, zw = e - rr * GDPW;
-        uint32_t w = 0;
-#pragma unroll
-        for (int k = 0; k < 4; k++) {
-            int idx = (N + 4 - (4 * zw + k) - rr) % N;
-            if (idx < 0) idx += N;
-            w |= (uint32_t)(uint8_t)__ldg(a.g + idx) << (8 * k);
-        }
-        *reinterpret_cast<uint32_t*>(gdp + gdp_off(rr) + 4 * zw) = w;
+        *reinterpret_cast<uint32_t*>(gdp + gdp_off(rr) + 4 * zw) = gword(N + 4 - 4 * zw - rr);
     }
     cp_async_wait<0>();
     __syncthreads();
