@@ -87,11 +87,23 @@ __device__ __forceinline__ int64_t lower_bound(const int64_t* pos, int64_t n, in
     return lo;
 }
 
-template <int MT>
-__device__ __forceinline__ void epilogue(const TileArgs& a, const int32_t* stash, int p0, int npb,
-                                         int nthreads = THREADS) {
+// LT: the job's l when it is 16 (every shift below is then a constant; with
+// the two digits at shifts 0 and 16 of the byte-aligned plan of int8-valued
+// streams, the recombination is one shift-add), else 0
+template <int MT, int LT>
+__device__ __forceinline__ void epilogue_l(const TileArgs& a, const int32_t* stash, int p0, int npb, int nthreads) {
     const int M = MT ? MT : a.M;
     const int S = a.S;
+    const int l = LT ? LT : a.l;
+    const bool two = LT && S == 2 && a.shift[0] == 0 && a.shift[1] == LT;
+    auto digits = [&](const int32_t* sp, int m) {
+        if (two) return (int64_t)sp[2 * m * NPB * SP] + (int64_t)((uint64_t)(int64_t)sp[(2 * m + 1) * NPB * SP] << LT);
+        int64_t v = 0;
+#pragma unroll
+        for (int s = 0; s < NE_MAX_DIGITS; s++)
+            if (s < S) v += shl64(sp[(m * S + s) * NPB * SP], a.shift[s]);
+        return v;
+    };
     const int lane = threadIdx.x & 31;
     const int npos = npb * T;
     const int64_t i0 = (int64_t)p0 * T;
@@ -108,10 +120,7 @@ __device__ __forceinline__ void epilogue(const TileArgs& a, const int32_t* stash
         const int32_t* sp = stash + pr * SP + q;
         if (a.fuse == NE_FUSE_NONE) {
             for (int m = 0; m < M; m++) {
-                int64_t v = 0;
-#pragma unroll
-                for (int s = 0; s < NE_MAX_DIGITS; s++)
-                    if (s < S) v += shl64(sp[(m * S + s) * NPB * SP], a.shift[s]);
+                int64_t v = digits(sp, m);
                 for (int64_t f = f0; f < f1; f++)
                     if (a.fault_pos[f] == i0 + i && a.fault_stream[f] == m) v ^= (int64_t)(1ull << a.fault_bit[f]);
                 a.out[(int64_t)m * a.N + i0 + i] = v;
@@ -126,15 +135,13 @@ __device__ __forceinline__ void epilogue(const TileArgs& a, const int32_t* stash
             if (m >= M) m -= M;
             int64_t v = 0;
             if (j > 0 || need_r) {
-#pragma unroll
-                for (int s = 0; s < NE_MAX_DIGITS; s++)
-                    if (s < S) v += shl64(sp[(m * S + s) * NPB * SP], a.shift[s]);
+                v = digits(sp, m);
                 for (int64_t f = f0; f < f1; f++)
                     if (a.fault_pos[f] == i0 + i && a.fault_stream[f] == m) v ^= (int64_t)(1ull << a.fault_bit[f]);
             }
             rot[j] = v;
         }
-        const bool flag = extract_rot<MT>(rot, M, a.l, check, res);
+        const bool flag = extract_rot<MT>(rot, M, l, check, res);
 #pragma unroll
         for (int j = 0; j < (MT ? MT : 32); j++) {
             if (!MT && j >= M) break;
@@ -155,6 +162,13 @@ __device__ __forceinline__ void epilogue(const TileArgs& a, const int32_t* stash
             }
         }
     }
+}
+
+template <int MT>
+__device__ __forceinline__ void epilogue(const TileArgs& a, const int32_t* stash, int p0, int npb,
+                                         int nthreads = THREADS) {
+    if (a.l == 16) epilogue_l<MT, 16>(a, stash, p0, npb, nthreads);
+    else epilogue_l<MT, 0>(a, stash, p0, npb, nthreads);
 }
 
 // bytes t of four words, XOR 0x80: four consecutive positions of one digit plane
