@@ -451,6 +451,7 @@ typedef struct {               /* what ne_batch_run needs to know on the host   
     int64_t ntt_table_off;     /* byte offsets of the transform jobs' table and scratch       */
     int64_t ntt_ws_off;
     int64_t ntt_units;         /* the largest (M + 1) L of the transform jobs                 */
+    int64_t table_bytes;       /* host bytes of the plan's tables (ne_batch_plan_staged)      */
 } ne_batch_info;
 
 /* Plan a batch: choose l and the digit plan of every job, lay out the digit
@@ -464,6 +465,16 @@ typedef struct {               /* what ne_batch_run needs to know on the host   
  * range. */
 ne_status ne_batch_plan(const ne_job* jobs, int32_t njobs, ne_batch_config cfg, void* workspace,
                         int64_t workspace_bytes, ne_batch_info* info, cudaStream_t s);
+
+/* As ne_batch_plan, with the tables built in `staging`, a pinned host buffer
+ * of at least info->table_bytes bytes (from a plan without a workspace), and
+ * uploaded from it asynchronously on s: the call never waits for the copy
+ * engines.  The caller keeps staging untouched until the upload has
+ * completed (for instance until the batch run on s has).  workspace may be
+ * null to only size the plan, as for ne_batch_plan. */
+ne_status ne_batch_plan_staged(const ne_job* jobs, int32_t njobs, ne_batch_config cfg, void* workspace,
+                               int64_t workspace_bytes, void* staging, int64_t staging_bytes, ne_batch_info* info,
+                               cudaStream_t s);
 
 /* Run a planned batch.  c: int32 stream arena, ops: int8 operator arena,
  * out: int64 output arena (d_hat of every job), flags: check bitmaps (all

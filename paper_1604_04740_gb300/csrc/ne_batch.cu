@@ -607,8 +607,11 @@ ne_status plain_digits(int32_t lo, int32_t hi, ne_digits* dg) {
 
 }  // namespace
 
-extern "C" ne_status ne_batch_plan(const ne_job* jobs, int32_t njobs, ne_batch_config cfg, void* workspace,
-                                   int64_t workspace_bytes, ne_batch_info* info, cudaStream_t s) {
+// the plan; with a workspace its tables are uploaded on s, from the pinned
+// host buffer staging when one is given (a copy that never waits for the host)
+static ne_status plan_batch(const ne_job* jobs, int32_t njobs, ne_batch_config cfg, void* workspace,
+                            int64_t workspace_bytes, void* staging, int64_t staging_bytes, ne_batch_info* info,
+                            cudaStream_t s) {
     if (!info || (njobs > 0 && !jobs) || njobs < 0) return fail(NE_EINVAL, "ne_batch_plan: bad arguments");
     if (cfg.ctas_per_sm < 1 || cfg.ctas_per_sm > 4) return fail(NE_EINVAL, "ne_batch_plan: ctas_per_sm=%d", cfg.ctas_per_sm);
     if (cfg.order != NE_ORDER_JOB && cfg.order != NE_ORDER_LPT) return fail(NE_EINVAL, "ne_batch_plan: order=%d", cfg.order);
@@ -791,7 +794,11 @@ extern "C" ne_status ne_batch_plan(const ne_job* jobs, int32_t njobs, ne_batch_c
     info->ntt_table_off = L.ntt_table;
     info->ntt_ws_off = L.ntt_ws;
     info->ntt_units = ntt_units;
+    info->table_bytes = L.planes + (int64_t)nj.size() * (int64_t)sizeof(NJob);
     if (!workspace) return NE_OK;
+    if (staging && staging_bytes < info->table_bytes)
+        return fail(NE_EINVAL, "ne_batch_plan: staging buffer of %lld bytes < %lld", (long long)staging_bytes,
+                    (long long)info->table_bytes);
     if (!nj.empty()) {
         // the twiddle tables are filled here, outside any stream capture of the runs
         ne_status st = ntt_any_init_tables(s);
@@ -800,13 +807,21 @@ extern "C" ne_status ne_batch_plan(const ne_job* jobs, int32_t njobs, ne_batch_c
     if (workspace_bytes < L.total) return fail(NE_ENOMEM, "ne_batch_plan: workspace %lld < %lld bytes",
                                                (long long)workspace_bytes, (long long)L.total);
     if (!aligned(workspace, 256)) return fail(NE_EINVAL, "ne_batch_plan: workspace must be 256-byte aligned");
-    std::vector<uint8_t> host((size_t)L.planes, 0);
-    std::memcpy(host.data() + L.jobs, dj.data(), dj.size() * sizeof(DevJob));
+    std::vector<uint8_t> host_vec;
+    uint8_t* host;
+    if (staging) {
+        host = static_cast<uint8_t*>(staging);
+        std::memset(host, 0, (size_t)L.jobs);      // the counters (the gaps between tables are never read)
+    } else {
+        host_vec.assign((size_t)L.planes, 0);
+        host = host_vec.data();
+    }
+    std::memcpy(host + L.jobs, dj.data(), dj.size() * sizeof(DevJob));
     // the product tiles first (their own launch), then the convolution tiles;
     // within each list job order, or the most costly first (stable; all tiles
     // of a product job cost the same, so its jobs are sorted instead)
     const bool lpt = cfg.order == NE_ORDER_LPT;
-    DevTile* dst = reinterpret_cast<DevTile*>(host.data() + L.tiles);
+    DevTile* dst = reinterpret_cast<DevTile*>(host + L.tiles);
     if (lpt) std::stable_sort(gjobs.begin(), gjobs.end(), [](const GemmJob& x, const GemmJob& y) { return x.cost > y.cost; });
     for (const GemmJob& g : gjobs)
         for (int a = 0; a < g.rt; a++)
@@ -815,15 +830,33 @@ extern "C" ne_status ne_batch_plan(const ne_job* jobs, int32_t njobs, ne_batch_c
     for (size_t t = 0; t < idx.size(); t++) idx[t] = (uint32_t)t;
     if (lpt) std::stable_sort(idx.begin(), idx.end(), [&](uint32_t x, uint32_t y) { return cost_c[x] > cost_c[y]; });
     for (size_t t = 0; t < idx.size(); t++) *dst++ = tiles_c[idx[t]];
-    if (!segs.empty()) std::memcpy(host.data() + L.segs, segs.data(), segs.size() * sizeof(DevSeg));
-    if (cudaMemcpyAsync(workspace, host.data(), host.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
+    if (!segs.empty()) std::memcpy(host + L.segs, segs.data(), segs.size() * sizeof(DevSeg));
+    const void* njsrc = nj.data();
+    if (staging && !nj.empty()) {
+        std::memcpy(host + L.planes, nj.data(), nj.size() * sizeof(NJob));
+        njsrc = host + L.planes;
+    }
+    if (cudaMemcpyAsync(workspace, host, (size_t)L.planes, cudaMemcpyHostToDevice, s) != cudaSuccess)
         return check_launch("ne_batch_plan: copy tables");
-    if (!nj.empty() && cudaMemcpyAsync(static_cast<uint8_t*>(workspace) + L.ntt_table, nj.data(),
+    if (!nj.empty() && cudaMemcpyAsync(static_cast<uint8_t*>(workspace) + L.ntt_table, njsrc,
                                        nj.size() * sizeof(NJob), cudaMemcpyHostToDevice, s) != cudaSuccess)
         return check_launch("ne_batch_plan: copy transform jobs");
     // no wait: a copy from pageable memory returns once its bytes are staged
-    // (so the host vectors may go), and it is ordered on s before the runs
+    // (so the host vectors may go), one from the pinned staging buffer at once;
+    // both are ordered on s before the runs
     return NE_OK;
+}
+
+extern "C" ne_status ne_batch_plan(const ne_job* jobs, int32_t njobs, ne_batch_config cfg, void* workspace,
+                                   int64_t workspace_bytes, ne_batch_info* info, cudaStream_t s) {
+    return plan_batch(jobs, njobs, cfg, workspace, workspace_bytes, nullptr, 0, info, s);
+}
+
+extern "C" ne_status ne_batch_plan_staged(const ne_job* jobs, int32_t njobs, ne_batch_config cfg, void* workspace,
+                                          int64_t workspace_bytes, void* staging, int64_t staging_bytes,
+                                          ne_batch_info* info, cudaStream_t s) {
+    if (workspace && !staging) return fail(NE_EINVAL, "ne_batch_plan_staged: null staging buffer");
+    return plan_batch(jobs, njobs, cfg, workspace, workspace_bytes, staging, staging_bytes, info, s);
 }
 
 extern "C" ne_status ne_batch_run(ne_batch_info info, const int32_t* c, const int8_t* ops, int64_t* out, uint32_t* flags,

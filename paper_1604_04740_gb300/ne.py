@@ -61,7 +61,7 @@ class ne_batch_info(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in ("njobs", "ntiles", "nsegs", "grid", "ngemm_tiles", "gemm_grid")] + \
                [(n, ctypes.c_int64) for n in ("flag_words", "workspace_bytes", "mma_ops", "useful_ops")] + \
                [(n, ctypes.c_int32) for n in ("ntransform", "ntt_max_logL", "ntt_max_M", "ntt_min_logL")] + \
-               [(n, ctypes.c_int64) for n in ("ntt_table_off", "ntt_ws_off", "ntt_units")]
+               [(n, ctypes.c_int64) for n in ("ntt_table_off", "ntt_ws_off", "ntt_units", "table_bytes")]
 
 
 def params(M: int, l: int, w: int = 64) -> ne_params:
@@ -114,6 +114,8 @@ def _load():
         "ne_probe_imad_peak": [i32, ctypes.POINTER(i64), P],
         "ne_probe_mixed_peak": [i32, i32, i32, i32, i32, ctypes.POINTER(i64), P],
         "ne_batch_plan": [ctypes.POINTER(ne_job), i32, ne_batch_config, P, i64, ctypes.POINTER(ne_batch_info), P],
+        "ne_batch_plan_staged": [ctypes.POINTER(ne_job), i32, ne_batch_config, P, i64, P, i64,
+                                 ctypes.POINTER(ne_batch_info), P],
         "ne_batch_run": [ne_batch_info, P, P, P, P, P, P, P, P, P, P, P],
         "ne_batch_run_static": [ctypes.POINTER(ne_job), i32, ne_batch_config, P, P, P, P, P, P, P, P, P, P],
         "ne_copy_regions_h2d": [P, P, P, P, P, i64, P],
@@ -619,18 +621,28 @@ def _job_array(jobs):
     return ctypes.cast(a.ctypes.data, ctypes.POINTER(ne_job)), len(a)
 
 
-def ne_batch_plan(jobs, cfg: ne_batch_config, workspace: torch.Tensor | None = None) -> ne_batch_info:
+def ne_batch_plan(jobs, cfg: ne_batch_config, workspace: torch.Tensor | None = None,
+                  staging: torch.Tensor | None = None) -> ne_batch_info:
     """jobs: a ctypes array of ne_job or a numpy JOB_DTYPE array (host).
-    With workspace None only sizes the plan (info.workspace_bytes); otherwise
-    writes the tables into it (uint8 device tensor, 256-byte aligned) by a
-    copy ordered on the current stream: run the batch on the same stream."""
+    With workspace None only sizes the plan (info.workspace_bytes,
+    info.table_bytes); otherwise writes the tables into it (uint8 device
+    tensor, 256-byte aligned) by a copy ordered on the current stream: run the
+    batch on the same stream.  staging: a pinned uint8 host tensor of at least
+    info.table_bytes bytes to build the tables in and upload them from without
+    the host waiting (keep it untouched until the run on the stream is done)."""
     info = ne_batch_info()
     ws_ptr, ws_bytes = None, 0
     if workspace is not None:
         ws_ptr = _ptr(workspace, torch.uint8, "workspace")
         ws_bytes = workspace.numel()
     ptr, n = _job_array(jobs)
-    _call("ne_batch_plan", ptr, n, cfg, ws_ptr, ws_bytes, ctypes.byref(info), _stream())
+    if staging is None:
+        _call("ne_batch_plan", ptr, n, cfg, ws_ptr, ws_bytes, ctypes.byref(info), _stream())
+    else:
+        if staging.is_cuda or not staging.is_pinned() or staging.dtype != torch.uint8 or not staging.is_contiguous():
+            raise ValueError("staging must be a contiguous pinned uint8 host tensor")
+        _call("ne_batch_plan_staged", ptr, n, cfg, ws_ptr, ws_bytes, ctypes.c_void_p(staging.data_ptr()),
+              staging.numel(), ctypes.byref(info), _stream())
     return info
 
 

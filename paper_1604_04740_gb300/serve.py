@@ -137,6 +137,11 @@ class Server:
         # per-lane pinned words for the batch status and flag count (read without touching
         # the default stream, which would wait for every lane)
         self.status_h = [torch.zeros(1, dtype=torch.int32).pin_memory() for _ in range(lanes)]
+        # pinned per-lane staging for the plan tables: their upload never waits for the
+        # copy engines (a lane plans again only after its previous batch is done).  8 MiB
+        # holds the tables of about half a million tiles, so the loop itself rarely has
+        # to pin a larger buffer (a pinned allocation can take tens of milliseconds)
+        self.staging = [torch.empty(8 << 20, dtype=torch.uint8).pin_memory() for _ in range(lanes)]
         self.nflag_h = [torch.zeros(1, dtype=torch.int64).pin_memory() for _ in range(lanes)]
         self.flagged = 0
         # host-side timing of the last run: the longest loop iteration and the
@@ -144,6 +149,10 @@ class Server:
         self.max_iter_s = 0.0
         self.max_launch_s = 0.0
         self.max_phase_s = {"plan": 0.0, "copy": 0.0, "run": 0.0}
+        # the longest device span of a micro-batch (events on its lane, from before its
+        # input copies to after its status read) and how many requests it held
+        self.max_device_s = 0.0
+        self.max_device_requests = 0
 
     # -- one micro-batch: requests [a, b) ------------------------------------------------
     def _launch(self, T: _Table, a: int, b: int, lane: int):
@@ -179,8 +188,12 @@ class Server:
         status = v(int(starts[5]), 256, torch.int32)[:1]
         ws = v(int(starts[6]), parts[6], torch.uint8)
         stream = self.streams[lane]
+        if self.staging[lane].numel() < info.table_bytes:
+            self.staging[lane] = torch.empty(2 * info.table_bytes, dtype=torch.uint8).pin_memory()
+        ev0 = torch.cuda.Event(enable_timing=True)
         with torch.cuda.stream(stream):
-            info = ne.ne_batch_plan(jobs, self.cfg, ws)
+            ev0.record(stream)
+            info = ne.ne_batch_plan(jobs, self.cfg, ws, staging=self.staging[lane])
             t_c = time.perf_counter()
             ne.ne_copy_regions_h2d(c, self.c_host, c_off * 4, T.c_pool[a:b] * 4, T.c_elems[a:b] * 4)
             ne.ne_copy_regions_h2d(ops, self.op_host, op_off, T.op_pool[a:b], T.op_bytes[a:b])
@@ -189,17 +202,20 @@ class Server:
             ne.ne_batch_run(info, c, ops, out, flags, nflag, ws, status=status)
             self.status_h[lane].copy_(status, non_blocking=True)
             self.nflag_h[lane].copy_(nflag, non_blocking=True)
-            ev = torch.cuda.Event()
+            ev = torch.cuda.Event(enable_timing=True)
             ev.record(stream)
         t_e = time.perf_counter()
         for phase, dt in (("plan", t_c - t_p), ("copy", t_r - t_c), ("run", t_e - t_r)):
             self.max_phase_s[phase] = max(self.max_phase_s[phase], dt)
-        return dict(ev=ev, region=(off, nb), a=a, b=b, out=out, out_off=out_off, lane=lane)
+        return dict(ev0=ev0, ev=ev, region=(off, nb), a=a, b=b, out=out, out_off=out_off, lane=lane)
 
     def _finish(self, fl, T: _Table, reqs, t):
         for i in range(fl["a"], fl["b"]):
             reqs[i].done = t
         lane = fl["lane"]
+        dev_s = fl["ev0"].elapsed_time(fl["ev"]) * 1e-3
+        if dev_s > self.max_device_s:
+            self.max_device_s, self.max_device_requests = dev_s, fl["b"] - fl["a"]
         if int(self.status_h[lane][0]) != 0:
             raise RuntimeError("a request's inputs left the planned value range")
         self.flagged += int(self.nflag_h[lane][0])
@@ -251,6 +267,7 @@ class Server:
             rq.arrival = float(arr[i])
         self.max_iter_s = self.max_launch_s = 0.0
         self.max_phase_s = {"plan": 0.0, "copy": 0.0, "run": 0.0}
+        self.max_device_s, self.max_device_requests = 0.0, 0
         last = time.perf_counter()
         while done < n:
             now = time.perf_counter()

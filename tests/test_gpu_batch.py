@@ -234,3 +234,27 @@ def test_plan_rejects_bad_jobs(mods):
         b = B.Batch([bad], generate=False)
         with pytest.raises(ne.NEError):
             b.plan(B.default_config())
+
+
+def test_staged_plan_uploads_the_same_tables(mods):
+    B, ne = mods
+    b = B.Batch(small_specs(B, ne) + [B.JobSpec(ne.NE_JOB_CCONV, 3, N=4160)], seed=10, fault_rate=1e-3)
+    cfg = B.default_config(ntt_min_n=4096)
+    b.plan(cfg)
+    b.run()
+    torch.cuda.synchronize()
+    out0, fl0, nf0 = b.out.clone(), b.flags.clone(), int(b.nflag.item())
+    info = ne.ne_batch_plan(b.jobs, cfg)
+    assert info.table_bytes > 0 and info.ntransform == 1
+    with pytest.raises(ne.NEError):
+        ne.ne_batch_plan(b.jobs, cfg, b.ws_view, staging=torch.empty(info.table_bytes - 1, dtype=torch.uint8).pin_memory())
+    with pytest.raises(ValueError):
+        ne.ne_batch_plan(b.jobs, cfg, b.ws_view, staging=torch.empty(info.table_bytes, dtype=torch.uint8))
+    # stale tables in the workspace and garbage in the staging buffer change nothing
+    b.ws_view.fill_(0xA5)
+    staging = torch.full((info.table_bytes + 64,), 0x5A, dtype=torch.uint8).pin_memory()
+    b.info = ne.ne_batch_plan(b.jobs, cfg, b.ws_view, staging=staging)
+    b.out.fill_(0)
+    b.run()
+    torch.cuda.synchronize()
+    assert torch.equal(b.out, out0) and torch.equal(b.flags, fl0) and int(b.nflag.item()) == nf0
