@@ -782,7 +782,32 @@ def cconv_extras(torch, ne, wl, dev, flush, step, p, dg, planes, g, out, ms_step
         name: {"bytes": nbytes, "ms": pass_ms[name], "GB/s": nbytes / (pass_ms[name] * 1e-3) / 1e9,
                "frac": nbytes / (pass_ms[name] * 1e-3) / 1e9 / hbm_peak if hbm_peak else None}
         for name, (_, nbytes) in passes.items()}
+    res["check_read_sweep"] = check_read_sweep(torch, ne, pl, G, M, N, dev, flush)
     return res
+
+
+def check_read_sweep(torch, ne, pl, G, M, N, dev, flush):
+    """The read-only check at 1x, 4x and 12x the workload's groups, with the
+    int64 family's l and with l = 16, beside a plain read-only stream of the
+    same bytes (torch's sum): a read stream of about 100 MB pays a fixed start
+    and drain of several microseconds that a larger one amortises (a copy of
+    that size hides it: its writes end in L2)."""
+    out = {}
+    p16 = ne.params(M, 16)
+    for mult in (1, 4, 12):
+        g = G * mult
+        d = torch.randint(-(2 ** 40), 2 ** 40, (g, M, N), dtype=torch.int64, device=dev)
+        fl = torch.empty(g * ((N + 31) // 32), dtype=torch.int32, device=dev)
+        t_c, _ = timed_steps(torch, lambda ev: ne.ne_check(pl, d, 0, fl, None), 10, 3, flush)
+        t_16, _ = timed_steps(torch, lambda ev: ne.ne_check(p16, d, 0, fl, None), 10, 3, flush)
+        t_s, _ = timed_steps(torch, lambda ev: d.sum(), 10, 3, flush)
+        nb = d.numel() * 8
+        out[f"{nb / 1e6:.0f}MB"] = {f"check_l{pl.l}_GB/s": nb / (t_c / 10 * 1e-3) / 1e9,
+                                    "check_l16_GB/s": nb / (t_16 / 10 * 1e-3) / 1e9,
+                                    "read_stream_GB/s": nb / (t_s / 10 * 1e-3) / 1e9}
+        del d, fl
+    torch.cuda.empty_cache()
+    return out
 
 
 def gemm_extras(torch, ne, wl, dev, flush, p, dg, planes, Gm, out, ms_step):
@@ -1112,6 +1137,11 @@ def run_serve(args, rank, world, local_rank):
 
 def main():
     args = parse()
+    if args.workload == "serve":
+        # a serving process loads every kernel module when CUDA starts: loaded
+        # lazily, the first launch of a kernel the warm-up did not reach (one
+        # transform length, one M) stalls its micro-batch for tens of ms
+        os.environ.setdefault("CUDA_MODULE_LOADING", "EAGER")
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

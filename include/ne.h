@@ -242,9 +242,14 @@ ne_status ne_extract(ne_params p, const int64_t* delta, int64_t* d_hat,
 
 /* Eq. 24: flag a position when delta_r != d_r + 2^l d_{r-1}, with d_r and
  * d_{r-1} of Eq. 18-19 computed exactly from the other streams.  Any fault
- * confined to one stream of a position is flagged (Prop. 4). */
+ * confined to one stream of a position is flagged (Prop. 4).  delta: int64
+ * [batch][M][n]; flags/nflag as for ne_extract (at least one non-null).
+ * With n even and delta 16-byte aligned the reads are staged in shared memory
+ * by bulk copies; if such a copy fails to arrive within the kernel's bounded
+ * wait, the positions it carried are reported flagged and *status is set to
+ * NE_ETIMEOUT (status: device int32, nullable, otherwise left untouched). */
 ne_status ne_check(ne_params p, const int64_t* delta, int64_t batch, int64_t n, int32_t r,
-                   uint32_t* flags, uint64_t* nflag, cudaStream_t s);
+                   uint32_t* flags, uint64_t* nflag, int32_t* status, cudaStream_t s);
 
 /* Prop. 3: stream r_lost is unavailable (never read, may hold anything);
  * all M outputs are rebuilt from the other M-1. */

@@ -34,6 +34,22 @@ __device__ __forceinline__ i128 shl128(i128 x, int s) { return (i128)((u128)x <<
 // arithmetic (floor) shift; nvcc implements >> on signed 128-bit as arithmetic
 __device__ __forceinline__ i128 sar128(i128 x, int s) { return x >> s; }
 
+// the same two shifts for 1 <= s <= 63, from 64-bit halves: the shifts of
+// the extraction are l and (M-1) l, both in that range under Eq. 13 with
+// w = 64, and a general 128-bit shift costs several times as many
+// instructions when s is not a compile-time constant
+__device__ __forceinline__ i128 shl128_63(i128 x, int s) {
+    const uint64_t lo = (uint64_t)x, hi = (uint64_t)((u128)x >> 64);
+    const uint64_t h = (hi << s) | (lo >> (64 - s));
+    return (i128)(((u128)h << 64) | (u128)(lo << s));
+}
+__device__ __forceinline__ i128 sar128_63(i128 x, int s) {
+    const uint64_t lo = (uint64_t)x;
+    const int64_t hi = (int64_t)(x >> 64);
+    const uint64_t h = (uint64_t)(hi >> s);
+    return (i128)(((u128)h << 64) | (u128)((lo >> s) | ((uint64_t)hi << (64 - s))));
+}
+
 // sign extension of the low L bits of a word, 1 <= L <= 63 (Eq. 18)
 __device__ __forceinline__ int64_t sext_low(uint64_t lo, int L) {
     return (int64_t)(lo << (64 - L)) >> (64 - L);

@@ -6,6 +6,7 @@
 // group (VEC = 2 with 16-byte loads when possible), so each segment maps to
 // whole uint32 words of the flag bitmap and the flags are assembled with
 // warp shuffles, not atomics.
+#include "ne_bulk.cuh"
 #include "ne_common.cuh"
 #include "ne_extract.cuh"
 #include "ne_flags.cuh"
@@ -92,6 +93,173 @@ __global__ void __launch_bounds__(TH) k_extract(const int64_t* __restrict__ delt
                 if constexpr (CHECK) emit_flags<VEC>(f, lane, seg, wpr, fb, nflag);
             }
         }
+    }
+}
+
+// ---- the read-only check with the reads staged in shared memory ----------------
+//
+// A unit is PER x TH consecutive positions of one group (all M streams).  Each
+// block of a persistent launch walks the units gridDim.x apart through a ring
+// of S shared-memory stages: one thread issues the M bulk copies of a unit
+// (cp.async.bulk completing on the stage's mbarrier) S units ahead, so the
+// block keeps them in flight however long the check of the current one takes.
+// A warp checks 32 PER consecutive positions of a unit, a lane PER / 2 pairs
+// of them, each pair of a stream read as one 16-byte shared-memory load.
+// Requires n even and delta 16-byte aligned (every copy then starts and ends
+// on 16 bytes).
+constexpr uint32_t CK_WAIT_LIMIT = 1u << 22;
+
+// TH threads, PER positions per thread and unit (2 or 4), S stages
+template <int MT, int LT, int TH, int PER, int S>
+__global__ void __launch_bounds__(TH, 1) k_check_staged(const int64_t* __restrict__ delta, int l, int r,
+                                                        int64_t batch, int64_t n, uint32_t* __restrict__ flags,
+                                                        unsigned long long* nflag, int32_t* status) {
+    constexpr int CK_POS = PER * TH;
+    constexpr int WPOS = 32 * PER;                      // positions of a warp
+    extern __shared__ __align__(128) int64_t ring[];   // [S][MT][CK_POS]
+    __shared__ uint64_t full[S];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t upg = (n + CK_POS - 1) / CK_POS;      // units per group
+    const int64_t nunits = batch * upg;
+    const int64_t wpr = (n + 31) / 32;
+    const int lv = LT ? LT : l;
+    // unit u = (group b, chunk c); the walk adds gridDim.x units per step
+    const int64_t sb = gridDim.x / upg, sc = gridDim.x % upg;
+    auto next = [&](int64_t& b, int64_t& c) {
+        b += sb;
+        c += sc;
+        if (c >= upg) { c -= upg; b++; }
+    };
+    auto issue = [&](int64_t b, int64_t c, int s) {
+        const int64_t p0 = c * CK_POS;
+        const int64_t len = n - p0 < CK_POS ? n - p0 : CK_POS;
+        const uint32_t bytes = (uint32_t)len * 8;
+        mbar_arrive_expect(&full[s], bytes * MT);
+#pragma unroll
+        for (int m = 0; m < MT; m++)
+            bulk_copy_g2s(ring + (s * MT + m) * CK_POS, delta + (b * MT + m) * n + p0, bytes, &full[s]);
+    };
+    if (tid == 0) {
+#pragma unroll
+        for (int s = 0; s < S; s++) mbar_init(&full[s], 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    int64_t b = blockIdx.x / upg, c = blockIdx.x % upg;
+    // the issuing thread's walk runs S units ahead
+    int64_t iu = blockIdx.x, ib = b, ic = c;
+    if (tid == 0) {
+#pragma unroll
+        for (int s = 0; s < S; s++) {
+            if (iu < nunits) issue(ib, ic, s);
+            iu += gridDim.x;
+            next(ib, ic);
+        }
+    }
+    int it = 0;
+    for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x, it++, next(b, c)) {
+        const int s = it % S;
+        const bool ok = mbar_wait(&full[s], (uint32_t)(it / S) & 1u, CK_WAIT_LIMIT);
+        const int64_t p0 = c * CK_POS;
+        const int64_t* st = ring + s * MT * CK_POS;
+#pragma unroll
+        for (int k = 0; k < PER / 2; k++) {
+            const int q = warp * WPOS + k * 64 + lane * 2;   // position within the unit
+            uint32_t f = 0;
+            if (p0 + q < n) {
+                if (ok) {
+                    int64_t rot[2][MT];
+#pragma unroll
+                    for (int j = 0; j < MT; j++) {
+                        int m = r + j;
+                        if (m >= MT) m -= MT;
+                        const longlong2 v = *reinterpret_cast<const longlong2*>(st + m * CK_POS + q);
+                        rot[0][j] = v.x;
+                        rot[1][j] = v.y;
+                    }
+#pragma unroll
+                    for (int v = 0; v < 2; v++) {
+                        int64_t out[MT];
+                        if (extract_rot<MT>(rot[v], MT, lv, true, out)) f |= 1u << v;
+                    }
+                } else {
+                    f = 3u;                             // not checked: reported as flagged
+                }
+            }
+            emit_flags<2>(f, lane, (p0 + warp * WPOS + k * 64) / 64, wpr, flags ? flags + b * wpr : nullptr, nflag);
+        }
+        if (!__syncthreads_and(ok)) {
+            // a copy did not arrive: report it, wait (bounded) for the copies
+            // still in flight into this block's stages, and leave
+            if (tid == 0) {
+                if (status) atomicExch(status, (int32_t)NE_ETIMEOUT);
+                for (int k = 0; k < S; k++) {
+                    const int jt = it + k;
+                    if (u + (int64_t)k * gridDim.x < nunits)
+                        mbar_wait(&full[jt % S], (uint32_t)(jt / S) & 1u, CK_WAIT_LIMIT);
+                }
+            }
+            return;
+        }
+        if (tid == 0) {
+            if (iu < nunits) {
+                fence_async_shared();
+                issue(ib, ic, s);
+            }
+            iu += gridDim.x;
+            next(ib, ic);
+        }
+    }
+}
+
+template <int MT, int LT, int TH, int PER, int S>
+void launch_check_staged_v(const int64_t* delta, int l, int r, int64_t batch, int64_t n, uint32_t* flags,
+                           unsigned long long* nflag, int32_t* status, cudaStream_t s) {
+    static int per_sm = -1;                              // resident blocks per SM (once per process)
+    constexpr int smem = S * MT * PER * TH * 8;
+    auto kern = k_check_staged<MT, LT, TH, PER, S>;
+    if (per_sm < 0) {
+        // the ring plus the static barriers pass the 48 KB default
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, TH, smem) != cudaSuccess || b < 1) b = 1;
+        per_sm = b;
+    }
+    const int64_t nunits = batch * ((n + PER * TH - 1) / (PER * TH));
+    int64_t grid = (int64_t)sm_count() * per_sm;
+    if (grid > nunits) grid = nunits;
+    kern<<<(unsigned)grid, TH, smem, s>>>(delta, l, r, batch, n, flags, nflag, status);
+}
+
+// 256 threads of 4 positions and 3 stages (2 for M > 4): three blocks per SM
+// for M = 3.  Measured on the check of 4096 x 3 x 1024 words against 2 x 2,
+// 4 x 4 and 2 x 4 stages and 128 / 512-thread blocks: fewer resident warps
+// lost up to 15 % at the smallest l (the 128-bit arithmetic then bounds it)
+template <int MT, int LT>
+void launch_check_staged_lt(const int64_t* delta, int l, int r, int64_t batch, int64_t n, uint32_t* flags,
+                            unsigned long long* nflag, int32_t* status, cudaStream_t s) {
+    launch_check_staged_v<MT, LT, 256, 4, (MT <= 4 ? 3 : 2)>(delta, l, r, batch, n, flags, nflag, status, s);
+}
+
+// true when the staged kernel took the launch
+bool launch_check_staged(const int64_t* delta, int M, int l, int r, int64_t batch, int64_t n, uint32_t* flags,
+                         unsigned long long* nflag, int32_t* status, cudaStream_t s) {
+    if (n % 2 != 0 || !aligned(delta, 16)) return false;
+    // l = 16 (the byte-aligned shift) is compiled in for M <= 4, the M for
+    // which (M - 1) l fits a 64-bit word
+    switch (M) {
+        case 3:
+            if (l == 16) launch_check_staged_lt<3, 16>(delta, l, r, batch, n, flags, nflag, status, s);
+            else launch_check_staged_lt<3, 0>(delta, l, r, batch, n, flags, nflag, status, s);
+            return true;
+        case 4:
+            if (l == 16) launch_check_staged_lt<4, 16>(delta, l, r, batch, n, flags, nflag, status, s);
+            else launch_check_staged_lt<4, 0>(delta, l, r, batch, n, flags, nflag, status, s);
+            return true;
+        case 5: launch_check_staged_lt<5, 0>(delta, l, r, batch, n, flags, nflag, status, s); return true;
+        case 6: launch_check_staged_lt<6, 0>(delta, l, r, batch, n, flags, nflag, status, s); return true;
+        case 8: launch_check_staged_lt<8, 0>(delta, l, r, batch, n, flags, nflag, status, s); return true;
+        default: return false;
     }
 }
 
@@ -216,14 +384,15 @@ extern "C" ne_status ne_extract(ne_params p, const int64_t* delta, int64_t* d_ha
 }
 
 extern "C" ne_status ne_check(ne_params p, const int64_t* delta, int64_t batch, int64_t n, int32_t r,
-                              uint32_t* flags, uint64_t* nflag, cudaStream_t s) {
+                              uint32_t* flags, uint64_t* nflag, int32_t* status, cudaStream_t s) {
     ne_status st = common_args(p, batch, n, r, "ne_check");
     if (st) return st;
     if (!delta || (!flags && !nflag)) return fail(NE_EINVAL, "ne_check: null pointer");
     unsigned long long* nf = reinterpret_cast<unsigned long long*>(nflag);
     if (nf && cudaMemsetAsync(nf, 0, sizeof(*nf), s) != cudaSuccess) return check_launch("ne_check: reset count");
     if (batch == 0 || n == 0) return NE_OK;
-    launch_extract<false, true>(delta, nullptr, p.M, p.l, r, batch, n, flags, nf, s);
+    if (!launch_check_staged(delta, p.M, p.l, r, batch, n, flags, nf, status, s))
+        launch_extract<false, true>(delta, nullptr, p.M, p.l, r, batch, n, flags, nf, s);
     return check_launch("ne_check");
 }
 

@@ -131,7 +131,9 @@ __global__ void __launch_bounds__(kThreads) k_lsb(const LsbArgs a) {
 #pragma unroll
                     for (int v = 0; v < VEC; v++) {
                         int64_t o[MR];
-                        if (extract_rot<MT>(rot[v], Mv, a.l, FUSE == NE_FUSE_EXTRACT_CHECK, o)) f |= 1u << v;
+                        // the gather keeps the general shifts: 10 % faster there (the others equal)
+                        if (extract_rot<MT, KIND != K_PERM>(rot[v], Mv, a.l, FUSE == NE_FUSE_EXTRACT_CHECK, o))
+                            f |= 1u << v;
 #pragma unroll
                         for (int j = 0; j < MR; j++) {
                             if (!MT && j >= Mv) break;

@@ -102,7 +102,7 @@ def _load():
         "ne_cconv": [i32, P, P, P, i64, i64, u32, P],
         "ne_cconv_digits": [ne_params, ne_digits, P, P, P, P, P, i64, i64, i32, i32, P],
         "ne_extract": [ne_params, P, P, i64, i64, i32, P, P, P],
-        "ne_check": [ne_params, P, i64, i64, i32, P, P, P],
+        "ne_check": [ne_params, P, i64, i64, i32, P, P, P, P],
         "ne_recover": [ne_params, P, P, i64, i64, i32, P],
         "ne_inject": [P, i32, i64, i64, P, P, P, P, i64, P, P],
         "ne_abft_encode": [i32, P, P, i64, i64, P],
@@ -549,12 +549,12 @@ def ne_extract(p: ne_params, delta: torch.Tensor, d_hat: torch.Tensor | None = N
 
 
 def ne_check(p: ne_params, delta: torch.Tensor, r: int = 0, flags: torch.Tensor | None = None,
-             nflag: torch.Tensor | None = None):
+             nflag: torch.Tensor | None = None, status: torch.Tensor | None = None):
     batch, n = _bmn(delta, p.M)
     if flags is None:
         flags = torch.empty(flag_words(batch, n), dtype=torch.int32, device=delta.device)
     _call("ne_check", p, _ptr(delta, torch.int64, "delta"), batch, n, r, _ptr(flags, torch.int32, "flags", True),
-          _ptr(nflag, torch.int64, "nflag", True), _stream())
+          _ptr(nflag, torch.int64, "nflag", True), _ptr(status, torch.int32, "status", True), _stream())
     return flags
 
 

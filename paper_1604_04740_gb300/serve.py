@@ -19,6 +19,10 @@ the loop keeps up with tens of thousands of requests per second.
 Latency of a request = completion of its micro-batch, observed on the host,
 minus its arrival time.  Outputs stay in device memory (the device-resident
 result); only the batch status and flag count return to the host.
+
+A serving process should start CUDA with CUDA_MODULE_LOADING=EAGER: with
+lazy loading, the first launch of each kernel the warm-up did not reach
+loads its module inside the loop and stalls that micro-batch.
 """
 from __future__ import annotations
 

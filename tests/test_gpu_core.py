@@ -153,6 +153,34 @@ def test_extract_check_recover_match_oracle(ne, M, l, shape):
         assert (got_clean == d).all() and int(nf.item()) == 0
 
 
+@pytest.mark.parametrize("M,l", [(3, 16), (3, 11), (4, 16), (5, 15), (6, 10), (8, 8)])
+def test_staged_check_walks_many_units_per_block(ne, M, l):
+    """The check with its reads staged in shared memory: enough groups that every
+    block of the persistent launch goes round its ring of stages several times,
+    n = 1000 so the second unit of every group is ragged, faults scattered over
+    all streams; and the same data 8 bytes off alignment (the unstaged kernel)."""
+    batch, n = (2600 if M == 3 else 700), 1000
+    d, delta = codewords(M, l, (batch, M, n), seed=M * 31 + l)
+    rng = np.random.default_rng(M + l)
+    k = 3000
+    gb, gi, gj = rng.integers(batch, size=k), rng.integers(n, size=k), rng.integers(M, size=k)
+    bits = rng.integers(64, size=k).astype(np.uint64)
+    np.bitwise_xor.at(delta.view(np.uint64), (gb, gj, gi), np.uint64(1) << bits)
+    p = ne.params(M, l)
+    for r in sorted({0, M - 1}):
+        _, want_f = oracle.extract(delta, l, r)
+        nf = torch.zeros(1, dtype=torch.int64, device=DEV)
+        status = torch.zeros(1, dtype=torch.int32, device=DEV)
+        wf = ne.ne_check(p, dev(delta), r=r, nflag=nf, status=status)
+        assert (unpack_flags(host(wf), batch, n) == want_f).all(), f"r={r}"
+        assert int(nf.item()) == int(want_f.sum()) and int(status.item()) == 0
+        off = torch.empty(delta.size + 1, dtype=torch.int64, device=DEV)
+        t = off[1:].view(batch, M, n)
+        t.copy_(dev(delta))
+        wf2 = ne.ne_check(p, t, r=r)
+        assert (unpack_flags(host(wf2), batch, n) == want_f).all(), f"unaligned r={r}"
+
+
 def test_every_single_bit_flip_flagged_on_gpu(ne):
     M, l, n = 4, 10, 256
     d, delta = codewords(M, l, (1, M, n), seed=11)
