@@ -1080,6 +1080,10 @@ def run_batch(args, rank, world, local_rank):
         print(json.dumps(line), flush=True)
 
 
+# a micro-batch stops growing at about 2.5 ms of device work (serve.work_estimate)
+SERVE_BATCH_WORK = 3e11
+
+
 def run_serve(args, rank, world, local_rank):
     """The serving loop: Poisson arrivals swept over rates, requests from the
     ragged-batch distribution, 1 % of them with one lost stream, admission by
@@ -1094,7 +1098,7 @@ def run_serve(args, rank, world, local_rank):
     rates = [1000, 2000, 5000, 10000, 20000, 50000]
     # convolutions of N >= 4096 on the exact-transform path (the batch autotuner's choice for this mix)
     srv = S.Server(budget_bytes=100 * 10 ** 9, lanes=4, max_batch=256, device=dev, host_pool_elems=1 << 27,
-                   cfg=B.default_config(ntt_min_n=4096))
+                   cfg=B.default_config(ntt_min_n=4096), max_batch_work=SERVE_BATCH_WORK)
     # warm-up: the library, the allocator pool, both job kinds, both convolution paths and
     # every kernel the mix can reach (lazy module loading would otherwise charge the first rate)
     srv.run(B.mixed_jobs(99, 32, conv=(256, 65536)), np.zeros(32))
@@ -1110,11 +1114,13 @@ def run_serve(args, rank, world, local_rank):
         ent = S.summarize(srv.run(specs, arr, seed=rate))
         ent.update(max_loop_iteration_ms=srv.max_iter_s * 1e3, max_launch_ms=srv.max_launch_s * 1e3,
                    **{f"max_{k}_ms": v * 1e3 for k, v in srv.max_phase_s.items()},
-                   max_batch_device_ms=srv.max_device_s * 1e3, max_batch_device_requests=srv.max_device_requests)
+                   max_batch_device_ms=srv.max_device_s * 1e3, max_batch_device_requests=srv.max_device_requests,
+                   max_batch_copy_ms=srv.max_copy_span_s * 1e3, max_batch_kernels_ms=srv.max_kernel_span_s * 1e3)
         pla = S.summarize(srv.run(S.plain_copy(specs), arr, seed=rate))
         pla.update(max_loop_iteration_ms=srv.max_iter_s * 1e3, max_launch_ms=srv.max_launch_s * 1e3,
                    **{f"max_{k}_ms": v * 1e3 for k, v in srv.max_phase_s.items()},
-                   max_batch_device_ms=srv.max_device_s * 1e3, max_batch_device_requests=srv.max_device_requests)
+                   max_batch_device_ms=srv.max_device_s * 1e3, max_batch_device_requests=srv.max_device_requests,
+                   max_batch_copy_ms=srv.max_copy_span_s * 1e3, max_batch_kernels_ms=srv.max_kernel_span_s * 1e3)
         out[str(rate)] = {"entangled": ent, "plain": pla,
                           "throughput_overhead_pct": 100 * (pla["jobs_per_s"] / ent["jobs_per_s"] - 1)}
         top = ent
@@ -1125,7 +1131,8 @@ def run_serve(args, rank, world, local_rank):
                 "scaling": "weak", "vs_baseline": None, "dtype": "s8", "data": "synthetic",
                 "config": {"workload": f"serving: Poisson arrivals at {rates} jobs/s, {args.jobs} requests per rate "
                                        "from the ragged-batch distribution, 1% lose one stream, 100 GB HBM budget, "
-                                       "continuous batching on 4 CUDA-stream lanes (max 256 requests per micro-batch), "
+                                       "continuous batching on 4 CUDA-stream lanes (max 256 requests and about 2.5 ms of estimated "
+                                       "device work per micro-batch), "
                                        "convolutions of N >= 4096 as exact transforms",
                            "value_is": "useful Gop/s at the highest rate", "results": "device-resident"},
                 "serving": out, "roofline": None, "cpu_baseline": None,

@@ -98,10 +98,27 @@ class Request:
     done: float = -1.0
 
 
+def work_estimate(T, ntt_min_n: int) -> np.ndarray:
+    """Rough device work of each request of table T, in int8 tensor-op
+    equivalents: 2 M S m n k for a product and 2 M S N^2 for a convolution on
+    tensor tiles (S = 2 digit planes per stream for the entangled form, 1 for
+    the plain one), and 280 (2 M + 1) N log2 N for a convolution of N >=
+    ntt_min_n on the transform path (the factor from the ragged batch, where
+    528 such convolutions take as long as 4.1e11 tile ops)."""
+    S = np.where(T.plain != 0, 1.0, 2.0)
+    M = T.M.astype(np.float64)
+    N = T.N.astype(np.float64)
+    gemm = 2.0 * M * S * T.rows * T.cols * T.k
+    tiles = 2.0 * M * S * N * N
+    ntt = 280.0 * (2.0 * M + 1.0) * N * np.log2(np.maximum(N, 2.0))
+    conv = np.where((ntt_min_n > 0) & (T.N >= ntt_min_n), ntt, tiles)
+    return np.where(T.kind == ne.NE_JOB_GEMM, gemm, conv)
+
+
 class _Table:
     """Per-request numpy columns of one run()."""
 
-    def __init__(self, specs, c_pool, op_pool):
+    def __init__(self, specs, c_pool, op_pool, ntt_min_n: int = 0):
         G = ne.NE_JOB_GEMM
         self.kind = np.array([s.kind for s in specs], np.int32)
         self.M = np.array([s.M for s in specs], np.int32)
@@ -120,6 +137,8 @@ class _Table:
         self.op_bytes = np.where(gemm, self.k.astype(np.int64) * self.cols, self.N.astype(np.int64))
         self.out_elems = self.M * pout
         self.flag_words = (pout + 31) // 32
+        # rough device work per request (work_estimate), cumulated for the admission cap
+        self.cum_work = np.concatenate([[0.0], np.cumsum(work_estimate(self, ntt_min_n))])
         self.c_pool = np.asarray(c_pool, np.int64)
         self.op_pool = np.asarray(op_pool, np.int64)
 
@@ -127,11 +146,15 @@ class _Table:
 class Server:
     def __init__(self, budget_bytes: int, lanes: int = 4, max_batch: int = 256, device="cuda",
                  cfg: ne.ne_batch_config | None = None, host_pool_elems: int = 1 << 27, seed: int = 0,
-                 keep_outputs: bool = False):
+                 keep_outputs: bool = False, max_batch_work: float | None = None):
         self.device = torch.device(device)
         self.pool = Pool(budget_bytes, self.device)
         self.streams = [torch.cuda.Stream(self.device) for _ in range(lanes)]
         self.max_batch = max_batch
+        # admission also stops once a micro-batch's estimated work (work_estimate)
+        # would pass this: the persistent launches of a long micro-batch fill every
+        # SM, so the ones behind it on other lanes wait for all of it
+        self.max_batch_work = max_batch_work
         self.cfg = cfg or B.default_config()
         self.keep_outputs = keep_outputs
         # pinned host pools the requests' inputs come from
@@ -154,9 +177,12 @@ class Server:
         self.max_launch_s = 0.0
         self.max_phase_s = {"plan": 0.0, "copy": 0.0, "run": 0.0}
         # the longest device span of a micro-batch (events on its lane, from before its
-        # input copies to after its status read) and how many requests it held
+        # input copies to after its status read) and how many requests it held, and
+        # the longest input-copy and kernel parts of a micro-batch
         self.max_device_s = 0.0
         self.max_device_requests = 0
+        self.max_copy_span_s = 0.0
+        self.max_kernel_span_s = 0.0
 
     # -- one micro-batch: requests [a, b) ------------------------------------------------
     def _launch(self, T: _Table, a: int, b: int, lane: int):
@@ -201,6 +227,8 @@ class Server:
             t_c = time.perf_counter()
             ne.ne_copy_regions_h2d(c, self.c_host, c_off * 4, T.c_pool[a:b] * 4, T.c_elems[a:b] * 4)
             ne.ne_copy_regions_h2d(ops, self.op_host, op_off, T.op_pool[a:b], T.op_bytes[a:b])
+            evc = torch.cuda.Event(enable_timing=True)
+            evc.record(stream)
             t_r = time.perf_counter()
             status.zero_()
             ne.ne_batch_run(info, c, ops, out, flags, nflag, ws, status=status)
@@ -211,7 +239,7 @@ class Server:
         t_e = time.perf_counter()
         for phase, dt in (("plan", t_c - t_p), ("copy", t_r - t_c), ("run", t_e - t_r)):
             self.max_phase_s[phase] = max(self.max_phase_s[phase], dt)
-        return dict(ev0=ev0, ev=ev, region=(off, nb), a=a, b=b, out=out, out_off=out_off, lane=lane)
+        return dict(ev0=ev0, evc=evc, ev=ev, region=(off, nb), a=a, b=b, out=out, out_off=out_off, lane=lane)
 
     def _finish(self, fl, T: _Table, reqs, t):
         for i in range(fl["a"], fl["b"]):
@@ -220,6 +248,8 @@ class Server:
         dev_s = fl["ev0"].elapsed_time(fl["ev"]) * 1e-3
         if dev_s > self.max_device_s:
             self.max_device_s, self.max_device_requests = dev_s, fl["b"] - fl["a"]
+        self.max_copy_span_s = max(self.max_copy_span_s, fl["ev0"].elapsed_time(fl["evc"]) * 1e-3)
+        self.max_kernel_span_s = max(self.max_kernel_span_s, fl["evc"].elapsed_time(fl["ev"]) * 1e-3)
         if int(self.status_h[lane][0]) != 0:
             raise RuntimeError("a request's inputs left the planned value range")
         self.flagged += int(self.nflag_h[lane][0])
@@ -248,7 +278,7 @@ class Server:
             else:
                 co, oo = int(rng_c[i] % np.uint64(span_c + 1)), int(rng_c[i] % np.uint64(span_o + 1))
             reqs.append(Request(i, s, float(arrivals[i]), c_pool=co, op_pool=oo))
-        T = _Table(specs, [rq.c_pool for rq in reqs], [rq.op_pool for rq in reqs])
+        T = _Table(specs, [rq.c_pool for rq in reqs], [rq.op_pool for rq in reqs], self.cfg.ntt_min_n)
         # no cyclic garbage collection inside the loop: a full collection can
         # stall the host for tens of milliseconds, which shows up as latency
         gc_on = gc.isenabled()
@@ -272,6 +302,7 @@ class Server:
         self.max_iter_s = self.max_launch_s = 0.0
         self.max_phase_s = {"plan": 0.0, "copy": 0.0, "run": 0.0}
         self.max_device_s, self.max_device_requests = 0.0, 0
+        self.max_copy_span_s = self.max_kernel_span_s = 0.0
         last = time.perf_counter()
         while done < n:
             now = time.perf_counter()
@@ -289,6 +320,11 @@ class Server:
             inflight = still
             if head < nxt and free_lanes:
                 b = min(nxt, head + self.max_batch)
+                if self.max_batch_work:
+                    # the longest prefix within the work cap, at least one request
+                    cap = T.cum_work[head] + self.max_batch_work
+                    j = int(np.searchsorted(T.cum_work, cap, side="right")) - 1
+                    b = max(head + 1, min(b, j))
                 fl = None
                 while b > head:
                     t_l = time.perf_counter()

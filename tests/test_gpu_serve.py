@@ -31,13 +31,16 @@ def _direct(ne, srv, rq):
     return d.reshape(-1)
 
 
-@pytest.mark.parametrize("rate,lanes,max_batch,budget", [(20000.0, 3, 8, 96 << 20), (50000.0, 4, 6, 48 << 20),
-                                                         (2000.0, 2, 64, 512 << 20)])
-def test_mix_equals_alone_and_oracle(mods, rate, lanes, max_batch, budget):
+@pytest.mark.parametrize("rate,lanes,max_batch,budget,work", [(20000.0, 3, 8, 96 << 20, None),
+                                                              (50000.0, 4, 6, 48 << 20, None),
+                                                              (2000.0, 2, 64, 512 << 20, None),
+                                                              (50000.0, 4, 64, 512 << 20, 3e7)])
+def test_mix_equals_alone_and_oracle(mods, rate, lanes, max_batch, budget, work):
     B, ne, S = mods
     specs = B.mixed_jobs(21, 40, mnk=(16, 192), conv=(64, 4096), recover_frac=0.15)
     assert any(s.fuse == ne.NE_FUSE_RECOVER for s in specs)
-    srv = S.Server(budget_bytes=budget, lanes=lanes, max_batch=max_batch, keep_outputs=True, host_pool_elems=1 << 22)
+    srv = S.Server(budget_bytes=budget, lanes=lanes, max_batch=max_batch, keep_outputs=True, host_pool_elems=1 << 22,
+                   max_batch_work=work)
     reqs = srv.run(specs, S.poisson_arrivals(3, len(specs), rate), seed=5)
     assert all(rq.done >= rq.arrival for rq in reqs)
     assert srv.pool.used == 0 and srv.flagged == 0
