@@ -77,6 +77,10 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip overhead, ABFT and CPU-baseline legs")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target length of the CPU-baseline sample")
     ap.add_argument("--split", action="store_true", help="batch: also time each class of jobs on its own")
+    ap.add_argument("--rates", type=lambda t: [int(x) for x in t.split(",")],
+                    default=[1000, 2000, 5000, 10000, 20000, 50000], help="serve: arrival rates (jobs/s)")
+    ap.add_argument("--no-other-configs", action="store_true",
+                    help="cconv: do not append the summaries of the other workloads")
     a = ap.parse_args()
     if a.steps is None:
         a.steps = {"cconv": 400, "cconv_ntt": 400, "gemm": 20, "gemm64": 2000, "batch": 10, "serve": 1}[a.workload]
@@ -112,6 +116,19 @@ class Workload:
             self.bound = self.n * 2 ** 14
             self.useful_ops = 2 * self.M * self.n ** 3
             self.desc = f"GEMM: M={self.M} streams of {self.n}x{self.n} times a shared {self.n}x{self.n} int8, int64 CUDA-core form"
+
+
+# the l-selection policy of each workload (the same for both arms): byte-aligned l for
+# the tensor path's digit planes, the smallest l for the int64 form
+L_POLICY = {"cconv": "byte", "cconv_ntt": "byte", "gemm": "byte", "gemm64": "smallest"}
+
+
+def workload_config(wl, l, k, world):
+    """The config dict of a workload's line, identical in both arms."""
+    cfg = {"workload": wl.desc, "l": l, "k": k, "l2": L2_NOTE, "parallelism": f"replicas x{world}"}
+    if wl.name in ("cconv", "cconv_ntt"):
+        cfg["global_batch"] = wl.G
+    return cfg
 
 
 # ---- clock sampling ------------------------------------------------------------------
@@ -261,26 +278,38 @@ def oracle_sample(wl, seconds, compare=None):
     return ops / dt / 1e9, oracle.threads(), f"{nr} of {n} rows of every stream (entangle + product + extract/check)", parity
 
 
+def reference_config(wl, world):
+    import oracle
+    pol = {"byte": oracle.POLICY_BYTE, "smallest": oracle.POLICY_SMALLEST}[L_POLICY[wl.name]]
+    l, k = oracle.choose_l(wl.M, 64, wl.bound, pol)
+    return workload_config(wl, l, k, world)
+
+
 def run_reference(args, rank, world):
+    """The reference arm: the CPU oracle as it stands, on the host cores, each
+    step a bounded sample of the workload (entangle + operation +
+    extract/check); value is the sample's useful operations over its time."""
     if rank != 0:
-        return
+        return None
     wl = Workload(args.workload)
     per_step = max(0.5, min(10.0, 150.0 / max(1, args.steps + args.warmup)))
-    vals = []
+    vals, secs = [], []
     desc = threads = None
     for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
         v, threads, desc, _ = oracle_sample(wl, per_step)
         if k >= args.warmup:
             vals.append(v)
+            secs.append(time.perf_counter() - t0)
     value = statistics.mean(vals)
-    line = {"metric": METRIC, "impl": "reference", "value": value, "unit": "Gop/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": wl.useful_ops / (value * 1e9) * 1e3,
+    return {"metric": METRIC, "impl": "reference", "value": value, "unit": "Gop/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(secs),
+            "step": f"a bounded sample of the workload: {desc}",
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
-            "data": "synthetic", "config": {"workload": wl.desc},
+            "data": "synthetic", "config": reference_config(wl, world),
             "cpu_baseline": {"value": value, "unit": "Gop/s", "cores": threads, "kind": "oracle",
                              "sample": f"per step: {desc}"},
             "e2e": {"value": value, "unit": "Gop/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
 
 
 # ---- our path ---------------------------------------------------------------------------
@@ -288,6 +317,7 @@ def run_reference(args, rank, world):
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_1604_04740_gb300 import ne
+    from paper_1604_04740_gb300 import probe
 
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
@@ -328,8 +358,8 @@ def run_ours(args, rank, world, local_rank):
         dom_src = ("ne_cconv_digits.cu", "ne_cconv_tile.cuh", "ne_extract.cuh", "ne_mma.cuh", "ne_entangle.cuh")
         h2d = wl.c.nbytes + wl.g.nbytes
         d2h = out.numel() * 8 + flags.numel() * 4 + 8
-        cfg = {"workload": wl.desc, "l": l, "k": k, "digits": list(dg.shifts), "global_batch": G,
-               "l2": L2_NOTE, "parallelism": f"replicas x{world}"}
+        cfg = workload_config(wl, l, k, world)
+        digit_plan = list(dg.shifts)
     elif wl.name == "cconv_ntt":
         M, G, N = wl.M, wl.G, wl.N
         l, k = ne.ne_choose_l(M, 64, wl.bound, ne.NE_L_BYTE)
@@ -360,8 +390,8 @@ def run_ours(args, rank, world, local_rank):
         dom_src = ("ne_ntt.cu", "ne_entangle.cuh", "ne_extract.cuh")
         h2d = wl.c.nbytes + wl.g.nbytes
         d2h = out.numel() * 8 + flags.numel() * 4 + 8
-        cfg = {"workload": wl.desc, "l": l, "k": k, "digits": list(dg.shifts), "global_batch": G,
-               "l2": L2_NOTE, "parallelism": f"replicas x{world}"}
+        cfg = workload_config(wl, l, k, world)
+        digit_plan = list(dg.shifts)
     elif wl.name == "gemm":
         M, n = wl.M, wl.n
         l, k = ne.ne_choose_l(M, 64, wl.bound, ne.NE_L_BYTE)
@@ -394,8 +424,8 @@ def run_ours(args, rank, world, local_rank):
         dom_src = ("ne_gemm_digits.cu", "ne_extract.cuh", "ne_mma.cuh")
         h2d = wl.c.nbytes + wl.Gm.nbytes
         d2h = out.numel() * 8 + flags.numel() * 4 + 8
-        cfg = {"workload": wl.desc, "l": l, "k": k, "digits": list(dg.shifts),
-               "l2": L2_NOTE, "parallelism": f"replicas x{world}"}
+        cfg = workload_config(wl, l, k, world)
+        digit_plan = list(dg.shifts)
     else:
         M, n = wl.M, wl.n
         l, k = ne.ne_choose_l(M, 64, wl.bound, ne.NE_L_SMALLEST)
@@ -413,7 +443,7 @@ def run_ours(args, rank, world, local_rank):
             ne.ne_entangle(p, cb.reshape(M, n * n), eps)
             if ev is not None:
                 ev[0].record(stream)
-            ne.ne_gemm(eps.view(M, n, n), opb, delta)
+            ne.ne_gemm(p, eps.view(M, n, n), opb, delta, fuse=ne.NE_FUSE_NONE)
             if ev is not None:
                 ev[1].record(stream)
             ne.ne_extract(p, delta.view(1, M, n * n), ob, 0, fb, nb)
@@ -427,8 +457,8 @@ def run_ours(args, rank, world, local_rank):
         dom_src = ("ne_ops_i64.cu",)
         h2d = wl.c.nbytes + wl.Gm.nbytes
         d2h = out.numel() * 8 + flags.numel() * 4 + 8
-        cfg = {"workload": wl.desc, "l": l, "k": k, "l2": L2_NOTE,
-               "parallelism": f"replicas x{world}"}
+        cfg = workload_config(wl, l, k, world)
+        digit_plan = None
 
     # --- main timed region ---------------------------------------------------------------
     try:
@@ -458,20 +488,20 @@ def run_ours(args, rank, world, local_rank):
     if mma_ops_per_launch is not None:
         # live ceiling of the int8 tensor instruction (register-resident probe)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ne.ne_probe_mma_peak(64)
+        probe.mma_peak(64)
         e0.record(stream)
-        ops = ne.ne_probe_mma_peak(4096)
+        ops = probe.mma_peak(4096)
         e1.record(stream)
         torch.cuda.synchronize()
         peak_mma = ops / (e0.elapsed_time(e1) * 1e-3) / 1e12
-        ne.ne_probe_dp4a_peak(64)
+        probe.dp4a_peak(64)
         e0.record(stream)
-        ops = ne.ne_probe_dp4a_peak(8192)
+        ops = probe.dp4a_peak(8192)
         e1.record(stream)
         torch.cuda.synchronize()
         peak_dp4a = ops / (e0.elapsed_time(e1) * 1e-3) / 1e12
         achieved = mma_ops_per_launch / (inner_avg * 1e-3) / 1e12
-        hybrid = wl.name == "cconv" and os.environ.get("NE_CCONV_HYBRID", "") != "0"
+        hybrid = wl.name == "cconv"
         peak_mixed = {}
         if hybrid:
             # both int8 pipes in the convolution kernel's warp layout (8 tensor + 4 dp4a warps,
@@ -480,14 +510,14 @@ def run_ours(args, rank, world, local_rank):
             I, DW = 2048, 4
             for num, den in ((0, 1), (1, 8), (1, 4), (3, 8), (1, 2)):
                 idp = (256 * I * num) // (DW * (den - num))
-                ne.ne_probe_mixed_peak(16, (256 * 16 * num) // (DW * (den - num)), 8, DW, 3)
+                probe.mixed_peak(16, (256 * 16 * num) // (DW * (den - num)), 8, DW, 3)
                 e0.record(stream)
-                ops = ne.ne_probe_mixed_peak(I, idp, 8, DW, 3)
+                ops = probe.mixed_peak(I, idp, 8, DW, 3)
                 e1.record(stream)
                 torch.cuda.synchronize()
                 peak_mixed[f"{num}/{den}"] = ops / (e0.elapsed_time(e1) * 1e-3) / 1e12
         peak = max(peak_mixed.values()) if hybrid else peak_mma
-        src = ("measured in this run: mma.sync.m16n8k32 s8 register-resident probe (ne_probe_mma_peak)"
+        src = ("measured in this run: mma.sync.m16n8k32 s8 register-resident probe (probe/ne_probe.h, ne_probe_mma_peak)"
                + ("; the kernel splits each group between the two int8 pipes (10 of 16 blocks on 8 tensor "
                   "warps, 6 on 4 dp4a warps), so the peak is the best of ne_probe_mixed_peak (both pipes in "
                   "the kernel's warp layout) over the dp4a work shares in peak_mixed" if hybrid else "")
@@ -499,9 +529,9 @@ def run_ours(args, rank, world, local_rank):
                 "ms_per_launch": inner_avg}
     elif wl.name == "cconv_ntt":
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ne.ne_probe_imad_peak(64)
+        probe.imad_peak(64)
         e0.record(stream)
-        ops = ne.ne_probe_imad_peak(16384)
+        ops = probe.imad_peak(16384)
         e1.record(stream)
         torch.cuda.synchronize()
         peak_imad = ops / (e0.elapsed_time(e1) * 1e-3) / 1e12
@@ -589,15 +619,52 @@ def run_ours(args, rank, world, local_rank):
         v, threads, desc, parity = oracle_sample(wl, args.cpu_seconds, compare=host_out)
         cpu = {"value": v, "unit": "Gop/s", "cores": threads, "kind": "oracle", "sample": desc,
                "outputs_match_gpu": parity}
+        # the same binary on one thread (a shorter sample)
+        import oracle
+        oracle.set_threads(1)
+        try:
+            v1, _, desc1, _ = oracle_sample(wl, max(1.0, args.cpu_seconds / 4))
+        finally:
+            oracle.set_threads(threads)
+        cpu["single_thread"] = {"value": v1, "unit": "Gop/s", "cores": 1, "sample": desc1}
 
+    if wl.name == "gemm64":
+        extras["fault_and_drop"] = gemm64_fault_and_drop(torch, ne, p, c, Gm, out, M, n, dev)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "Gop/s", "n_gpus": world, "steps": K, "warmup": W,
                 "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "s8" if mma_ops_per_launch is not None else "int64", "data": "synthetic",
                 "config": cfg, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": launches_per_step * K}
+        line["digit_plan"] = digit_plan
         line.update(extras)
-        print(json.dumps(line), flush=True)
+        return line
+    return None
+
+
+def gemm64_fault_and_drop(torch, ne, p, c, Gm, out, M, n, dev):
+    """The small product's fault model: one seeded bit flip in one entangled
+    output stream must be flagged, and with that stream dropped (fail-stop)
+    every output must come back equal to the clean run's (whose parity with
+    the oracle the cpu_baseline leg reports)."""
+    from paper_1604_04740_gb300 import inputs
+    eps = ne.ne_entangle(p, c).view(M, n, n)
+    _, pos, strm, bit = inputs.fault_list(1, 1, n * n, M, 1)
+    fl = (torch.from_numpy(pos.astype(np.int64)).to(dev), torch.from_numpy(strm.astype(np.int32)).to(dev),
+          torch.from_numpy(bit.astype(np.int32)).to(dev))
+    flags = torch.zeros(n * n // 32, dtype=torch.int32, device=dev)
+    nflag = torch.zeros(1, dtype=torch.int64, device=dev)
+    got = ne.ne_gemm(p, eps, Gm, None, flags, nflag, fuse=ne.NE_FUSE_EXTRACT_CHECK, r=0, faults=fl)
+    f = np.unpackbits(flags.cpu().numpy().view(np.uint8), bitorder="little")
+    clean = out.view(M, n, n)
+    keep = torch.ones(n * n, dtype=torch.bool, device=dev)
+    keep[int(pos[0])] = False
+    unflagged_equal = bool(torch.equal(got.view(M, -1)[:, keep], clean.reshape(M, -1)[:, keep]))
+    rec = ne.ne_gemm(p, eps, Gm, None, None, None, fuse=ne.NE_FUSE_RECOVER, r=int(strm[0]), faults=fl)
+    return {"fault": {"stream": int(strm[0]), "position": int(pos[0]), "bit": int(bit[0])},
+            "flagged": int(nflag.item()) == 1 and int(f[int(pos[0])]) == 1 and int(f.sum()) == 1,
+            "other_outputs_equal_clean_run": unflagged_equal,
+            "dropped_stream": int(strm[0]), "recovered_equal_clean_run": bool(torch.equal(rec, clean))}
 
 
 def cconv_extras(torch, ne, wl, dev, flush, step, p, dg, planes, g, out, ms_step, hbm_peak):
@@ -609,26 +676,18 @@ def cconv_extras(torch, ne, wl, dev, flush, step, p, dg, planes, g, out, ms_step
     res = {}
     x64 = torch.from_numpy(wl.c.astype(np.int64)).to(dev)       # raw streams as int64 words
     c = torch.from_numpy(wl.c).to(dev)
-    # (1) plain, same tensor kernel and digit count as the entangled words
-    raw_planes = torch.empty_like(planes)
-    dg_same = ne.digits(dg.shifts)
     out2 = torch.empty_like(out)
-
+    dg1 = ne.digits((0,))
+    # (1) plain, the same one-launch kernel from the same raw int32 streams with
+    # the same digit set (0, l): definition 2, the operation unaware of the
+    # entanglement; the only differences are Eq. 16 in the load and the
+    # extraction/check in the epilogue
     def plain_same(ev):
-        ne.ne_split_digits(dg_same, x64, M, raw_planes)
-        ne.ne_cconv_digits(p, dg_same, raw_planes, g, out2, None, None, ne.NE_FUSE_NONE, 0)
+        ne.ne_cconv_entangled(p, dg, c, g, out2, None, None, ne.NE_FUSE_NONE, 0, plain=True)
 
     t_same, _ = timed_steps(torch, plain_same, K, W, flush)
-    # (2) plain, fewest digits the raw int8-valued streams need (one)
-    dg1 = ne.digits((0,))
-    raw1 = torch.empty((G, M, 1, N), dtype=torch.int8, device=dev)
-
-    def plain_min(ev):
-        ne.ne_split_digits(dg1, x64, M, raw1)
-        ne.ne_cconv_digits(p, dg1, raw1, g, out2, None, None, ne.NE_FUSE_NONE, 0)
-
-    t_min, _ = timed_steps(torch, plain_min, K, W, flush)
-
+    # (2) plain, the same kernel with the fewest digits the raw int8-valued
+    # streams need (one): definition 3, the price of the (M-1) l extra bits
     def plain_fused(ev):
         ne.ne_cconv_entangled(p, ne.raw_digits(), c, g, out2, None, None, ne.NE_FUSE_NONE, 0, plain=True)
 
@@ -640,8 +699,32 @@ def cconv_extras(torch, ne, wl, dev, flush, step, p, dg, planes, g, out, ms_step
 
     t_two, _ = timed_steps(torch, two_launch, K, W, flush)
     ent_ms = ms_step
+    # (2b) one faulted step: one bit flip per 10^4 output words (seed 1, at most one
+    # per position), injected by the kernel's fault hook before the extraction
+    from paper_1604_04740_gb300 import inputs
+    grp, pos, strm, bit = inputs.fault_list(1, G, N, M, G * M * N // 10 ** 4)
+    flat = grp * N + pos
+    fpos = torch.from_numpy(flat.astype(np.int64)).to(dev)
+    fstr = torch.from_numpy(strm.astype(np.int32)).to(dev)
+    fbit = torch.from_numpy(bit.astype(np.int32)).to(dev)
+    ffl = torch.empty(G * N // 32, dtype=torch.int32, device=dev)
+    fnf = torch.zeros(1, dtype=torch.int64, device=dev)
+
+    def faulted(ev):
+        ne.ne_cconv_entangled(p, dg, c, g, out2, ffl, fnf, ne.NE_FUSE_EXTRACT_CHECK, 0, faults=(fpos, fstr, fbit))
+
+    t_f, _ = timed_steps(torch, faulted, K, W, flush)
+    want = np.zeros(G * N, np.uint8)
+    want[flat] = 1
+    got = np.unpackbits(ffl.cpu().numpy().view(np.uint8), bitorder="little")
+    res["fault_injection"] = {"injected": int(len(flat)), "flagged": int(fnf.item()),
+                              "flags_equal_injected_set": bool((got == want).all()), "ms": t_f / K,
+                              "model": "one bit flip per 1e4 output words of delta, at most one per position "
+                                       "(seed 1), XORed in by the fused kernel's fault hook before Eq. 17-20/24"}
+    del ffl
     # (3) int64 CUDA-core family: the same direct kernel on raw and entangled words
     pl = ne.params(M, ne.ne_choose_l(M, 64, wl.bound, ne.NE_L_SMALLEST)[0])
+    pP, pA5 = ne.planes_of(M), ne.planes_of(M + 1)
     eps = torch.empty((G, M, N), dtype=torch.int64, device=dev)
     d64 = torch.empty_like(eps)
     o64 = torch.empty_like(eps)
@@ -649,11 +732,11 @@ def cconv_extras(torch, ne, wl, dev, flush, step, p, dg, planes, g, out, ms_step
     Ki = 4
 
     def plain_i64(ev):
-        ne.ne_cconv(x64, g, d64)
+        ne.ne_cconv(pP, x64, g, d64, fuse=ne.NE_FUSE_NONE)
 
     def ent_i64(ev):
         ne.ne_entangle(pl, c, eps)
-        ne.ne_cconv(eps, g, d64)
+        ne.ne_cconv(pl, eps, g, d64, fuse=ne.NE_FUSE_NONE)
         ne.ne_extract(pl, d64, o64, 0, fl, None)
 
     t_pi, _ = timed_steps(torch, plain_i64, Ki, 1, flush)
@@ -678,7 +761,7 @@ def cconv_extras(torch, ne, wl, dev, flush, step, p, dg, planes, g, out, ms_step
 
     def abft_i64(ev):
         ne.ne_abft_encode(M, c, x5)
-        ne.ne_cconv(x5, g, a64)
+        ne.ne_cconv(pA5, x5, g, a64, fuse=ne.NE_FUSE_NONE)
         ne.ne_abft_check(M, a64, fl, nfa)
 
     t_ai, _ = timed_steps(torch, abft_i64, Ki, 1, flush)
@@ -696,7 +779,7 @@ def cconv_extras(torch, ne, wl, dev, flush, step, p, dg, planes, g, out, ms_step
     # (8) the stand-alone linear passes of the int64 family (Eq. 16, Eq. 17-20 with
     # Eq. 24, Eq. 24 alone, Proposition 3), each against the HBM roofline
     ne.ne_entangle(pl, c, eps)
-    ne.ne_cconv(eps, g, d64)
+    ne.ne_cconv(pl, eps, g, d64, fuse=ne.NE_FUSE_NONE)
     nw = G * M * N
     passes = {
         "entangle_i64": (lambda ev: ne.ne_entangle(pl, c, eps), nw * 4 + nw * 8),
@@ -760,17 +843,20 @@ def cconv_extras(torch, ne, wl, dev, flush, step, p, dg, planes, g, out, ms_step
     torch.cuda.synchronize()
     ms = lambda t, k: t / k  # noqa: E731
     res["overhead_pct"] = {
-        "vs_plain_same_kernel_same_digits": 100 * (ent_ms / ms(t_same, K) - 1),
-        "vs_plain_fewest_digits": 100 * (ent_ms / ms(t_min, K) - 1),
-        "vs_plain_fused_one_digit": 100 * (ent_ms / ms(t_pf, K) - 1),
+        "definition": {"int64_family": "1: entangle + the int64 CUDA-core kernel + extract/check vs the same "
+                                       "kernel on the raw streams widened to int64",
+                       "vs_plain_same_kernel_same_digits": "2: the same one-launch tensor kernel from the same raw "
+                                                           "int32 streams with the same digit set",
+                       "vs_plain_fewest_digits": "3: the same kernel with one digit (the raw streams' own width)"},
         "int64_family": 100 * (ms(t_ei, Ki) / ms(t_pi, Ki) - 1),
-        "abft_tensor_vs_plain_same_kernel": 100 * (ms(t_abft, K) / ms(t_same, K) - 1),
+        "vs_plain_same_kernel_same_digits": 100 * (ent_ms / ms(t_same, K) - 1),
+        "vs_plain_fewest_digits": 100 * (ent_ms / ms(t_pf, K) - 1),
+        "abft_tensor_vs_plain_fewest_digits": 100 * (ms(t_abft, K) / ms(t_pf, K) - 1),
         "abft_int64_vs_plain_int64": 100 * (ms(t_ai, Ki) / ms(t_pi, Ki) - 1),
         "ntt_vs_plain_ntt": 100 * (ms(t_ne, K) / ms(t_np, K) - 1),
     }
     res["ms"] = {"entangled_step": ent_ms, "entangled_two_launches": ms(t_two, K),
-                 "plain_same_digits": ms(t_same, K), "plain_one_digit": ms(t_min, K),
-                 "plain_fused_one_digit": ms(t_pf, K),
+                 "plain_same_kernel_same_digits": ms(t_same, K), "plain_fused_one_digit": ms(t_pf, K),
                  "plain_int64": ms(t_pi, Ki), "entangled_int64": ms(t_ei, Ki), "abft_tensor": ms(t_abft, K),
                  "abft_int64": ms(t_ai, Ki), "fail_stop_recovery_step": ms(t_rec, K),
                  "entangle_digits_pass": ms(t_e, K), "cross_correlation_step": ms(t_x, K),
@@ -811,28 +897,69 @@ def check_read_sweep(torch, ne, pl, G, M, N, dev, flush):
 
 
 def gemm_extras(torch, ne, wl, dev, flush, p, dg, planes, Gm, out, ms_step):
+    """Overheads of the large product against the plain operation (the three
+    definitions), one faulted step, and the two ABFT comparators, on this GPU."""
     M, n = wl.M, wl.n
     K, W = 5, 2
-    x64 = torch.from_numpy(wl.c.astype(np.int64)).to(dev).reshape(M, n * n)
+    c32 = torch.from_numpy(wl.c).to(dev).reshape(M, n * n)
     raw = torch.empty_like(planes)
     out2 = torch.empty_like(out)
-    dg_same = ne.digits(dg.shifts)
+    FN = ne.NE_FUSE_NONE
 
+    # definition 2: the same two launches (a digit pass over the raw streams, then the
+    # same tensor kernel) with the entangled words' digit set, on the raw streams
     def plain_same(ev):
-        ne.ne_split_digits(dg_same, x64, M, raw.view(M, dg.S, n * n))
-        ne.ne_gemm_digits(p, dg_same, raw, Gm, out2, None, None, ne.NE_FUSE_NONE, 0)
+        ne.ne_split_digits_raw(p, dg, c32, raw.view(M, dg.S, n * n))
+        ne.ne_gemm_digits(p, dg, raw, Gm, out2, None, None, FN, 0)
 
     t_same, _ = timed_steps(torch, plain_same, K, W, flush)
-    dg1 = ne.digits((0,))
+    # definition 3: the same with one digit, the raw int8-valued streams' own width
+    dg1 = ne.raw_digits()
     raw1 = torch.empty((M, 1, n, n), dtype=torch.int8, device=dev)
 
     def plain_min(ev):
-        ne.ne_split_digits(dg1, x64, M, raw1.view(M, 1, n * n))
-        ne.ne_gemm_digits(p, dg1, raw1, Gm, out2, None, None, ne.NE_FUSE_NONE, 0)
+        ne.ne_split_digits_raw(p, dg1, c32, raw1.view(M, 1, n * n))
+        ne.ne_gemm_digits(p, dg1, raw1, Gm, out2, None, None, FN, 0)
 
     t_min, _ = timed_steps(torch, plain_min, K, W, flush)
+    # one faulted step: one bit flip per 10^4 output words through the fused kernel's fault hook
+    from paper_1604_04740_gb300 import inputs
+    _, pos, strm, bit = inputs.fault_list(1, 1, n * n, M, M * n * n // 10 ** 4)
+    fl = (torch.from_numpy(pos.astype(np.int64)).to(dev), torch.from_numpy(strm.astype(np.int32)).to(dev),
+          torch.from_numpy(bit.astype(np.int32)).to(dev))
+    ffl = torch.empty(n * n // 32, dtype=torch.int32, device=dev)
+    fnf = torch.zeros(1, dtype=torch.int64, device=dev)
+    ne.ne_gemm_digits(p, dg, planes, Gm, out2, ffl, fnf, ne.NE_FUSE_EXTRACT_CHECK, 0, faults=fl)
+    want = np.zeros(n * n, np.uint8)
+    want[pos] = 1
+    got = np.unpackbits(ffl.cpu().numpy().view(np.uint8), bitorder="little")
+    fault = {"injected": int(len(pos)), "flagged": int(fnf.item()), "flags_equal_injected_set": bool((got == want).all()),
+             "model": "one bit flip per 1e4 output words of delta (seed 1), XORed in by the fused kernel's fault hook"}
+    del ffl, raw1
+    # definition 1: the int64 CUDA-core family at the full size -- the same kernel on the
+    # raw streams widened to int64, and on the entangled words followed by the extraction
+    pl = ne.params(M, ne.ne_choose_l(M, 64, wl.bound, ne.NE_L_SMALLEST)[0])
+    x64 = c32.to(torch.int64).view(M, n, n)
+    eps = torch.empty((M, n * n), dtype=torch.int64, device=dev)
+    d64 = torch.empty((M, n, n), dtype=torch.int64, device=dev)
+    f64 = torch.empty(n * n // 32, dtype=torch.int32, device=dev)
+    n64 = torch.zeros(1, dtype=torch.int64, device=dev)
+
+    def plain_i64(ev):
+        ne.ne_gemm(ne.planes_of(M), x64, Gm, d64, fuse=FN)
+
+    def ent_i64(ev):
+        ne.ne_entangle(pl, c32, eps)
+        ne.ne_gemm(pl, eps.view(M, n, n), Gm, d64, f64, n64, fuse=ne.NE_FUSE_EXTRACT_CHECK, r=0)
+
+    Ki = 2
+    t_pi, _ = timed_steps(torch, plain_i64, Ki, 1, flush)
+    t_ei, _ = timed_steps(torch, ent_i64, Ki, 1, flush)
+    torch.cuda.synchronize()
+    i64_match = bool(torch.equal(d64, out)) and int(n64.item()) == 0
+    del x64, eps, d64, f64
+    torch.cuda.empty_cache()
     # checksum ABFT (Eq. 3-6): the checksum stream as an (M+1)-th stream, two digits
-    c32 = torch.from_numpy(wl.c).to(dev).reshape(M, n * n)
     x5 = torch.empty((M + 1, n * n), dtype=torch.int64, device=dev)
     dgA = ne.digits((0, 8))
     aplanes = torch.empty((M + 1, 2, n, n), dtype=torch.int8, device=dev)
@@ -844,10 +971,11 @@ def gemm_extras(torch, ne, wl, dev, flush, p, dg, planes, Gm, out, ms_step):
     def abft_stream(ev):
         ne.ne_abft_encode(M, c32.view(1, M, n * n), x5.view(1, M + 1, n * n))
         ne.ne_split_digits(dgA, x5, M + 1, aplanes.view(M + 1, 2, n * n))
-        ne.ne_gemm_digits(pA, dgA, aplanes, Gm, aout, None, None, ne.NE_FUSE_NONE, 0)
+        ne.ne_gemm_digits(pA, dgA, aplanes, Gm, aout, None, None, FN, 0)
         ne.ne_abft_check(M, aout.view(1, M + 1, n * n), fla, nfa)
 
     t_abft, _ = timed_steps(torch, abft_stream, K, W, flush)
+    del x5, aplanes, aout
     # row/column checksum ABFT (ABFT RC-check) around the plain one-digit product of every stream
     A3 = c32.view(M, n, n)
     ac = torch.empty((M, n), dtype=torch.int64, device=dev)
@@ -857,6 +985,7 @@ def gemm_extras(torch, ne, wl, dev, flush, p, dg, planes, Gm, out, ms_step):
     rb = torch.empty(rw, dtype=torch.int32, device=dev)
     cb = torch.empty(cw, dtype=torch.int32, device=dev)
     nbad = torch.zeros(2, dtype=torch.int64, device=dev)
+    raw1 = torch.empty((M, 1, n, n), dtype=torch.int8, device=dev)
 
     def abft_rc(ev):
         plain_min(ev)
@@ -871,13 +1000,23 @@ def gemm_extras(torch, ne, wl, dev, flush, p, dg, planes, Gm, out, ms_step):
     t_rco, _ = timed_steps(torch, rc_only, K, W, flush)
     torch.cuda.synchronize()
     assert int(nbad.sum().item()) == 0 and int(nfa.item()) == 0, "clean products flagged by an ABFT check"
-    return {"overhead_pct": {"vs_plain_same_kernel_same_digits": 100 * (ms_step / (t_same / K) - 1),
-                             "vs_plain_fewest_digits": 100 * (ms_step / (t_min / K) - 1),
-                             "abft_checksum_stream_vs_plain_fewest_digits": 100 * (t_abft / t_min - 1),
-                             "abft_rc_check_vs_plain_fewest_digits": 100 * (t_rc / t_min - 1)},
-            "ms": {"entangled_step": ms_step, "plain_same_digits": t_same / K, "plain_one_digit": t_min / K,
+    return {"overhead_pct": {
+                "definition": {"int64_family": "1: entangle + the int64 CUDA-core product + extract/check vs the "
+                                               "same kernel on the raw streams widened to int64",
+                               "vs_plain_same_kernel_same_digits": "2: the same digit pass and tensor kernel on the "
+                                                                   "raw streams with the entangled digit set",
+                               "vs_plain_fewest_digits": "3: the same with one digit (the raw streams' own width)"},
+                "int64_family": 100 * (t_ei / t_pi - 1),
+                "vs_plain_same_kernel_same_digits": 100 * (ms_step / (t_same / K) - 1),
+                "vs_plain_fewest_digits": 100 * (ms_step / (t_min / K) - 1),
+                "abft_checksum_stream_vs_plain_fewest_digits": 100 * (t_abft / t_min - 1),
+                "abft_rc_check_vs_plain_fewest_digits": 100 * (t_rc / t_min - 1)},
+            "ms": {"entangled_step": ms_step, "plain_same_kernel_same_digits": t_same / K,
+                   "plain_one_digit": t_min / K, "plain_int64": t_pi / Ki, "entangled_int64": t_ei / Ki,
                    "abft_checksum_stream": t_abft / K, "abft_rc_check_step": t_rc / K,
-                   "abft_rc_encode_and_check_alone": t_rco / K}}
+                   "abft_rc_encode_and_check_alone": t_rco / K},
+            "int64_outputs_equal_tensor_path": i64_match,
+            "fault_injection": fault}
 
 
 def batch_split(B, ne, torch, specs, cfg, dev):
@@ -936,6 +1075,7 @@ def run_batch(args, rank, world, local_rank):
     from paper_1604_04740_gb300 import autotune
     from paper_1604_04740_gb300 import batch as B
     from paper_1604_04740_gb300 import ne
+    from paper_1604_04740_gb300 import probe
 
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
@@ -992,10 +1132,10 @@ def run_batch(args, rank, world, local_rank):
         op_ms.append(ea.elapsed_time(ec))
     # a run without the operation launch is not possible through the API; time the
     # entangle share from the launch list instead (profiles/)
-    peak_ops = ne.ne_probe_mma_peak(4096)
+    peak_ops = probe.mma_peak(4096)
     p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     p0.record(stream)
-    peak_ops = ne.ne_probe_mma_peak(4096)
+    peak_ops = probe.mma_peak(4096)
     p1.record(stream)
     torch.cuda.synchronize()
     peak = peak_ops / (p0.elapsed_time(p1) * 1e-3) / 1e12
@@ -1077,7 +1217,8 @@ def run_batch(args, rank, world, local_rank):
                 "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": K * batch_launches(info),
                 "autotune_trials": trials}
-        print(json.dumps(line), flush=True)
+        return line
+    return None
 
 
 # a micro-batch stops growing at about 2.5 ms of device work (serve.work_estimate)
@@ -1095,7 +1236,7 @@ def run_serve(args, rank, world, local_rank):
 
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
-    rates = [1000, 2000, 5000, 10000, 20000, 50000]
+    rates = args.rates
     # convolutions of N >= 4096 on the exact-transform path (the batch autotuner's choice for this mix)
     srv = S.Server(budget_bytes=100 * 10 ** 9, lanes=4, max_batch=256, device=dev, host_pool_elems=1 << 27,
                    cfg=B.default_config(ntt_min_n=4096), max_batch_work=SERVE_BATCH_WORK)
@@ -1139,15 +1280,53 @@ def run_serve(args, rank, world, local_rank):
                 "e2e": {"value": top["useful_Gop_s"] * world, "unit": "Gop/s",
                         "note": "requests' inputs are copied from pinned host memory inside the loop"},
                 "clocks": clocks, "gpu_launches": None}
-        print(json.dumps(line), flush=True)
+        return line
+    return None
+
+
+def other_configs(args, rank, world, local_rank):
+    """Summaries of the other workloads for the default line, each measured
+    here with fewer steps: the small int64 product (with its fault and dropped
+    stream), the large product, the ragged batch and the serving loop at two
+    rates.  A failure is recorded in place of its summary."""
+    import copy
+    import torch
+    out = {}
+    runs = [("gemm64_3x64", "gemm64", {"steps": 200, "warmup": 20, "cpu_seconds": 2.0}),
+            ("gemm_4x4096", "gemm", {"steps": 5, "warmup": 2, "cpu_seconds": 8.0}),
+            ("batch_2048", "batch", {"steps": 5, "warmup": 2, "cpu_seconds": 4.0}),
+            ("serve", "serve", {"jobs": 4000, "rates": [5000, 50000]})]
+    keep = ("value", "unit", "ms_per_step", "steps", "warmup", "dtype", "config", "digit_plan", "roofline",
+            "overhead_pct", "ms", "fault_injection", "fault_and_drop", "int64_outputs_equal_tensor_path",
+            "cpu_baseline", "e2e", "clocks", "gpu_launches", "jobs_per_s", "detection", "serving")
+    for name, wl, over in runs:
+        a = copy.copy(args)
+        a.workload = wl
+        a.jobs = 2048
+        for k, v in over.items():
+            setattr(a, k, v)
+        try:
+            if wl == "batch":
+                line = run_batch(a, rank, world, local_rank)
+            elif wl == "serve":
+                line = run_serve(a, rank, world, local_rank)
+            else:
+                line = run_ours(a, rank, world, local_rank)
+            out[name] = {k: line[k] for k in keep if k in line} if line else None
+        except Exception as e:  # recorded, not hidden: the summary says what failed
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+    return out
 
 
 def main():
     args = parse()
-    if args.workload == "serve":
+    if args.workload in ("serve", "cconv"):
         # a serving process loads every kernel module when CUDA starts: loaded
         # lazily, the first launch of a kernel the warm-up did not reach (one
-        # transform length, one M) stalls its micro-batch for tens of ms
+        # transform length, one M) stalls its micro-batch for tens of ms (the
+        # default line ends with the serving loop among its other workloads)
         os.environ.setdefault("CUDA_MODULE_LOADING", "EAGER")
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -1157,20 +1336,27 @@ def main():
             print(json.dumps({"impl": "reference", "unavailable": "the CPU oracle covers this workload only by "
                               "sampled jobs (bench.py --workload batch reports them in cpu_baseline)"}))
             return
-        run_reference(args, rank, world)
+        line = run_reference(args, rank, world)
+        if line:
+            print(json.dumps(line), flush=True)
         return
     if world > 1:
         import torch
         torch.cuda.set_device(local_rank)
         D.init("nccl")
     if args.workload == "batch":
-        run_batch(args, rank, world, local_rank)
+        line = run_batch(args, rank, world, local_rank)
     elif args.workload == "serve":
         if args.jobs == 2048:
             args.jobs = 4000
-        run_serve(args, rank, world, local_rank)
+        line = run_serve(args, rank, world, local_rank)
     else:
-        run_ours(args, rank, world, local_rank)
+        line = run_ours(args, rank, world, local_rank)
+        if (line is not None and args.workload == "cconv" and world == 1 and not args.no_extras
+                and not args.no_other_configs):
+            line["other_configs"] = other_configs(args, rank, world, local_rank)
+    if line is not None:
+        print(json.dumps(line), flush=True)
     D.finish()
 
 

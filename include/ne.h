@@ -75,6 +75,24 @@ typedef struct {
     int32_t hi;
 } ne_digits;
 
+/* Transient faults injected into the words delta of a fused operation after
+ * the operation and before its extraction -- the fault model of Sec. I: a
+ * fault corrupts one stream's result of the operation.  Entry f XORs bit
+ * (bit[f] mod 64) into delta_{stream[f]} at the flat output position pos[f]
+ * of the call: group * N + i for the batched convolutions, i * cols + j for
+ * the matrix product.  pos must be sorted ascending (an entry out of order may
+ * be missed).  An entry whose stream lies outside [0, M) hits nothing; under
+ * NE_FUSE_RECOVER an entry on the lost stream hits nothing (that stream is
+ * never computed).  The three arrays are device arrays of count entries,
+ * owned by the caller and only read; count = 0 injects nothing and the
+ * pointers may then be null. */
+typedef struct {
+    const int64_t* pos;
+    const int32_t* stream;
+    const int32_t* bit;
+    int64_t count;
+} ne_faults;
+
 /* l-selection policies for ne_choose_l */
 #define NE_L_PAPER    0  /* max (M-2)l+k s.t. (M-1)l+k <= w, k <= l; ties -> larger (M-1)l+k */
 #define NE_L_SMALLEST 1  /* smallest l with an admissible k whose Eq. 14 range covers the bound */
@@ -120,6 +138,18 @@ ne_status ne_entangle(ne_params p, const int32_t* c, int64_t* eps,
 ne_status ne_entangle_digits(ne_params p, ne_digits dg, const int32_t* c, int8_t* planes,
                              int64_t batch, int64_t n, int32_t* status, cudaStream_t s);
 
+/* Digit planes of the raw streams (no entanglement) with the digit set of an
+ * entangled plan: planes is int8 [batch][M][dg.S][n] holding c itself, the
+ * operand of the plain operation in the layout and digit count of the
+ * entangled one.  dg must be the plan of (p.l, lo, hi) with lo <= 0 <= hi (a
+ * raw value is then a word of Eq. 16 with a zero predecessor) and at most 4
+ * digits, or one digit at shift 0 with [lo, hi] inside [-128, 127] (the
+ * fewest digits of int8-valued streams); M <= 5; n a multiple of 8, c
+ * 16-byte and planes 8-byte aligned.
+ * An input outside [lo, hi] sets *status = NE_ERANGE (nullable). */
+ne_status ne_split_digits_raw(ne_params p, ne_digits dg, const int32_t* c, int8_t* planes,
+                              int64_t batch, int64_t n, int32_t* status, cudaStream_t s);
+
 /* Digit planes of arbitrary int64 words (entangled words produced elsewhere,
  * or the raw and checksum streams of the ABFT comparator): x is int64
  * [batch][P][n], planes is int8 [batch][P][dg.S][n].  Out-of-plan words set
@@ -131,16 +161,58 @@ ne_status ne_split_digits(ne_digits dg, const int64_t* x, int8_t* planes, int64_
 /* The LSB operation on each stream (Eq. 10), unaware of the entanglement    */
 /* ------------------------------------------------------------------------ */
 
-/* Matrix product per stream on CUDA cores in int64 (exact while every partial
- * sum fits 64 bits): out[m] = x[m] * G for streams m = 0..P-1 whose bit in
- * skip_mask is clear (skipped planes are not written: a fail-stopped core).
- * x: int64 [P][rows][k] (entangled words, or raw streams widened to int64),
- * G: int8 [k][cols], out: int64 [P][rows][cols].  P is the number of planes
- * (M for entangled streams, M+1 for the checksum comparator). */
-ne_status ne_gemm(int32_t P, const int64_t* x, const int8_t* G, int64_t* out,
-                  int32_t rows, int32_t cols, int32_t k, uint32_t skip_mask, cudaStream_t s);
+/* The operation of Eq. 10 in the form of the problem statement (Sec. II,
+ * Eq. 2): the M entangled streams eps_m (int64 words of Eq. 16) times the
+ * shared operator, each stream unchanged by the entanglement, with the
+ * extraction and check or the recovery behind it.
+ *  mode NE_MODE_I64:     int64 multiply-adds on the CUDA cores (exact while
+ *        every partial sum fits 64 bits).  The operation writes delta into
+ *        out; the fault hook and then the extraction (Eq. 17-20, with the
+ *        check of Eq. 24) run in place on out, in the same call and stream.
+ *        dg and status are not used.
+ *  mode NE_MODE_S8SLICE: the int8 tensor path.  The kernel's loader splits
+ *        every word into the balanced base-256 digits of the plan dg
+ *        (ne_plan_digits of the range the streams were entangled from), each
+ *        digit slice is multiplied exactly (int32 accumulation over chunks of
+ *        at most 2^31 / 2^14 terms) and recombined in int64, and the fault hook
+ *        and the extraction/check run in the epilogue: delta never reaches
+ *        memory.  A word with a non-zero digit outside dg sets
+ *        *status = NE_ERANGE (device int32, nullable).
+ *  fuse: NE_FUSE_NONE (out = delta of every computed plane), NE_FUSE_EXTRACT_CHECK
+ *        (out = d_hat, flags/nflag the Eq. 24 check of stream r, flags
+ *        nullable) or NE_FUSE_RECOVER (stream r is lost: never read nor
+ *        computed; out = d_hat from the other M-1, Prop. 3).
+ *  drop_mask: planes that are not computed (a fail-stopped core): with
+ *        NE_FUSE_NONE and NE_MODE_I64 any set of planes (their outputs are
+ *        not written); with NE_FUSE_RECOVER 0 or the bit of r; otherwise 0.
+ *  faults: transient faults XORed into delta before the extraction (ne_faults).
+ * With NE_FUSE_NONE and NE_MODE_I64, p.M is just the number of planes (1..32,
+ * l unused): the plain operation on raw streams widened to int64, or the M+1
+ * planes of the checksum comparator.  Otherwise p must satisfy Eq. 13. */
+#define NE_MODE_I64     0
+#define NE_MODE_S8SLICE 1
 
-/* The same product on the int8 tensor path: every digit plane is multiplied
+/* Matrix product (the GEMM experiment of Sec. V): out[m] = eps[m] * G.
+ * eps: int64 [M][rows][k]; G: int8 [k][cols]; out: int64 [M][rows][cols]
+ * (must not overlap eps); positions i * cols + j for flags [ceil(rows cols /
+ * 32)] and faults.  NE_MODE_S8SLICE: k a multiple of 16, cols of 8, M * dg.S
+ * <= 16, eps 16-byte aligned. */
+ne_status ne_gemm(ne_params p, const int64_t* eps, const int8_t* G, int64_t* out, uint32_t* flags, uint64_t* nflag,
+                  int32_t rows, int32_t cols, int32_t k, int32_t mode, ne_digits dg, int32_t fuse, int32_t r,
+                  uint32_t drop_mask, ne_faults faults, int32_t* status, cudaStream_t s);
+
+/* Batched circular convolution (Eq. 2): out[b][m][i] = sum_j eps[b][m][j]
+ * g[b][(i - j) mod N].  eps, out: int64 [batch][M][N] (no overlap); g: int8
+ * [batch][N]; flags [batch][ceil(N/32)]; fault positions b * N + i.
+ * NE_MODE_S8SLICE: N a multiple of 64 in [64, 65536], M * dg.S <= 16, eps
+ * 16-byte aligned. */
+ne_status ne_cconv(ne_params p, const int64_t* eps, const int8_t* g, int64_t* out, uint32_t* flags, uint64_t* nflag,
+                   int64_t batch, int64_t N, int32_t mode, ne_digits dg, int32_t fuse, int32_t r,
+                   uint32_t drop_mask, ne_faults faults, int32_t* status, cudaStream_t s);
+
+/* The product on the int8 tensor path from digit planes already split (by
+ * ne_entangle_digits, which writes 2 bytes per word of int8-valued streams
+ * instead of 8): every digit plane is multiplied
  * by G with int32 accumulation over K chunks of at most 2^31 / 2^14 terms
  * (no int32 overflow for int8 x int8), and the digits are recombined exactly
  * in int64.  planes: int8 [M][dg.S][rows][k]; G: int8 [k][cols].
@@ -150,40 +222,52 @@ ne_status ne_gemm(int32_t P, const int64_t* x, const int8_t* G, int64_t* out,
  *        (positions flattened as i*cols + j; flags nullable).
  *  fuse = NE_FUSE_RECOVER:       stream r is not computed at all; out = d_hat
  *        from the other M-1 streams (Prop. 3); flags ignored.
+ * faults: transient faults XORed into delta before the epilogue (see
+ * ne_faults; positions i * cols + j).
  * rows, cols >= 1; k >= 1 and a multiple of 16; cols a multiple of 8. */
 ne_status ne_gemm_digits(ne_params p, ne_digits dg, const int8_t* planes, const int8_t* G,
                          int64_t* out, uint32_t* flags, uint64_t* nflag,
                          int32_t rows, int32_t cols, int32_t k,
-                         int32_t fuse, int32_t r, cudaStream_t s);
+                         int32_t fuse, int32_t r, ne_faults faults, cudaStream_t s);
 
-/* Batched circular convolution on CUDA cores in int64 (the direct form):
- * out[b][m][i] = sum_j x[b][m][j] g[b][(i - j) mod N] for the P planes of
- * each group.  x, out: int64 [batch][P][N]; g: int8 [batch][N]. */
-ne_status ne_cconv(int32_t P, const int64_t* x, const int8_t* g, int64_t* out,
-                   int64_t batch, int64_t N, uint32_t skip_mask, cudaStream_t s);
-
-/* The same convolution on the int8 tensor path: the circulant of g is tiled
+/* The convolution on the int8 tensor path from digit planes already split:
+ * the circulant of g is tiled
  * into Toeplitz blocks built in shared memory and multiplied with the digit
  * planes (int32 accumulation, exact int64 recombination), with the same
- * fused epilogues as ne_gemm_digits.  planes: int8 [batch][M][dg.S][N];
+ * fused epilogues and fault hook as ne_gemm_digits (fault positions
+ * group * N + i).  planes: int8 [batch][M][dg.S][N];
  * g: int8 [batch][N]; out: int64 [batch][M][N]; flags: [batch][N/32].
  * N a multiple of 64 with 64 <= N <= 4096. */
 ne_status ne_cconv_digits(ne_params p, ne_digits dg, const int8_t* planes, const int8_t* g,
                           int64_t* out, uint32_t* flags, uint64_t* nflag,
-                          int64_t batch, int64_t N, int32_t fuse, int32_t r, cudaStream_t s);
+                          int64_t batch, int64_t N, int32_t fuse, int32_t r, ne_faults faults,
+                          cudaStream_t s);
 
 /* ne_cconv_digits fused with the entanglement in front: the tiles read the
  * raw streams c (int32 [batch][M][N], 16-byte aligned) and form the words of
  * Eq. 16 and their digits while loading, so one launch goes from the raw
  * streams to the extracted outputs.  dg must be the digit plan of its
  * (l, lo, hi) with words of at most 4 digits (ne_plan_digits); every input
- * outside [lo, hi] sets *status = NE_ERANGE (device int32, nullable).
- * plain = 1: the plain operation on the raw streams (dg one digit at shift 0
- * with a range inside [-128, 127]; NE_FUSE_NONE).  Other arguments as for
- * ne_cconv_digits. */
+ * outside [lo, hi] sets *status = NE_ERANGE (device int32, nullable); under
+ * NE_FUSE_RECOVER the lost stream's inputs are still read (as the
+ * predecessor in the next stream's words) and range-checked.
+ * plain = 1: the plain operation on the raw streams (NE_FUSE_NONE), with dg
+ * either one digit at shift 0 and a range inside [-128, 127], or the plan of
+ * (l, lo, hi) with lo <= 0 <= hi (the raw values split into the entangled
+ * words' digit set: the same kernel doing the same int8 work).  Other
+ * arguments as for ne_cconv_digits. */
 ne_status ne_cconv_entangled(ne_params p, ne_digits dg, const int32_t* c, const int8_t* g, int64_t* out,
                              uint32_t* flags, uint64_t* nflag, int64_t batch, int64_t N, int32_t fuse,
-                             int32_t r, int32_t plain, int32_t* status, cudaStream_t s);
+                             int32_t r, int32_t plain, ne_faults faults, int32_t* status, cudaStream_t s);
+
+/* Tuning knob (no counterpart in the paper; process-wide, for calls made
+ * after it): how ne_cconv_digits and ne_cconv_entangled split a group of at
+ * most 16 Toeplitz blocks between the int8 tensor pipe and the dp4a pipe of
+ * the CUDA cores.  -1: the default (the split measured fastest per digit-plane
+ * count); 0: tensor pipe only; HR in {22..26, 34, 42..44, 52, 62}: H dp4a warps
+ * of R outputs per thread take H * R / 2 of the blocks.  NE_EINVAL for any
+ * other value. */
+ne_status ne_set_cconv_split(int32_t variant);
 
 /* The same batched convolution through an exact number-theoretic transform
  * (the integer-exact form of the frequency-domain convolution of Sec. V),
@@ -192,14 +276,16 @@ ne_status ne_cconv_entangled(ne_params p, ne_digits dg, const int32_t* c, const 
  * the balanced base-256 digits of dg, each digit plane is convolved with g
  * modulo the prime 119 * 2^23 + 1 (exact: a digit plane's convolution is at
  * most N * 2^14 in magnitude), the digits are recombined in int64 and the
- * epilogue of ne_cconv_digits follows (fuse, r, flags, nflag as there; plain
- * requires NE_FUSE_NONE).  A word with a non-zero digit outside dg sets
- * *status = NE_ERANGE (status: device int32, nullable).
+ * epilogue of ne_cconv_digits follows (fuse, r, flags, nflag and faults as
+ * there; plain requires NE_FUSE_NONE).  A word with a non-zero digit outside
+ * dg sets *status = NE_ERANGE (status: device int32, nullable); with the
+ * range-checked split of a planned digit set the inputs are checked instead,
+ * the lost stream's included under NE_FUSE_RECOVER.
  * c: int32 [batch][M][N]; g: int8 [batch][N]; out: int64 [batch][M][N].
  * N = 1024; M * dg.S <= 15. */
 ne_status ne_cconv_ntt(ne_params p, ne_digits dg, const int32_t* c, const int8_t* g, int64_t* out,
                        uint32_t* flags, uint64_t* nflag, int64_t batch, int64_t N, int32_t fuse,
-                       int32_t r, int32_t plain, int32_t* status, cudaStream_t s);
+                       int32_t r, int32_t plain, ne_faults faults, int32_t* status, cudaStream_t s);
 
 /* Workspace bytes ne_cconv_ntt_any needs for batch groups of M streams of
  * length N (-1 for invalid sizes). */
@@ -209,9 +295,11 @@ int64_t ne_cconv_ntt_any_workspace(int32_t M, int64_t N, int64_t batch);
  * (plain = 1: the raw values) are transformed modulo two primes (77 * 2^19 + 1
  * and 69 * 2^19 + 1) at length N (a power of two) or at the next power of two
  * >= 2N - 1 (a linear convolution folded back), and the outputs rebuilt by the
- * Chinese remainder theorem, then the epilogue of ne_cconv_digits.
+ * Chinese remainder theorem, then the epilogue (and fault hook, positions
+ * group * N + i) of ne_cconv_digits.
  * cmin, cmax: the range of the stream values; an input outside it sets
- * *status = NE_ERANGE (device int32, nullable), and the host returns
+ * *status = NE_ERANGE (device int32, nullable; the lost stream's inputs are
+ * checked too under NE_FUSE_RECOVER), and the host returns
  * NE_ERANGE when N * max|c| (2^l + 1) * 128 could leave the two-prime range.
  * workspace: device, 16-byte aligned, at least ne_cconv_ntt_any_workspace
  * bytes (caller-owned scratch).  The first call on a device also fills the
@@ -220,8 +308,8 @@ int64_t ne_cconv_ntt_any_workspace(int32_t M, int64_t N, int64_t batch);
  * batch <= 65535. */
 ne_status ne_cconv_ntt_any(ne_params p, int32_t cmin, int32_t cmax, const int32_t* c, const int8_t* g,
                            int64_t* out, uint32_t* flags, uint64_t* nflag, int64_t batch, int64_t N,
-                           int32_t fuse, int32_t r, int32_t plain, int32_t* status, void* workspace,
-                           int64_t workspace_bytes, cudaStream_t s);
+                           int32_t fuse, int32_t r, int32_t plain, ne_faults faults, int32_t* status,
+                           void* workspace, int64_t workspace_bytes, cudaStream_t s);
 
 /* ------------------------------------------------------------------------ */
 /* Extraction, check and recovery (Eq. 17-20, Eq. 24, Prop. 3)               */
@@ -246,10 +334,21 @@ ne_status ne_extract(ne_params p, const int64_t* delta, int64_t* d_hat,
  * [batch][M][n]; flags/nflag as for ne_extract (at least one non-null).
  * With n even and delta 16-byte aligned the reads are staged in shared memory
  * by bulk copies; if such a copy fails to arrive within the kernel's bounded
- * wait, the positions it carried are reported flagged and *status is set to
- * NE_ETIMEOUT (status: device int32, nullable, otherwise left untouched). */
+ * wait, the positions it carried and those of every later unit of the same
+ * block are reported flagged (they are not checked), *status is set to
+ * NE_ETIMEOUT (status: device int32, nullable, otherwise left untouched), and
+ * the block waits, again bounded, for its copies in flight before it returns. */
 ne_status ne_check(ne_params p, const int64_t* delta, int64_t batch, int64_t n, int32_t r,
                    uint32_t* flags, uint64_t* nflag, int32_t* status, cudaStream_t s);
+
+/* Test support (no counterpart in the paper; process-wide): the number of
+ * polls of the first bounded wait of every block of ne_check's staged kernel
+ * (default and maximum 2^22, the limit every other wait keeps, the drain
+ * included).  0 makes that wait give up at once, so a test reaches the
+ * timeout path without any fault: the block reports NE_ETIMEOUT, reports
+ * every position of its units flagged, and drains its copies (which do
+ * arrive) before it returns.  NE_EINVAL above the maximum. */
+ne_status ne_check_set_wait_limit(uint32_t polls);
 
 /* Prop. 3: stream r_lost is unavailable (never read, may hold anything);
  * all M outputs are rebuilt from the other M-1. */
@@ -533,30 +632,6 @@ ne_status ne_batch_run_static(const ne_job* jobs, int32_t njobs, ne_batch_config
  * arrays are host arrays read during the call. */
 ne_status ne_copy_regions_h2d(void* dst_base, const void* src_base, const int64_t* dst_off, const int64_t* src_off,
                               const int64_t* nbytes, int64_t count, cudaStream_t s);
-
-/* Measurement support (no counterpart in the paper): runs a register-resident
- * loop of mma.sync.m16n8k32 s8 instructions on every SM -- the throughput
- * ceiling of the int8 tensor path on sm_103a -- and writes the number of
- * int8 operations (2 per multiply-add) it issued to *ops (host pointer).
- * The caller times the launch on stream s. */
-ne_status ne_probe_mma_peak(int32_t iters, int64_t* ops, cudaStream_t s);
-
-/* The same for dp4a on the CUDA cores (four int8 products added into an
- * int32 per instruction), the second int8 pipe the convolution uses. */
-ne_status ne_probe_dp4a_peak(int32_t iters, int64_t* ops, cudaStream_t s);
-
-/* The 32-bit integer multiply-add (IMAD) rate of the CUDA cores: *ops
- * receives the multiply-adds issued. */
-ne_status ne_probe_imad_peak(int32_t iters, int64_t* ops, cudaStream_t s);
-
-/* Both int8 pipes together: blocks_per_sm blocks per SM, each with mma_warps
- * warps running iters_mma rounds of the tensor loop above and dp4a_warps warps
- * running iters_dp4a rounds of the dp4a loop, so the split of work between the
- * pipes can match that of a kernel using both.  *ops receives the total int8
- * operations.  mma_warps + dp4a_warps in [1, 16]; blocks_per_sm in [1, 8]. */
-ne_status ne_probe_mixed_peak(int32_t iters_mma, int32_t iters_dp4a, int32_t mma_warps,
-                              int32_t dp4a_warps, int32_t blocks_per_sm, int64_t* ops,
-                              cudaStream_t s);
 
 /* Message of the last failed call on this host thread ("" if none). */
 const char* ne_last_error(void);

@@ -51,6 +51,8 @@ def _L():
         lib = ctypes.CDLL(build())
         i32, i64, p = ctypes.c_int, ctypes.c_int64, ctypes.c_void_p
         lib.or_threads.restype = i32
+        lib.or_set_threads.argtypes = [i32]
+        lib.or_set_threads.restype = None
         lib.or_range_eq14.argtypes = [i32, i32, i32]
         lib.or_range_eq14.restype = i64
         lib.or_choose_l.argtypes = [i32, i32, i64, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
@@ -96,6 +98,11 @@ def _arr(a, dtype):
 def threads() -> int:
     """OpenMP threads the oracle uses."""
     return int(_L().or_threads())
+
+
+def set_threads(n: int) -> None:
+    """OpenMP threads for the following calls (for timing; results are the same)."""
+    _L().or_set_threads(int(n))
 
 
 # ---- parameters (Eq. 13, Eq. 14, Table II) --------------------------------

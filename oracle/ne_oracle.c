@@ -105,6 +105,15 @@ int or_threads(void) {
 #endif
 }
 
+/* Threads for the following calls (timing only; the results do not depend on it). */
+void or_set_threads(int n) {
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 /* ---- parameter choice (Eq. 13, Eq. 14, Table II) ------------------------- */
 
 /* Eq. 14: the output range supported is |d| <= 2^((M-3)l+k) (2^(l-1) - 1).

@@ -17,6 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OBJDIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libne.so")
+PROBE = os.path.join(HERE, "probe")
+PROBE_LIB = os.path.join(PROBE, "libne_probe.so")
 
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -31,9 +33,10 @@ def _deps_mtime() -> float:
 
 def _compile(src: str, verbose: bool) -> str:
     obj = os.path.join(OBJDIR, os.path.basename(src) + ".o")
-    if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(src), _deps_mtime()):
+    deps = max(_deps_mtime(), max([os.path.getmtime(h) for h in glob.glob(os.path.join(PROBE, "*.h"))] + [0.0]))
+    if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(src), deps):
         return obj
-    cmd = [NVCC, *ARCH, *FLAGS, "-c", src, "-o", obj + ".tmp"]
+    cmd = [NVCC, *ARCH, *FLAGS, "-I", PROBE, "-c", src, "-o", obj + ".tmp"]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -45,19 +48,31 @@ def _compile(src: str, verbose: bool) -> str:
     return obj
 
 
-def build(verbose: bool = False) -> str:
-    os.makedirs(OBJDIR, exist_ok=True)
-    srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
-    with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 4)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, verbose), srcs))
+def _link(lib: str, objs) -> None:
     newest = max(os.path.getmtime(o) for o in objs)
-    if not os.path.exists(LIB) or os.path.getmtime(LIB) < newest:
-        tmp = LIB + f".{os.getpid()}.tmp"
+    manifest = os.path.join(OBJDIR, os.path.basename(lib) + ".objs")
+    listed = open(manifest).read() if os.path.exists(manifest) else ""
+    if not os.path.exists(lib) or os.path.getmtime(lib) < newest or listed != "\n".join(objs):
+        tmp = lib + f".{os.getpid()}.tmp"
         cmd = [NVCC, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart_static", "-lrt", "-lpthread", "-ldl"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-        os.replace(tmp, LIB)
+        os.replace(tmp, lib)
+        with open(manifest, "w") as f:
+            f.write("\n".join(objs))
+
+
+def build(verbose: bool = False) -> str:
+    """Builds libne.so (the library) and probe/libne_probe.so (the benchmark's
+    throughput probes, not part of the library's ABI); returns libne.so."""
+    os.makedirs(OBJDIR, exist_ok=True)
+    srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+    psrcs = sorted(glob.glob(os.path.join(PROBE, "*.cu")))
+    with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 4)) as ex:
+        objs = list(ex.map(lambda s: _compile(s, verbose), srcs + psrcs))
+    _link(LIB, objs[:len(srcs)])
+    _link(PROBE_LIB, objs[len(srcs):])
     return LIB
 
 

@@ -494,6 +494,7 @@ __device__ __forceinline__ void run_cconv(const BatchK& k, const DevJob* J, cons
     int64_t* fp;
     fill_common(k, J, fp, t.fault_stream, t.fault_bit, t.nfault);
     t.fault_pos = fp;
+    t.fault_base = 0;
     t.N = J->N;
     t.M = J->M;
     t.S = J->S;

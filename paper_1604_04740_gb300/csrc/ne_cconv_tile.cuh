@@ -30,6 +30,7 @@
 
 #include "ne_common.cuh"
 #include "ne_extract.cuh"
+#include "ne_faults.cuh"
 #include "ne_mma.cuh"
 
 namespace ne {
@@ -56,10 +57,11 @@ struct TileArgs {
     int64_t* out;                // [M][N]
     uint32_t* flags;             // [N/32] or null
     unsigned long long* nflag;   // or null
-    const int64_t* fault_pos;    // faults of this group, sorted by position (or null)
-    const int32_t* fault_stream;
+    const int64_t* fault_pos;    // faults, sorted by position (or null): output i of this
+    const int32_t* fault_stream; // group is position fault_base + i of the list
     const int32_t* fault_bit;
     int64_t nfault;
+    int64_t fault_base;
     int N, M, S, MS, l, r, fuse;
     int flags_atomic;            // bitmap pre-zeroed: OR in the set bits instead of storing words
     int shift[NE_MAX_DIGITS];
@@ -72,20 +74,19 @@ struct TileArgs {
     uint32_t raw_off;
     int raw_lo, raw_hi, raw_plain;
     int raw_byte[4];
+    // words form: the entangled words [M][N] themselves, split into the plan's
+    // digits while loading; a word with y = word + 0x80..80 and
+    // (y & w_nsmask) != w_nswant is outside the plan and sets *status = NE_ERANGE
+    const int64_t* cwords;
+    uint64_t w_nsmask, w_nswant;
 };
 
-__device__ __forceinline__ int64_t shl64(int64_t x, int s) { return (int64_t)((uint64_t)x << s); }
+// where a tile's digit rows come from
+constexpr int LD_PLANES = 0;   // digit planes in memory (cp.async)
+constexpr int LD_RAW = 1;      // the raw int32 streams: Eq. 16 and the split while loading
+constexpr int LD_WORDS = 2;    // the entangled int64 words: the split while loading
 
-// first index f in [0, n) with pos[f] >= key (pos sorted ascending)
-__device__ __forceinline__ int64_t lower_bound(const int64_t* pos, int64_t n, int64_t key) {
-    int64_t lo = 0, hi = n;
-    while (lo < hi) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (pos[mid] < key) lo = mid + 1;
-        else hi = mid;
-    }
-    return lo;
-}
+__device__ __forceinline__ int64_t shl64(int64_t x, int s) { return (int64_t)((uint64_t)x << s); }
 
 // LT: the job's l when it is 16 (every shift below is then a constant; with
 // the two digits at shifts 0 and 16 of the byte-aligned plan of int8-valued
@@ -110,9 +111,10 @@ __device__ __forceinline__ void epilogue_l(const TileArgs& a, const int32_t* sta
     const bool check = (a.fuse == NE_FUSE_EXTRACT_CHECK);
     const bool need_r = (a.fuse != NE_FUSE_RECOVER);
     int64_t f0 = 0, f1 = 0;
+    const int64_t key0 = a.fault_base + i0;
     if (a.nfault > 0) {
-        f0 = lower_bound(a.fault_pos, a.nfault, i0);
-        f1 = lower_bound(a.fault_pos, a.nfault, i0 + npos);
+        f0 = fault_lower_bound(a.fault_pos, 0, a.nfault, key0);
+        f1 = fault_lower_bound(a.fault_pos, f0, a.nfault, key0 + npos);
     }
     for (int base = threadIdx.x & ~31; base < npos; base += nthreads) {
         const int i = base + lane;
@@ -121,8 +123,7 @@ __device__ __forceinline__ void epilogue_l(const TileArgs& a, const int32_t* sta
         if (a.fuse == NE_FUSE_NONE) {
             for (int m = 0; m < M; m++) {
                 int64_t v = digits(sp, m);
-                for (int64_t f = f0; f < f1; f++)
-                    if (a.fault_pos[f] == i0 + i && a.fault_stream[f] == m) v ^= (int64_t)(1ull << a.fault_bit[f]);
+                if (f1 > f0) v = apply_faults(v, a.fault_pos, a.fault_stream, a.fault_bit, f0, f1, key0 + i, m);
                 a.out[(int64_t)m * a.N + i0 + i] = v;
             }
             continue;
@@ -136,8 +137,7 @@ __device__ __forceinline__ void epilogue_l(const TileArgs& a, const int32_t* sta
             int64_t v = 0;
             if (j > 0 || need_r) {
                 v = digits(sp, m);
-                for (int64_t f = f0; f < f1; f++)
-                    if (a.fault_pos[f] == i0 + i && a.fault_stream[f] == m) v ^= (int64_t)(1ull << a.fault_bit[f]);
+                if (f1 > f0) v = apply_faults(v, a.fault_pos, a.fault_stream, a.fault_bit, f0, f1, key0 + i, m);
             }
             rot[j] = v;
         }
@@ -182,11 +182,50 @@ __device__ __forceinline__ uint32_t pick4(uint32_t y0, uint32_t y1, uint32_t y2,
 // the caller commits and waits.  Fused: every work item (block, stream,
 // 16 positions) loads 16 inputs of c_m and c_{m-1}, forms the words of
 // Eq. 16 in 32 bits and stores the S digit rows' 16 bytes.
-template <bool RAW>
+template <int LD>
 __device__ __forceinline__ void load_window(const TileArgs& a, uint8_t* sig, int WB, int first, int NB, int nthr) {
     const int N = a.N, MS = a.MS;
     const int tid = threadIdx.x;
-    if constexpr (!RAW) {
+    if constexpr (LD == LD_WORDS) {
+        const int M = a.M, S = a.S;
+        bool bad = false;
+        for (int e = tid; e < WB * M * 4; e += nthr) {
+            const int c16 = e & 3, rowm = e >> 2;
+            const int blk_rel = rowm / M, m = rowm - blk_rel * M;
+            int ab = (first + blk_rel) % NB;
+            if (ab < 0) ab += NB;
+            uint8_t* dst = sig + (blk_rel * MS + m * S) * ROWB + c16 * 16;
+            if (a.fuse == NE_FUSE_RECOVER && m == a.r) {
+                for (int s = 0; s < S; s++) *reinterpret_cast<uint4*>(dst + s * ROWB) = make_uint4(0u, 0u, 0u, 0u);
+                continue;
+            }
+            const longlong2* src = reinterpret_cast<const longlong2*>(a.cwords + (int64_t)m * N + (int64_t)ab * T + c16 * 16);
+            uint64_t y[16];
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                const longlong2 v = __ldg(src + q);
+                y[2 * q] = (uint64_t)v.x + 0x8080808080808080ull;
+                y[2 * q + 1] = (uint64_t)v.y + 0x8080808080808080ull;
+            }
+#pragma unroll
+            for (int q = 0; q < 16; q++) bad |= (y[q] & a.w_nsmask) != a.w_nswant;
+#pragma unroll
+            for (int s = 0; s < NE_MAX_DIGITS; s++) {
+                if (s >= S) break;
+                const int sh = a.shift[s];
+                uint32_t w[4];
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const uint32_t v0 = (uint32_t)(y[4 * q] >> sh), v1 = (uint32_t)(y[4 * q + 1] >> sh);
+                    const uint32_t v2 = (uint32_t)(y[4 * q + 2] >> sh), v3 = (uint32_t)(y[4 * q + 3] >> sh);
+                    w[q] = __byte_perm(__byte_perm(v0, v1, 0x0040), __byte_perm(v2, v3, 0x0040), 0x5410) ^ 0x80808080u;
+                }
+                *reinterpret_cast<uint4*>(dst + s * ROWB) = make_uint4(w[0], w[1], w[2], w[3]);
+            }
+        }
+        if (bad && a.status) atomicExch(a.status, (int32_t)NE_ERANGE);
+        return;
+    } else if constexpr (LD == LD_PLANES) {
         const uint32_t sig_s = smem_u32(sig);
         for (int e = tid; e < WB * MS * 4; e += nthr) {
             const int c16 = e & 3, row = e >> 2;
@@ -213,6 +252,9 @@ __device__ __forceinline__ void load_window(const TileArgs& a, uint8_t* sig, int
         }
         const int64_t pos = (int64_t)ab * T + c16 * 16;
         const int mp = m == 0 ? M - 1 : m - 1;
+        // a lost stream r is never loaded as c_m, but its inputs still enter
+        // the words of stream r+1 (Eq. 16): check them there
+        const bool check_prev = a.fuse == NE_FUSE_RECOVER && mp == a.r;
         const int4* xm = reinterpret_cast<const int4*>(a.craw + (int64_t)m * N + pos);
         const int4* xp = reinterpret_cast<const int4*>(a.craw + (int64_t)mp * N + pos);
         uint32_t y[16];
@@ -237,6 +279,9 @@ __device__ __forceinline__ void load_window(const TileArgs& a, uint8_t* sig, int
                 y[4 * q + 1] += (uint32_t)v.y << a.l;
                 y[4 * q + 2] += (uint32_t)v.z << a.l;
                 y[4 * q + 3] += (uint32_t)v.w << a.l;
+                if (check_prev)
+                    worst = max(max(max(worst, (uint32_t)v.x - (uint32_t)a.raw_lo), (uint32_t)v.y - (uint32_t)a.raw_lo),
+                                max((uint32_t)v.z - (uint32_t)a.raw_lo, (uint32_t)v.w - (uint32_t)a.raw_lo));
             }
         }
 #pragma unroll
@@ -254,7 +299,7 @@ __device__ __forceinline__ void load_window(const TileArgs& a, uint8_t* sig, int
 
 // The tile of output blocks [p0, p0 + npb) of one group; all 256 threads of
 // the block take part.  smem: smem_bytes(MS) bytes, 128-byte aligned.
-template <int NTW, int MT, bool RAW = false>
+template <int NTW, int MT, int LD = LD_PLANES>
 __device__ __forceinline__ void tile(const TileArgs& a, uint8_t* smem, int p0, int npb) {
     const int MS = a.MS;
     const int N = a.N;
@@ -286,7 +331,7 @@ __device__ __forceinline__ void tile(const TileArgs& a, uint8_t* smem, int p0, i
     for (int u0 = 0; u0 < NB; u0 += uch) {
         const int uc = min(uch, NB - u0);
         // digit rows of input blocks (p0 - (u0 + uch - 1) + blk_rel) mod NB
-        load_window<RAW>(a, sig, WB, p0 - (u0 + uch - 1), NB, THREADS);
+        load_window<LD>(a, sig, WB, p0 - (u0 + uch - 1), NB, THREADS);
         cp_async_commit();
         // g copies: copy rr, byte z holds g[(T (u0 + uch) - (z + rr - PADB)) mod N]
         const int top = T * (u0 + uch);
@@ -376,7 +421,7 @@ __host__ __device__ constexpr int hybrid_smem_bytes(int MS) {
     return WBMAX * MS * ROWB + 4 * GW + 4 * GDP + MS * NPB * SP * 4;
 }
 
-template <int MT, int MSC, int HW, int R, bool RAW = false>
+template <int MT, int MSC, int HW, int R, int LD = LD_PLANES>
 __device__ __forceinline__ void tile_hybrid(const TileArgs& a, uint8_t* smem) {
     constexpr int MS = MSC;
     constexpr int NTHR = hybrid_threads(HW);
@@ -400,7 +445,7 @@ __device__ __forceinline__ void tile_hybrid(const TileArgs& a, uint8_t* smem) {
     const uint32_t sig_s = smem_u32(sig);
 
     // -- loads (every thread) --
-    load_window<RAW>(a, sig, WB, -(uch - 1), NB, NTHR);
+    load_window<LD>(a, sig, WB, -(uch - 1), NB, NTHR);
     cp_async_commit();
     // the filter, staged once in the stash's space (free until the stash is
     // written): 4-byte loads instead of a global byte load per copied byte

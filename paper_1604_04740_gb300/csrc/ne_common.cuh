@@ -14,6 +14,25 @@ ne_status check_launch(const char* what);
 int sm_count();                      // SMs of the current device (cached per device)
 ne_status validate_params(const ne_params& p);
 ne_status validate_digits(const ne_digits& dg);
+ne_status validate_faults(const ne_faults& f, const char* who);
+
+// internal launches shared by the entry points (ne_ops_i64.cu, ne_extract.cu)
+ne_status gemm_i64_launch(int32_t P, const int64_t* x, const int8_t* G, int64_t* out, int32_t rows, int32_t cols,
+                          int32_t k, uint32_t skip_mask, cudaStream_t s);
+ne_status cconv_i64_launch(int32_t P, const int64_t* x, const int8_t* g, int64_t* out, int64_t batch, int64_t N,
+                           uint32_t skip_mask, cudaStream_t s);
+ne_status faults_launch(int64_t* delta, int M, int64_t batch, int64_t n, const ne_faults& F, uint32_t skip_mask,
+                        cudaStream_t s);
+// the tensor-path operations on the entangled words, split into the digits of
+// dg in the tiles' loaders (ne_gemm_digits.cu, ne_cconv_digits.cu)
+ne_status gemm_s8slice(ne_params p, ne_digits dg, const int64_t* words, const int8_t* G, int64_t* out,
+                       uint32_t* flags, uint64_t* nflag, int32_t rows, int32_t cols, int32_t k, int32_t fuse,
+                       int32_t r, const ne_faults& faults, int32_t* status, cudaStream_t s);
+ne_status cconv_s8slice(ne_params p, ne_digits dg, const int64_t* words, const int8_t* g, int64_t* out,
+                        uint32_t* flags, uint64_t* nflag, int64_t batch, int64_t N, int32_t fuse, int32_t r,
+                        const ne_faults& faults, int32_t* status, cudaStream_t s);
+ne_status extract_launch(const ne_params& p, const int64_t* delta, int64_t* d_hat, int64_t batch, int64_t n, int r,
+                         bool check, uint32_t* flags, unsigned long long* nflag, cudaStream_t s);
 
 // grid of roughly `waves` full waves of `threads`-thread blocks on this GPU
 inline int wave_blocks(int threads, int waves = 4) {

@@ -206,7 +206,8 @@ __global__ void __launch_bounds__(256, 3) k_entangle_digits8(const int32_t* __re
 
 // Digit planes on the range-checked fast path (ne_entangle.cuh): eight
 // positions per thread over the flat (group, chunk) space.
-template <int MT>
+// PLAIN: the digits of the raw streams (no predecessor term).
+template <int MT, bool PLAIN = false>
 __global__ void __launch_bounds__(256) k_entangle_digits_fast(const int32_t* __restrict__ c, int8_t* __restrict__ planes,
                                                               int l, FastPlan F, int64_t batch, int64_t n,
                                                               int32_t* status) {
@@ -214,7 +215,8 @@ __global__ void __launch_bounds__(256) k_entangle_digits_fast(const int32_t* __r
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     uint32_t worst = 0;
     for (FlatWalk w((int64_t)blockIdx.x * blockDim.x + threadIdx.x, stride, nchunk); w.b < batch; w.next())
-        worst = max(worst, entangle_chunk8<MT>(c + w.b * MT * n + w.q * 8, planes + w.b * MT * F.S * n + w.q * 8, n, l, F));
+        worst = max(worst, entangle_chunk8<MT, PLAIN>(c + w.b * MT * n + w.q * 8, planes + w.b * MT * F.S * n + w.q * 8,
+                                                      n, l, F));
     if (worst > (uint32_t)F.hi - (uint32_t)F.lo && status) atomicExch(status, (int32_t)NE_ERANGE);
 }
 
@@ -360,6 +362,51 @@ extern "C" ne_status ne_entangle_digits(ne_params p, ne_digits dg, const int32_t
         k_entangle_digits<1><<<grid_rows(batch, n, T), T, 0, s>>>(c, planes, p.M, p.l, P, batch, n, status);
     }
     return check_launch("ne_entangle_digits");
+}
+
+extern "C" ne_status ne_split_digits_raw(ne_params p, ne_digits dg, const int32_t* c, int8_t* planes,
+                                         int64_t batch, int64_t n, int32_t* status, cudaStream_t s) {
+    ne_status st = validate_params(p);
+    if (st) return st;
+    if ((st = validate_digits(dg))) return st;
+    if (batch < 0 || n < 0) return fail(NE_EINVAL, "ne_split_digits_raw: batch=%lld n=%lld", (long long)batch, (long long)n);
+    if (p.M > 5) return fail(NE_EINVAL, "ne_split_digits_raw: M=%d exceeds 5", p.M);
+    // the raw value c_m is the word of Eq. 16 with a zero predecessor, so its
+    // digits are in the plan whenever 0 lies in the plan's range
+    FastPlan F;
+    bool planned = false;
+    if (dg.S == 1 && dg.shift[0] == 0 && dg.lo <= dg.hi && dg.lo >= -128 && dg.hi <= 127) {
+        // one digit: int8-valued streams as they are
+        F.off = 0x80u;
+        F.ns_mask = F.ns_want = 0;
+        F.lim = 256u;
+        F.S = 1;
+        F.lo = dg.lo;
+        F.hi = dg.hi;
+        for (int t = 0; t < 4; t++) F.byte_of[t] = 0;
+        F.pmask = 0;
+        planned = true;
+    } else if (dg.lo <= 0 && 0 <= dg.hi && dg.l == p.l) {
+        ne_digits ref;
+        planned = ne_plan_digits(dg.l, dg.lo, dg.hi, &ref) == NE_OK && ref.S == dg.S;
+        for (int s2 = 0; planned && s2 < dg.S; s2++) planned = ref.shift[s2] == dg.shift[s2];
+        planned = planned && make_fast_plan(dg, p.l, &F);
+    }
+    if (!planned)
+        return fail(NE_EINVAL, "ne_split_digits_raw: dg must be one digit of values in [-128, 127] or the plan of "
+                               "(l, lo, hi) with lo <= 0 <= hi and words of at most 4 digits");
+    if (n % 8 != 0 || !aligned(c, 16) || !aligned(planes, 8))
+        return fail(NE_EINVAL, "ne_split_digits_raw: n must be a multiple of 8, c 16-byte and planes 8-byte aligned");
+    if (batch == 0 || n == 0) return NE_OK;
+    if (!c || !planes) return fail(NE_EINVAL, "ne_split_digits_raw: null pointer");
+    const int T = 256;
+    const int blocks = flat_blocks(batch * (n / 8), T);
+    switch (p.M) {
+        case 3: k_entangle_digits_fast<3, true><<<blocks, T, 0, s>>>(c, planes, p.l, F, batch, n, status); break;
+        case 4: k_entangle_digits_fast<4, true><<<blocks, T, 0, s>>>(c, planes, p.l, F, batch, n, status); break;
+        default: k_entangle_digits_fast<5, true><<<blocks, T, 0, s>>>(c, planes, p.l, F, batch, n, status); break;
+    }
+    return check_launch("ne_split_digits_raw");
 }
 
 extern "C" ne_status ne_abft_encode(int32_t M, const int32_t* c, int64_t* x, int64_t batch, int64_t n,

@@ -108,12 +108,16 @@ __global__ void __launch_bounds__(TH) k_extract(const int64_t* __restrict__ delt
 // Requires n even and delta 16-byte aligned (every copy then starts and ends
 // on 16 bytes).
 constexpr uint32_t CK_WAIT_LIMIT = 1u << 22;
+// polls of each block's first wait (ne_check_set_wait_limit; every other wait,
+// the drain included, keeps CK_WAIT_LIMIT)
+uint32_t g_first_wait_limit = CK_WAIT_LIMIT;
 
 // TH threads, PER positions per thread and unit (2 or 4), S stages
 template <int MT, int LT, int TH, int PER, int S>
 __global__ void __launch_bounds__(TH, 1) k_check_staged(const int64_t* __restrict__ delta, int l, int r,
                                                         int64_t batch, int64_t n, uint32_t* __restrict__ flags,
-                                                        unsigned long long* nflag, int32_t* status) {
+                                                        unsigned long long* nflag, int32_t* status,
+                                                        uint32_t first_limit) {
     constexpr int CK_POS = PER * TH;
     constexpr int WPOS = 32 * PER;                      // positions of a warp
     extern __shared__ __align__(128) int64_t ring[];   // [S][MT][CK_POS]
@@ -159,7 +163,7 @@ __global__ void __launch_bounds__(TH, 1) k_check_staged(const int64_t* __restric
     int it = 0;
     for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x, it++, next(b, c)) {
         const int s = it % S;
-        const bool ok = mbar_wait(&full[s], (uint32_t)(it / S) & 1u, CK_WAIT_LIMIT);
+        const bool ok = mbar_wait(&full[s], (uint32_t)(it / S) & 1u, it == 0 ? first_limit : CK_WAIT_LIMIT);
         const int64_t p0 = c * CK_POS;
         const int64_t* st = ring + s * MT * CK_POS;
 #pragma unroll
@@ -189,16 +193,29 @@ __global__ void __launch_bounds__(TH, 1) k_check_staged(const int64_t* __restric
             emit_flags<2>(f, lane, (p0 + warp * WPOS + k * 64) / 64, wpr, flags ? flags + b * wpr : nullptr, nflag);
         }
         if (!__syncthreads_and(ok)) {
-            // a copy did not arrive: report it, wait (bounded) for the copies
-            // still in flight into this block's stages, and leave
+            // a copy did not arrive in time: report the timeout, report every
+            // position of every later unit of this block flagged (none of them
+            // is checked), wait (bounded) for the copies still in flight into
+            // this block's stages, and leave
+            if (tid == 0 && status) atomicExch(status, (int32_t)NE_ETIMEOUT);
+            int64_t rb = b, rc = c;
+            next(rb, rc);
+            for (int64_t v = u + gridDim.x; v < nunits; v += gridDim.x, next(rb, rc)) {
+#pragma unroll
+                for (int k = 0; k < PER / 2; k++) {
+                    const int64_t q = rc * CK_POS + warp * WPOS + k * 64 + lane * 2;
+                    emit_flags<2>(q < n ? 3u : 0u, lane, (rc * CK_POS + warp * WPOS + k * 64) / 64, wpr,
+                                  flags ? flags + rb * wpr : nullptr, nflag);
+                }
+            }
             if (tid == 0) {
-                if (status) atomicExch(status, (int32_t)NE_ETIMEOUT);
                 for (int k = 0; k < S; k++) {
                     const int jt = it + k;
                     if (u + (int64_t)k * gridDim.x < nunits)
                         mbar_wait(&full[jt % S], (uint32_t)(jt / S) & 1u, CK_WAIT_LIMIT);
                 }
             }
+            __syncthreads();
             return;
         }
         if (tid == 0) {
@@ -228,7 +245,7 @@ void launch_check_staged_v(const int64_t* delta, int l, int r, int64_t batch, in
     const int64_t nunits = batch * ((n + PER * TH - 1) / (PER * TH));
     int64_t grid = (int64_t)sm_count() * per_sm;
     if (grid > nunits) grid = nunits;
-    kern<<<(unsigned)grid, TH, smem, s>>>(delta, l, r, batch, n, flags, nflag, status);
+    kern<<<(unsigned)grid, TH, smem, s>>>(delta, l, r, batch, n, flags, nflag, status, g_first_wait_limit);
 }
 
 // 256 threads of 4 positions and 3 stages (2 for M > 4): three blocks per SM
@@ -332,6 +349,20 @@ __global__ void k_inject(int64_t* delta, int P, int64_t batch, int64_t n, const 
     }
 }
 
+// the fault hook of the unfused operations: entry f XORs bit (bit[f] mod 64)
+// into delta_{stream[f]} at flat position pos[f] = group * n + i; streams
+// outside [0, M), streams in skip_mask (never computed) and positions outside
+// the array hit nothing
+__global__ void k_apply_faults(int64_t* delta, int M, int64_t batch, int64_t n, ne_faults F, uint32_t skip_mask) {
+    for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < F.count; f += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t key = F.pos[f];
+        const int m = F.stream[f];
+        if (key < 0 || key >= batch * n || m < 0 || m >= M || ((skip_mask >> m) & 1u)) continue;
+        const int64_t g = key / n, i = key - g * n;
+        atomicXor(reinterpret_cast<unsigned long long*>(delta + (g * M + m) * n + i), 1ull << (F.bit[f] & 63));
+    }
+}
+
 // ---- checksum ABFT check / recovery -----------------------------------------------
 
 __global__ void __launch_bounds__(kThreads) k_abft_check(const int64_t* __restrict__ d, int M, int64_t batch, int64_t n,
@@ -370,6 +401,30 @@ __global__ void __launch_bounds__(kThreads) k_abft_recover(int64_t* d, int M, in
 
 }  // namespace
 
+namespace ne {
+
+// Internal launches for the operations' unfused epilogues (arguments checked
+// by the caller).  The extraction reads every stream of a position before it
+// writes any, and no position twice, so d_hat may be delta itself.
+ne_status faults_launch(int64_t* delta, int M, int64_t batch, int64_t n, const ne_faults& F, uint32_t skip_mask,
+                        cudaStream_t s) {
+    if (F.count <= 0) return NE_OK;
+    int blocks = (int)((F.count + 255) / 256);
+    if (blocks > 4096) blocks = 4096;
+    k_apply_faults<<<blocks, 256, 0, s>>>(delta, M, batch, n, F, skip_mask);
+    return check_launch("fault hook");
+}
+
+ne_status extract_launch(const ne_params& p, const int64_t* delta, int64_t* d_hat, int64_t batch, int64_t n, int r,
+                         bool check, uint32_t* flags, unsigned long long* nflag, cudaStream_t s) {
+    if (batch == 0 || n == 0) return NE_OK;
+    if (check) launch_extract<true, true>(delta, d_hat, p.M, p.l, r, batch, n, flags, nflag, s);
+    else launch_extract<true, false>(delta, d_hat, p.M, p.l, r, batch, n, nullptr, nullptr, s);
+    return check_launch("extraction");
+}
+
+}  // namespace ne
+
 extern "C" ne_status ne_extract(ne_params p, const int64_t* delta, int64_t* d_hat, int64_t batch, int64_t n,
                                 int32_t r, uint32_t* flags, uint64_t* nflag, cudaStream_t s) {
     ne_status st = common_args(p, batch, n, r, "ne_extract");
@@ -394,6 +449,12 @@ extern "C" ne_status ne_check(ne_params p, const int64_t* delta, int64_t batch, 
     if (!launch_check_staged(delta, p.M, p.l, r, batch, n, flags, nf, status, s))
         launch_extract<false, true>(delta, nullptr, p.M, p.l, r, batch, n, flags, nf, s);
     return check_launch("ne_check");
+}
+
+extern "C" ne_status ne_check_set_wait_limit(uint32_t polls) {
+    if (polls > CK_WAIT_LIMIT) return fail(NE_EINVAL, "ne_check_set_wait_limit: %u polls exceed %u", polls, CK_WAIT_LIMIT);
+    g_first_wait_limit = polls;
+    return NE_OK;
 }
 
 extern "C" ne_status ne_recover(ne_params p, const int64_t* delta, int64_t* d_hat, int64_t batch, int64_t n,

@@ -19,6 +19,7 @@
 // digit-plane tiles arrive by cp.async in a 3-stage pipeline.
 #include "ne_common.cuh"
 #include "ne_extract.cuh"
+#include "ne_faults.cuh"
 #include "ne_mma.cuh"
 
 namespace {
@@ -43,7 +44,34 @@ struct GemmArgs {
     int M, S, MS, l, r, fuse;
     int direct_flags;       // cols % 32 == 0: each warp owns whole bitmap words
     int shift[NE_MAX_DIGITS];
+    ne_faults faults;       // flat positions i * cols + j (count 0: none)
+    // words form (WORDS): the entangled words themselves [M][rows][k], split
+    // into the digits of the plan while the tiles load; a word whose bytes
+    // outside the plan's digits differ from the balanced split's (y & ns_mask
+    // != ns_want, y = word + 0x80..80) sets *status = NE_ERANGE
+    const int64_t* words;
+    int32_t* status;
+    uint64_t ns_mask, ns_want;
 };
+
+// The S digit bytes of 16 words (already offset by 0x80 in every byte) as S
+// rows of 16 bytes: row s holds byte shift[s] / 8 of each word XOR 0x80.
+__device__ __forceinline__ void store_digit_rows(const uint64_t (&y)[16], const int* shift, int S, uint8_t* dst,
+                                                 int row_stride) {
+#pragma unroll
+    for (int s = 0; s < NE_MAX_DIGITS; s++) {
+        if (s >= S) break;
+        const int sh = shift[s];
+        uint32_t w[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const uint32_t v0 = (uint32_t)(y[4 * q] >> sh), v1 = (uint32_t)(y[4 * q + 1] >> sh);
+            const uint32_t v2 = (uint32_t)(y[4 * q + 2] >> sh), v3 = (uint32_t)(y[4 * q + 3] >> sh);
+            w[q] = __byte_perm(__byte_perm(v0, v1, 0x0040), __byte_perm(v2, v3, 0x0040), 0x5410) ^ 0x80808080u;
+        }
+        *reinterpret_cast<uint4*>(dst + s * row_stride) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
 
 int smem_bytes(int MS) {
     const int pipe = STAGES * (MS * A_STAGE_PER_PLANE + B_STAGE);
@@ -74,6 +102,14 @@ __device__ __forceinline__ void gemm_epilogue(const GemmArgs& a, const int32_t* 
     const bool check = (a.fuse == NE_FUSE_EXTRACT_CHECK);
     const bool need_r = (a.fuse != NE_FUSE_RECOVER);
     const int64_t plane = (int64_t)a.rows * a.cols;
+    // the faults of this tile's row band (every thread finds the same range)
+    const ne_faults& F = a.faults;
+    int64_t f0 = 0, f1 = 0;
+    if (F.count > 0) {
+        const int last_row = min(row0 + BM, a.rows) - 1;
+        f0 = fault_lower_bound(F.pos, 0, F.count, (int64_t)row0 * a.cols + col0);
+        f1 = fault_lower_bound(F.pos, f0, F.count, (int64_t)last_row * a.cols + min(col0 + BN, a.cols));
+    }
     for (int base = threadIdx.x & ~31; base < BM * BN; base += nthreads) {
         const int idx = base + lane;
         const int i = idx / BN, j = idx % BN;
@@ -86,10 +122,10 @@ __device__ __forceinline__ void gemm_epilogue(const GemmArgs& a, const int32_t* 
             if (a.fuse == NE_FUSE_NONE) {
                 for (int m = 0; m < M; m++) {
                     int64_t v = 0;
-                    
 #pragma unroll
                     for (int s = 0; s < NE_MAX_DIGITS; s++)
                         if (s < S) v += shl64(sp[(m * S + s) * BM * SB], a.shift[s]);
+                    if (f1 > f0) v = apply_faults(v, F.pos, F.stream, F.bit, f0, f1, pos, m);
                     a.out[m * plane + pos] = v;
                 }
             } else {
@@ -100,11 +136,12 @@ __device__ __forceinline__ void gemm_epilogue(const GemmArgs& a, const int32_t* 
                     int m = a.r + jj;
                     if (m >= M) m -= M;
                     int64_t v = 0;
-                    if (jj > 0 || need_r)
-                        
+                    if (jj > 0 || need_r) {
 #pragma unroll
-                    for (int s = 0; s < NE_MAX_DIGITS; s++)
-                        if (s < S) v += shl64(sp[(m * S + s) * BM * SB], a.shift[s]);
+                        for (int s = 0; s < NE_MAX_DIGITS; s++)
+                            if (s < S) v += shl64(sp[(m * S + s) * BM * SB], a.shift[s]);
+                        if (f1 > f0) v = apply_faults(v, F.pos, F.stream, F.bit, f0, f1, pos, m);
+                    }
                     rot[jj] = v;
                 }
                 f = extract_rot<MT>(rot, M, a.l, check, res);
@@ -133,7 +170,7 @@ __device__ __forceinline__ void gemm_epilogue(const GemmArgs& a, const int32_t* 
     }
 }
 
-template <int MT>
+template <int MT, bool WORDS>
 __global__ void __launch_bounds__(512, 1) k_gemm_digits(GemmArgs a) {
     extern __shared__ __align__(128) uint8_t smem[];
     const int MS = a.MS;
@@ -153,6 +190,34 @@ __global__ void __launch_bounds__(512, 1) k_gemm_digits(GemmArgs a) {
     // A loads: MS planes x 32 rows x 4 chunks of 16 bytes
     auto load_A = [&](int stage, int kt) {
         const int k0 = kt * BK;
+        if constexpr (WORDS) {
+            // M streams x 32 rows x 4 chunks of 16 words, split into S digit rows each
+            bool bad = false;
+            for (int e = tid; e < a.M * BM * 4; e += nthreads) {
+                const int c16 = e & 3, r = (e >> 2) % BM, m = (e >> 2) / BM;
+                const int gi = row0 + r, gk = k0 + 16 * c16;
+                const bool ok = gi < rows && gk < K && !((a.fuse == NE_FUSE_RECOVER) && m == a.r);
+                uint64_t y[16];
+                if (ok) {
+                    const longlong2* src =
+                        reinterpret_cast<const longlong2*>(a.words + ((int64_t)m * rows + gi) * K + gk);
+#pragma unroll
+                    for (int q = 0; q < 8; q++) {
+                        const longlong2 v = __ldg(src + q);
+                        y[2 * q] = (uint64_t)v.x + 0x8080808080808080ull;
+                        y[2 * q + 1] = (uint64_t)v.y + 0x8080808080808080ull;
+                    }
+#pragma unroll
+                    for (int q = 0; q < 16; q++) bad |= (y[q] & a.ns_mask) != a.ns_want;
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 16; q++) y[q] = 0x8080808080808080ull;    // digits 0
+                }
+                store_digit_rows(y, a.shift, a.S, As + ((stage * MS + m * a.S) * BM + r) * RB + 16 * c16, BM * RB);
+            }
+            if (bad && a.status) atomicExch(a.status, (int32_t)NE_ERANGE);
+            return;
+        }
         const int nchunks = MS * BM * 4;
         for (int e = tid; e < nchunks; e += nthreads) {
             const int c16 = e & 3, r = (e >> 2) % BM, pl = (e >> 2) / BM;
@@ -268,44 +333,57 @@ __global__ void __launch_bounds__(512, 1) k_gemm_digits(GemmArgs a) {
     gemm_epilogue<MT>(a, stash, row0, col0);
 }
 
-template <int MT>
+template <int MT, bool WORDS>
 ne_status launch(const GemmArgs& a, cudaStream_t s) {
     static bool attr_set[64] = {false};
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-        if (cudaFuncSetAttribute(k_gemm_digits<MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes(16)) !=
-            cudaSuccess)
+        if (cudaFuncSetAttribute(k_gemm_digits<MT, WORDS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 smem_bytes(16)) != cudaSuccess)
             return check_launch("ne_gemm_digits: shared-memory attribute");
         attr_set[dev] = true;
     }
     dim3 grid((a.cols + BN - 1) / BN, (a.rows + BM - 1) / BM);
-    k_gemm_digits<MT><<<grid, a.MS * 32, smem_bytes(a.MS), s>>>(a);
+    k_gemm_digits<MT, WORDS><<<grid, a.MS * 32, smem_bytes(a.MS), s>>>(a);
     return check_launch("ne_gemm_digits");
 }
 
-}  // namespace
+template <bool WORDS>
+ne_status dispatch(const GemmArgs& a, cudaStream_t s) {
+    switch (a.M) {
+        case 3: return launch<3, WORDS>(a, s);
+        case 4: return launch<4, WORDS>(a, s);
+        case 5: return launch<5, WORDS>(a, s);
+        default: return launch<0, WORDS>(a, s);
+    }
+}
 
-extern "C" ne_status ne_gemm_digits(ne_params p, ne_digits dg, const int8_t* planes, const int8_t* G, int64_t* out,
-                                    uint32_t* flags, uint64_t* nflag, int32_t rows, int32_t cols, int32_t k,
-                                    int32_t fuse, int32_t r, cudaStream_t s) {
+
+// The tensor-path product from digit planes (planes non-null) or from the
+// entangled words themselves (words non-null, split in the loader).
+ne_status gemm_tensor(const char* who, ne_params p, ne_digits dg, const int8_t* planes, const int64_t* words,
+                      const int8_t* G, int64_t* out, uint32_t* flags, uint64_t* nflag, int32_t rows, int32_t cols,
+                      int32_t k, int32_t fuse, int32_t r, const ne_faults& faults, int32_t* status, cudaStream_t s) {
     ne_status st = validate_params(p);
     if (st) return st;
     if ((st = validate_digits(dg))) return st;
-    if (rows < 0 || cols < 0 || k < 0) return fail(NE_EINVAL, "ne_gemm_digits: negative size");
-    if (k % 16 != 0 || k > KMAX) return fail(NE_EINVAL, "ne_gemm_digits: k=%d must be a multiple of 16, <= %d", k, KMAX);
-    if (cols % 8 != 0) return fail(NE_EINVAL, "ne_gemm_digits: cols=%d must be a multiple of 8", cols);
-    if (fuse < NE_FUSE_NONE || fuse > NE_FUSE_RECOVER) return fail(NE_EINVAL, "ne_gemm_digits: fuse=%d", fuse);
-    if (r < 0 || r >= p.M) return fail(NE_EINVAL, "ne_gemm_digits: r=%d", r);
+    if ((st = validate_faults(faults, who))) return st;
+    if (rows < 0 || cols < 0 || k < 0) return fail(NE_EINVAL, "%s: negative size", who);
+    if (k % 16 != 0 || k > KMAX) return fail(NE_EINVAL, "%s: k=%d must be a multiple of 16, <= %d", who, k, KMAX);
+    if (cols % 8 != 0) return fail(NE_EINVAL, "%s: cols=%d must be a multiple of 8", who, cols);
+    if (fuse < NE_FUSE_NONE || fuse > NE_FUSE_RECOVER) return fail(NE_EINVAL, "%s: fuse=%d", who, fuse);
+    if (r < 0 || r >= p.M) return fail(NE_EINVAL, "%s: r=%d", who, r);
     const int MS = p.M * dg.S;
-    if (MS > 16) return fail(NE_EINVAL, "ne_gemm_digits: M*S=%d exceeds 16 planes", MS);
-    if ((int64_t)(rows + BM - 1) / BM > 65535) return fail(NE_EINVAL, "ne_gemm_digits: rows too large");
+    if (MS > 16) return fail(NE_EINVAL, "%s: M*S=%d exceeds 16 planes", who, MS);
+    if ((int64_t)(rows + BM - 1) / BM > 65535) return fail(NE_EINVAL, "%s: rows too large", who);
     unsigned long long* nf = reinterpret_cast<unsigned long long*>(nflag);
-    if (nf && cudaMemsetAsync(nf, 0, sizeof(*nf), s) != cudaSuccess) return check_launch("ne_gemm_digits: reset");
+    if (nf && cudaMemsetAsync(nf, 0, sizeof(*nf), s) != cudaSuccess)
+        return check_launch("digit-plane product: reset count");
     if (rows == 0 || cols == 0) return NE_OK;
-    if (!planes || !G || !out) return fail(NE_EINVAL, "ne_gemm_digits: null pointer");
-    if (!aligned(planes, 16) || !aligned(G, 4) || !aligned(out, 8))
-        return fail(NE_EINVAL, "ne_gemm_digits: planes 16-byte and G 4-byte alignment required");
+    if ((!planes && !words) || !G || !out) return fail(NE_EINVAL, "%s: null pointer", who);
+    if (!aligned(planes ? (const void*)planes : (const void*)words, 16) || !aligned(G, 4) || !aligned(out, 8))
+        return fail(NE_EINVAL, "%s: the streams must be 16-byte and G 4-byte aligned", who);
     GemmArgs a;
     a.planes = planes;
     a.G = G;
@@ -322,25 +400,40 @@ extern "C" ne_status ne_gemm_digits(ne_params p, ne_digits dg, const int8_t* pla
     a.direct_flags = (cols % 32 == 0);
     a.flags = (fuse == NE_FUSE_EXTRACT_CHECK) ? flags : nullptr;
     a.nflag = (fuse == NE_FUSE_EXTRACT_CHECK) ? nf : nullptr;
-    for (int i = 0; i < NE_MAX_DIGITS; i++) a.shift[i] = i < dg.S ? dg.shift[i] : 0;
+    uint64_t stored = 0;
+    for (int i = 0; i < NE_MAX_DIGITS; i++) {
+        a.shift[i] = i < dg.S ? dg.shift[i] : 0;
+        if (i < dg.S) stored |= 0xffull << dg.shift[i];
+    }
+    a.faults = faults;
+    a.words = words;
+    a.status = status;
+    a.ns_mask = ~stored;
+    a.ns_want = 0x8080808080808080ull & ~stored;
     if (a.flags && !a.direct_flags) {
-        const size_t words = ((size_t)rows * cols + 31) / 32;
-        if (cudaMemsetAsync(a.flags, 0, words * 4, s) != cudaSuccess) return check_launch("ne_gemm_digits: flags");
+        const size_t nw = ((size_t)rows * cols + 31) / 32;
+        if (cudaMemsetAsync(a.flags, 0, nw * 4, s) != cudaSuccess) return check_launch("digit-plane product: flags");
     }
-    if (k == 0) {
-        // empty inner dimension: every product is 0, so every output is 0
-        for (int m = 0; m < p.M; m++)
-            if (cudaMemsetAsync(out + (int64_t)m * rows * cols, 0, (size_t)rows * cols * 8, s) != cudaSuccess)
-                return check_launch("ne_gemm_digits: zero fill");
-        if (a.flags && a.direct_flags &&
-            cudaMemsetAsync(a.flags, 0, ((size_t)rows * cols / 32) * 4, s) != cudaSuccess)
-            return check_launch("ne_gemm_digits: flags");
-        return NE_OK;
-    }
-    switch (p.M) {
-        case 3: return launch<3>(a, s);
-        case 4: return launch<4>(a, s);
-        case 5: return launch<5>(a, s);
-        default: return launch<0>(a, s);
-    }
+    // k = 0 needs no special case: the tile loop is empty, every product is 0
+    return words ? dispatch<true>(a, s) : dispatch<false>(a, s);
+}
+
+}  // namespace
+
+namespace ne {
+
+ne_status gemm_s8slice(ne_params p, ne_digits dg, const int64_t* words, const int8_t* G, int64_t* out,
+                       uint32_t* flags, uint64_t* nflag, int32_t rows, int32_t cols, int32_t k, int32_t fuse,
+                       int32_t r, const ne_faults& faults, int32_t* status, cudaStream_t s) {
+    return gemm_tensor("ne_gemm (S8SLICE)", p, dg, nullptr, words, G, out, flags, nflag, rows, cols, k, fuse, r,
+                       faults, status, s);
+}
+
+}  // namespace ne
+
+extern "C" ne_status ne_gemm_digits(ne_params p, ne_digits dg, const int8_t* planes, const int8_t* G, int64_t* out,
+                                    uint32_t* flags, uint64_t* nflag, int32_t rows, int32_t cols, int32_t k,
+                                    int32_t fuse, int32_t r, ne_faults faults, cudaStream_t s) {
+    return gemm_tensor("ne_gemm_digits", p, dg, planes, nullptr, G, out, flags, nflag, rows, cols, k, fuse, r, faults,
+                       nullptr, s);
 }

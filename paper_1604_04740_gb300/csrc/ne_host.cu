@@ -60,6 +60,12 @@ ne_status validate_digits(const ne_digits& dg) {
     return NE_OK;
 }
 
+ne_status validate_faults(const ne_faults& f, const char* who) {
+    if (f.count < 0) return fail(NE_EINVAL, "%s: fault count %lld < 0", who, (long long)f.count);
+    if (f.count > 0 && (!f.pos || !f.stream || !f.bit)) return fail(NE_EINVAL, "%s: null fault list", who);
+    return NE_OK;
+}
+
 }  // namespace ne
 
 using namespace ne;

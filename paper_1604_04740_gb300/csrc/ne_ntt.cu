@@ -36,6 +36,7 @@
 #include "ne_common.cuh"
 #include "ne_entangle.cuh"
 #include "ne_extract.cuh"
+#include "ne_faults.cuh"
 
 namespace {
 
@@ -238,6 +239,7 @@ struct NttArgs {
     int64_t batch;
     int M, S, MS, l, r, fuse, plain;
     int shift[NE_MAX_DIGITS];
+    ne_faults faults;           // flat positions b * N + i (count 0: none)
     // generic digit split: bytes of a 64-bit word that hold no stored digit, and 0x80 in each
     uint64_t ns_mask, ns_want;
     // fast digit split (words of in-range inputs fit 32 bits): the input range
@@ -253,9 +255,11 @@ constexpr size_t ntt_smem_bytes(int MS) {
 // Digit s of the 32 words of this lane (positions 32 n1 + lane) as residues
 // below 2P: FAST forms the words in 32 bits and checks the inputs against the
 // plan's range; otherwise every 64-bit word is checked digit by digit.
+// check_prev: cp is the input of a lost stream (never loaded as cm itself),
+// so its range is checked here.
 template <bool FAST>
 __device__ __forceinline__ bool load_digits(const NttArgs& a, const int32_t* cm, const int32_t* cp, int sh,
-                                            uint32_t (&v)[32]) {
+                                            bool check_prev, uint32_t (&v)[32]) {
     using namespace ntt;
     if constexpr (FAST) {
         uint32_t worst = 0;
@@ -266,7 +270,11 @@ __device__ __forceinline__ bool load_digits(const NttArgs& a, const int32_t* cm,
             const int32_t x = __ldg(cm + 32 * n1);
             worst = max(worst, (uint32_t)x - (uint32_t)a.lo);
             uint32_t y = (uint32_t)x + a.off32;
-            if (!a.plain) y += (uint32_t)__ldg(cp + 32 * n1) << a.l;
+            if (!a.plain) {
+                const int32_t xp = __ldg(cp + 32 * n1);
+                if (check_prev) worst = max(worst, (uint32_t)xp - (uint32_t)a.lo);
+                y += (uint32_t)xp << a.l;
+            }
             const int d = (int32_t)((y ^ 0x80808080u) << up) >> 24;
             v[n1] = (uint32_t)(d + (int)P);
         }
@@ -319,7 +327,7 @@ __global__ void __launch_bounds__(448, 2) k_cconv_ntt(const NttArgs a) {
             } else {
                 // Eq. 16 for the 32 positions of this lane, digit s of the plan
                 const bool bad = load_digits<FAST>(a, a.c + (b * Mv + m) * N + lane, a.c + (b * Mv + mp) * N + lane,
-                                                   a.shift[s], v);
+                                                   a.shift[s], a.fuse == NE_FUSE_RECOVER && mp == a.r, v);
                 if (bad && a.status) atomicExch(a.status, (int32_t)NE_ERANGE);
             }
             forward(v, buf, tw, lane);
@@ -354,6 +362,12 @@ __global__ void __launch_bounds__(448, 2) k_cconv_ntt(const NttArgs a) {
         // int8-valued streams, with every shift a constant)
         const int32_t* resall = reinterpret_cast<const int32_t*>(bufs);
         const bool l16 = a.l == 16 && a.S == 2 && a.shift[0] == 0 && a.shift[1] == 16;
+        const ne_faults& F = a.faults;
+        int64_t f0 = 0, f1 = 0;                 // this group's faults
+        if (F.count > 0) {
+            f0 = fault_lower_bound(F.pos, 0, F.count, b * N);
+            f1 = fault_lower_bound(F.pos, f0, F.count, (b + 1) * N);
+        }
         for (int base = warp * 32; base < N; base += blockDim.x) {
             const int i = base + lane;
             int64_t rot[MR];
@@ -371,6 +385,7 @@ __global__ void __launch_bounds__(448, 2) k_cconv_ntt(const NttArgs a) {
                         for (int ss = 0; ss < a.S; ss++)
                             w += (uint64_t)(int64_t)resall[(mm * a.S + ss) * BUF + i] << a.shift[ss];
                     }
+                    if (f1 > f0) w = (uint64_t)apply_faults((int64_t)w, F.pos, F.stream, F.bit, f0, f1, b * N + i, mm);
                 }
                 rot[j] = (int64_t)w;
             }
@@ -430,10 +445,11 @@ ne_status launch_ntt(const NttArgs& a, bool fast, cudaStream_t s) {
 
 extern "C" ne_status ne_cconv_ntt(ne_params p, ne_digits dg, const int32_t* c, const int8_t* g, int64_t* out,
                                   uint32_t* flags, uint64_t* nflag, int64_t batch, int64_t N, int32_t fuse,
-                                  int32_t r, int32_t plain, int32_t* status, cudaStream_t s) {
+                                  int32_t r, int32_t plain, ne_faults faults, int32_t* status, cudaStream_t s) {
     ne_status st = validate_params(p);
     if (st) return st;
     if ((st = validate_digits(dg))) return st;
+    if ((st = validate_faults(faults, "ne_cconv_ntt"))) return st;
     if (batch < 0) return fail(NE_EINVAL, "ne_cconv_ntt: batch < 0");
     if (N != ntt::N) return fail(NE_EINVAL, "ne_cconv_ntt: N=%lld; the transform length is %d", (long long)N, ntt::N);
     if (fuse < NE_FUSE_NONE || fuse > NE_FUSE_RECOVER) return fail(NE_EINVAL, "ne_cconv_ntt: fuse=%d", fuse);
@@ -462,6 +478,7 @@ extern "C" ne_status ne_cconv_ntt(ne_params p, ne_digits dg, const int32_t* c, c
     a.r = fuse == NE_FUSE_NONE ? 0 : r;
     a.fuse = fuse;
     a.plain = plain ? 1 : 0;
+    a.faults = faults;
     uint64_t stored = 0;
     for (int i = 0; i < NE_MAX_DIGITS; i++) {
         a.shift[i] = i < dg.S ? dg.shift[i] : 0;

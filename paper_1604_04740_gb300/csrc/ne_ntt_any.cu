@@ -33,6 +33,7 @@
 #include "ne_common.cuh"
 #include "ne_entangle.cuh"
 #include "ne_extract.cuh"
+#include "ne_faults.cuh"
 #include "ne_ntt_any.cuh"
 
 namespace ne {
@@ -155,6 +156,7 @@ __device__ __forceinline__ NJob job_of(const NJobs& J, int64_t b) {
     j.out_off += b * J.out_stride;
     j.flag_off += b * J.flag_stride;
     j.ws_off += b * J.ws_stride;
+    j.fault_key0 += b * J.fault_key_stride;
     return j;
 }
 
@@ -196,7 +198,10 @@ __device__ __forceinline__ void load_residues(const NttAnyArgs& a, const NJob& j
         int64_t e = x;
         if (!j.plain) {
             const int mp = p == 0 ? j.M - 1 : p - 1;
-            e = entangle_word(x, __ldg(a.c + j.c_off + (int64_t)mp * j.N + i), j.l);
+            const int32_t xp = __ldg(a.c + j.c_off + (int64_t)mp * j.N + i);
+            // a lost stream is never loaded itself, but its inputs enter this word
+            if (j.fuse == NE_FUSE_RECOVER && mp == j.r) worst = max(worst, (uint32_t)xp - (uint32_t)j.lo);
+            e = entangle_word(x, xp, j.l);
         }
         // |e| < 2^41: shift into [0, 2^42) by a multiple of both primes, then reduce
         r0 = (uint32_t)((uint64_t)(e + (int64_t)prime(0) * (int64_t)(1 << 22)) % prime(0));
@@ -541,17 +546,6 @@ __global__ void __launch_bounds__(BTHREADS) k_block(const NttAnyArgs a) {
     }
 }
 
-// first index f in [0, n) with pos[f] >= key (pos sorted ascending)
-__device__ __forceinline__ int64_t fault_lower_bound(const int64_t* pos, int64_t n, int64_t key) {
-    int64_t lo = 0, hi = n;
-    while (lo < hi) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (pos[mid] < key) lo = mid + 1;
-        else hi = mid;
-    }
-    return lo;
-}
-
 // fold, CRT, extraction / check / faults of one job, 32 positions per warp
 template <int MT>
 __device__ __forceinline__ void final_job(const NttAnyArgs& a, const NJob& j) {
@@ -569,8 +563,8 @@ __device__ __forceinline__ void final_job(const NttAnyArgs& a, const NJob& j) {
             const bool valid = n < j.N;
             int64_t f0 = 0, f1 = 0;                                   // this warp's faults
             if (a.fault_pos && j.fault_end > j.fault_begin) {
-                f0 = j.fault_begin + fault_lower_bound(a.fault_pos + j.fault_begin, j.fault_end - j.fault_begin, base);
-                f1 = j.fault_begin + fault_lower_bound(a.fault_pos + j.fault_begin, j.fault_end - j.fault_begin, base + 32);
+                f0 = fault_lower_bound(a.fault_pos, j.fault_begin, j.fault_end, j.fault_key0 + base);
+                f1 = fault_lower_bound(a.fault_pos, f0, j.fault_end, j.fault_key0 + base + 32);
             }
             int64_t rot[MR];
 #pragma unroll
@@ -595,8 +589,8 @@ __device__ __forceinline__ void final_job(const NttAnyArgs& a, const NJob& j) {
                     const uint32_t t = red1(mul_shoup(d, inv, invq, P2), P2);
                     uint64_t y = (uint64_t)x[0] + (uint64_t)P1 * t;
                     v = y > PP / 2 ? (int64_t)(y - PP) : (int64_t)y;
-                    for (int64_t f = f0; f < f1; f++)                    // transient faults (batch)
-                        if (a.fault_pos[f] == n && a.fault_stream[f] == m) v ^= (int64_t)(1ull << a.fault_bit[f]);
+                    if (f1 > f0)                                          // transient faults
+                        v = apply_faults(v, a.fault_pos, a.fault_stream, a.fault_bit, f0, f1, j.fault_key0 + n, m);
                 }
                 rot[jj] = v;
             }
@@ -761,10 +755,11 @@ extern "C" int64_t ne_cconv_ntt_any_workspace(int32_t M, int64_t N, int64_t batc
 
 extern "C" ne_status ne_cconv_ntt_any(ne_params p, int32_t cmin, int32_t cmax, const int32_t* c, const int8_t* g,
                                       int64_t* out, uint32_t* flags, uint64_t* nflag, int64_t batch, int64_t N,
-                                      int32_t fuse, int32_t r, int32_t plain, int32_t* status, void* workspace,
-                                      int64_t workspace_bytes, cudaStream_t s) {
+                                      int32_t fuse, int32_t r, int32_t plain, ne_faults faults, int32_t* status,
+                                      void* workspace, int64_t workspace_bytes, cudaStream_t s) {
     ne_status st = validate_params(p);
     if (st) return st;
+    if ((st = validate_faults(faults, "ne_cconv_ntt_any"))) return st;
     if (batch < 0 || N < 2 || N > 65536) return fail(NE_EINVAL, "ne_cconv_ntt_any: N=%lld must be in [2, 65536]",
                                                      (long long)N);
     if (cmin > cmax) return fail(NE_EINVAL, "ne_cconv_ntt_any: empty input range");
@@ -797,7 +792,9 @@ extern "C" ne_status ne_cconv_ntt_any(ne_params p, int32_t cmin, int32_t cmax, c
     j.plain = plain ? 1 : 0;
     j.lo = cmin;
     j.hi = cmax;
-    j.fault_begin = j.fault_end = 0;
+    j.fault_begin = 0;
+    j.fault_end = faults.count;
+    j.fault_key0 = 0;
     ntt_any_job_constants(j);
     a.jobs.table = nullptr;
     a.jobs.njobs = batch;
@@ -806,6 +803,7 @@ extern "C" ne_status ne_cconv_ntt_any(ne_params p, int32_t cmin, int32_t cmax, c
     a.jobs.out_stride = (int64_t)p.M * N;
     a.jobs.flag_stride = (N + 31) / 32;
     a.jobs.ws_stride = (int64_t)(p.M + 1) * 2 * j.L;
+    a.jobs.fault_key_stride = N;
     a.c = c;
     a.g = g;
     a.out = out;
@@ -814,8 +812,8 @@ extern "C" ne_status ne_cconv_ntt_any(ne_params p, int32_t cmin, int32_t cmax, c
     a.flags_atomic = 0;
     a.status = status;
     a.ws = static_cast<uint32_t*>(workspace);
-    a.fault_pos = nullptr;
-    a.fault_stream = nullptr;
-    a.fault_bit = nullptr;
+    a.fault_pos = faults.count > 0 ? faults.pos : nullptr;
+    a.fault_stream = faults.stream;
+    a.fault_bit = faults.bit;
     return ntt_any_run(a, lg, lg, p.M, (int64_t)(p.M + 1) * j.L, s);
 }

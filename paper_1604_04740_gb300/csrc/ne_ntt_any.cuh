@@ -14,6 +14,7 @@ struct NJob {
     int64_t flag_off;            // uint32 word offset of the check bitmap
     int64_t ws_off;              // uint32 element offset of the workspace [M + 1][2][L]
     int64_t fault_begin, fault_end;   // the job's range in the (position-sorted) fault lists
+    int64_t fault_key0;          // the list's position of the job's output 0 (0 in a batch)
     int32_t M, N, L, logL, l, r, fuse, plain, lo, hi;
     uint32_t gscale[2];          // 2^64 / L mod each prime: the filter transform's Montgomery scale
 };
@@ -23,7 +24,7 @@ struct NJob {
 struct NJobs {
     const NJob* table;
     NJob tmpl;
-    int64_t c_stride, g_stride, out_stride, flag_stride, ws_stride;
+    int64_t c_stride, g_stride, out_stride, flag_stride, ws_stride, fault_key_stride;
     int64_t njobs;
 };
 
@@ -37,7 +38,7 @@ struct NttAnyArgs {
     int flags_atomic;            // bitmap pre-zeroed: OR the set bits in
     int32_t* status;
     uint32_t* ws;
-    const int64_t* fault_pos;    // batch fault hook (or null)
+    const int64_t* fault_pos;    // fault hook (or null)
     const int32_t* fault_stream;
     const int32_t* fault_bit;
     uint32_t crt_inv, crt_invq;  // P1^-1 mod P2 and its Shoup quotient (set by ntt_any_run)

@@ -151,11 +151,13 @@ __global__ void __launch_bounds__(CT) k_cconv_i64(const int64_t* __restrict__ x,
 
 }  // namespace
 
-extern "C" ne_status ne_gemm(int32_t P, const int64_t* x, const int8_t* G, int64_t* out, int32_t rows, int32_t cols,
-                             int32_t k, uint32_t skip_mask, cudaStream_t s) {
-    if (P < 1 || P > 32 || rows < 0 || cols < 0 || k < 0) return fail(NE_EINVAL, "ne_gemm: bad sizes");
+namespace ne {
+
+// The plain launches of the two kernels (argument checks are the caller's):
+// planes whose bit is set in skip_mask are not computed and not written.
+ne_status gemm_i64_launch(int32_t P, const int64_t* x, const int8_t* G, int64_t* out, int32_t rows, int32_t cols,
+                          int32_t k, uint32_t skip_mask, cudaStream_t s) {
     if (rows == 0 || cols == 0) return NE_OK;
-    if (!x || !G || !out) return fail(NE_EINVAL, "ne_gemm: null pointer");
     if (k == 0) {
         for (int p = 0; p < P; p++)
             if (!(skip_mask & (1u << p)) &&
@@ -169,11 +171,9 @@ extern "C" ne_status ne_gemm(int32_t P, const int64_t* x, const int8_t* G, int64
     return check_launch("ne_gemm");
 }
 
-extern "C" ne_status ne_cconv(int32_t P, const int64_t* x, const int8_t* g, int64_t* out, int64_t batch, int64_t N,
-                              uint32_t skip_mask, cudaStream_t s) {
-    if (P < 1 || P > 32 || batch < 0 || N < 0) return fail(NE_EINVAL, "ne_cconv: bad sizes");
+ne_status cconv_i64_launch(int32_t P, const int64_t* x, const int8_t* g, int64_t* out, int64_t batch, int64_t N,
+                           uint32_t skip_mask, cudaStream_t s) {
     if (batch == 0 || N == 0) return NE_OK;
-    if (!x || !g || !out) return fail(NE_EINVAL, "ne_cconv: null pointer");
     if ((N + CI - 1) / CI > 2147483647LL) return fail(NE_EINVAL, "ne_cconv: N too large");
     for (int64_t b0 = 0; b0 < batch; b0 += 65535) {
         int64_t nb = batch - b0 < 65535 ? batch - b0 : 65535;
@@ -184,3 +184,5 @@ extern "C" ne_status ne_cconv(int32_t P, const int64_t* x, const int8_t* g, int6
     }
     return NE_OK;
 }
+
+}  // namespace ne

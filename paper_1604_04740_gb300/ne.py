@@ -18,6 +18,7 @@ from . import build as _build
 NE_OK, NE_EINVAL, NE_ERANGE, NE_ECUDA, NE_ETIMEOUT, NE_ENOMEM = range(6)
 NE_L_PAPER, NE_L_SMALLEST, NE_L_BYTE = 0, 1, 2
 NE_FUSE_NONE, NE_FUSE_EXTRACT_CHECK, NE_FUSE_RECOVER = 0, 1, 2
+NE_MODE_I64, NE_MODE_S8SLICE = 0, 1
 NE_MAX_DIGITS = 8
 
 
@@ -41,6 +42,39 @@ class ne_digits(ctypes.Structure):
 
     def __repr__(self):
         return f"ne_digits(S={self.S}, shift={self.shifts})"
+
+
+class ne_faults(ctypes.Structure):
+    _fields_ = [("pos", ctypes.c_void_p), ("stream", ctypes.c_void_p), ("bit", ctypes.c_void_p),
+                ("count", ctypes.c_int64)]
+
+
+def faults(pos: torch.Tensor | None = None, stream: torch.Tensor | None = None,
+           bit: torch.Tensor | None = None) -> ne_faults:
+    """The ne_faults of three device tensors (pos int64, stream int32, bit
+    int32, equal lengths; pos ascending).  No arguments: no faults.  The
+    caller keeps the tensors alive until the call that uses them has run."""
+    f = ne_faults()
+    if pos is None:
+        if stream is not None or bit is not None:
+            raise ValueError("fault lists need pos, stream and bit together")
+        return f
+    n = pos.numel()
+    if stream.numel() != n or bit.numel() != n:
+        raise ValueError("fault lists differ in length")
+    f.pos = _ptr(pos, torch.int64, "fault pos")
+    f.stream = _ptr(stream, torch.int32, "fault stream")
+    f.bit = _ptr(bit, torch.int32, "fault bit")
+    f.count = n
+    return f
+
+
+def _faults_arg(fl) -> ne_faults:
+    if fl is None:
+        return ne_faults()
+    if isinstance(fl, ne_faults):
+        return fl
+    return faults(*fl)
 
 
 NE_JOB_GEMM, NE_JOB_CCONV = 0, 1
@@ -97,31 +131,30 @@ def _load():
         "ne_plan_digits": [i32, i32, i32, ctypes.POINTER(ne_digits)],
         "ne_entangle": [ne_params, P, P, i64, i64, P],
         "ne_entangle_digits": [ne_params, ne_digits, P, P, i64, i64, P, P],
-        "ne_gemm": [i32, P, P, P, i32, i32, i32, u32, P],
-        "ne_gemm_digits": [ne_params, ne_digits, P, P, P, P, P, i32, i32, i32, i32, i32, P],
-        "ne_cconv": [i32, P, P, P, i64, i64, u32, P],
-        "ne_cconv_digits": [ne_params, ne_digits, P, P, P, P, P, i64, i64, i32, i32, P],
+        "ne_gemm": [ne_params, P, P, P, P, P, i32, i32, i32, i32, ne_digits, i32, i32, u32, ne_faults, P, P],
+        "ne_gemm_digits": [ne_params, ne_digits, P, P, P, P, P, i32, i32, i32, i32, i32, ne_faults, P],
+        "ne_cconv": [ne_params, P, P, P, P, P, i64, i64, i32, ne_digits, i32, i32, u32, ne_faults, P, P],
+        "ne_cconv_digits": [ne_params, ne_digits, P, P, P, P, P, i64, i64, i32, i32, ne_faults, P],
         "ne_extract": [ne_params, P, P, i64, i64, i32, P, P, P],
         "ne_check": [ne_params, P, i64, i64, i32, P, P, P, P],
         "ne_recover": [ne_params, P, P, i64, i64, i32, P],
+        "ne_check_set_wait_limit": [u32],
         "ne_inject": [P, i32, i64, i64, P, P, P, P, i64, P, P],
         "ne_abft_encode": [i32, P, P, i64, i64, P],
         "ne_abft_check": [i32, P, i64, i64, P, P, P],
         "ne_abft_recover": [i32, P, i64, i64, i32, P],
         "ne_split_digits": [ne_digits, P, P, i64, i32, i64, P, P],
-        "ne_probe_mma_peak": [i32, ctypes.POINTER(i64), P],
-        "ne_probe_dp4a_peak": [i32, ctypes.POINTER(i64), P],
-        "ne_probe_imad_peak": [i32, ctypes.POINTER(i64), P],
-        "ne_probe_mixed_peak": [i32, i32, i32, i32, i32, ctypes.POINTER(i64), P],
+        "ne_split_digits_raw": [ne_params, ne_digits, P, P, i64, i64, P, P],
         "ne_batch_plan": [ctypes.POINTER(ne_job), i32, ne_batch_config, P, i64, ctypes.POINTER(ne_batch_info), P],
         "ne_batch_plan_staged": [ctypes.POINTER(ne_job), i32, ne_batch_config, P, i64, P, i64,
                                  ctypes.POINTER(ne_batch_info), P],
         "ne_batch_run": [ne_batch_info, P, P, P, P, P, P, P, P, P, P, P],
         "ne_batch_run_static": [ctypes.POINTER(ne_job), i32, ne_batch_config, P, P, P, P, P, P, P, P, P, P],
         "ne_copy_regions_h2d": [P, P, P, P, P, i64, P],
-        "ne_cconv_entangled": [ne_params, ne_digits, P, P, P, P, P, i64, i64, i32, i32, i32, P, P],
-        "ne_cconv_ntt_any": [ne_params, i32, i32, P, P, P, P, P, i64, i64, i32, i32, i32, P, P, i64, P],
-        "ne_cconv_ntt": [ne_params, ne_digits, P, P, P, P, P, i64, i64, i32, i32, i32, P, P],
+        "ne_cconv_entangled": [ne_params, ne_digits, P, P, P, P, P, i64, i64, i32, i32, i32, ne_faults, P, P],
+        "ne_set_cconv_split": [i32],
+        "ne_cconv_ntt_any": [ne_params, i32, i32, P, P, P, P, P, i64, i64, i32, i32, i32, ne_faults, P, P, i64, P],
+        "ne_cconv_ntt": [ne_params, ne_digits, P, P, P, P, P, i64, i64, i32, i32, i32, ne_faults, P, P],
         "ne_abft_rc_encode": [P, P, P, P, i64, i64, i64, i64, P],
         "ne_abft_rc_check": [P, P, P, P, P, P, P, P, P, i64, i64, i64, i64, P],
         "ne_abft_rc_correct": [P, P, P, P, P, i64, i64, i64, P],
@@ -226,6 +259,21 @@ def ne_entangle_digits(p: ne_params, dg: ne_digits, c: torch.Tensor, planes: tor
     return planes
 
 
+def ne_split_digits_raw(p: ne_params, dg: ne_digits, c: torch.Tensor, planes: torch.Tensor | None = None,
+                        status: torch.Tensor | None = None) -> torch.Tensor:
+    """The raw streams c int32 [..., M, n] as digit planes int8 [..., M, S, n]
+    with an entangled plan's digit set (the plain operation's operand)."""
+    batch, n = _bmn(c, p.M)
+    shape = tuple(c.shape[:-1]) + (dg.S, n)
+    if planes is None:
+        planes = torch.empty(shape, dtype=torch.int8, device=c.device)
+    if tuple(planes.shape) != shape:
+        raise ValueError(f"planes must be {shape}")
+    _call("ne_split_digits_raw", p, dg, _ptr(c, torch.int32, "c"), _ptr(planes, torch.int8, "planes"), batch, n,
+          _ptr(status, torch.int32, "status", True), _stream())
+    return planes
+
+
 def ne_split_digits(dg: ne_digits, x: torch.Tensor, P: int, planes: torch.Tensor | None = None,
                     status: torch.Tensor | None = None) -> torch.Tensor:
     """x int64 [..., P, n] -> planes int8 [..., P, S, n]."""
@@ -240,58 +288,40 @@ def ne_split_digits(dg: ne_digits, x: torch.Tensor, P: int, planes: torch.Tensor
     return planes
 
 
-def ne_probe_dp4a_peak(iters: int) -> int:
-    """The dp4a counterpart of ne_probe_mma_peak."""
-    ops = ctypes.c_int64()
-    _call("ne_probe_dp4a_peak", iters, ctypes.byref(ops), _stream())
-    return ops.value
-
-
-def ne_probe_mixed_peak(iters_mma: int, iters_dp4a: int, mma_warps: int, dp4a_warps: int,
-                        blocks_per_sm: int) -> int:
-    """Both int8 pipes in one launch (see ne_probe_mma_peak); returns the int8 operations issued."""
-    ops = ctypes.c_int64(0)
-    _call("ne_probe_mixed_peak", iters_mma, iters_dp4a, mma_warps, dp4a_warps, blocks_per_sm,
-          ctypes.byref(ops), _stream())
-    return ops.value
-
-
-def ne_probe_imad_peak(iters: int) -> int:
-    """32-bit IMAD throughput probe; returns the multiply-adds issued."""
-    ops = ctypes.c_int64(0)
-    _call("ne_probe_imad_peak", iters, ctypes.byref(ops), _stream())
-    return ops.value
-
-
-def ne_probe_mma_peak(iters: int) -> int:
-    """Launch the int8 tensor-path throughput probe on the current stream;
-    returns the number of int8 operations it issues (time it with events)."""
-    ops = ctypes.c_int64()
-    _call("ne_probe_mma_peak", iters, ctypes.byref(ops), _stream())
-    return ops.value
-
-
 # ---- operations ----------------------------------------------------------------
 
-def ne_gemm(x: torch.Tensor, G: torch.Tensor, out: torch.Tensor | None = None, skip_mask: int = 0) -> torch.Tensor:
-    """x int64 [P, rows, k] @ G int8 [k, cols] -> int64 [P, rows, cols]."""
-    P, rows, k = x.shape
+def ne_gemm(p: ne_params, eps: torch.Tensor, G: torch.Tensor, out: torch.Tensor | None = None,
+            flags: torch.Tensor | None = None, nflag: torch.Tensor | None = None, mode: int = NE_MODE_I64,
+            dg: ne_digits | None = None, fuse: int = NE_FUSE_EXTRACT_CHECK, r: int = 0, drop_mask: int = 0,
+            faults=None, status: torch.Tensor | None = None) -> torch.Tensor:
+    """eps int64 [M, rows, k] @ G int8 [k, cols] -> int64 [M, rows, cols]: delta
+    (NE_FUSE_NONE) or d_hat.  mode NE_MODE_I64 (CUDA cores) or NE_MODE_S8SLICE
+    (int8 tensor path, the words split into the digits of dg in the kernel).
+    faults: None, an ne_faults or (pos, stream, bit) device tensors."""
+    M, rows, k = eps.shape
+    if M != p.M:
+        raise ValueError("eps must be [M, rows, k]")
     k2, cols = G.shape
     if k != k2:
         raise ValueError("inner dimensions differ")
     if out is None:
-        out = torch.empty((P, rows, cols), dtype=torch.int64, device=x.device)
-    if tuple(out.shape) != (P, rows, cols):
+        out = torch.empty((M, rows, cols), dtype=torch.int64, device=eps.device)
+    if tuple(out.shape) != (M, rows, cols):
         raise ValueError("out shape")
-    _call("ne_gemm", P, _ptr(x, torch.int64, "x"), _ptr(G, torch.int8, "G"), _ptr(out, torch.int64, "out"),
-          rows, cols, k, skip_mask, _stream())
+    _call("ne_gemm", p, _ptr(eps, torch.int64, "eps"), _ptr(G, torch.int8, "G"), _ptr(out, torch.int64, "out"),
+          _ptr(flags, torch.int32, "flags", True), _ptr(nflag, torch.int64, "nflag", True), rows, cols, k, mode,
+          dg if dg is not None else ne_digits(), fuse, r, drop_mask, _faults_arg(faults),
+          _ptr(status, torch.int32, "status", True), _stream())
     return out
 
 
 def ne_gemm_digits(p: ne_params, dg: ne_digits, planes: torch.Tensor, G: torch.Tensor,
                    out: torch.Tensor | None = None, flags: torch.Tensor | None = None,
-                   nflag: torch.Tensor | None = None, fuse: int = NE_FUSE_EXTRACT_CHECK, r: int = 0) -> torch.Tensor:
-    """planes int8 [M, S, rows, k]; G int8 [k, cols] -> int64 [M, rows, cols]."""
+                   nflag: torch.Tensor | None = None, fuse: int = NE_FUSE_EXTRACT_CHECK, r: int = 0,
+                   faults=None) -> torch.Tensor:
+    """planes int8 [M, S, rows, k]; G int8 [k, cols] -> int64 [M, rows, cols].
+    faults: None, an ne_faults, or (pos, stream, bit) device tensors
+    (positions i * cols + j, ascending)."""
     M, S, rows, k = planes.shape
     if M != p.M or S != dg.S:
         raise ValueError("planes shape does not match (M, S)")
@@ -302,26 +332,40 @@ def ne_gemm_digits(p: ne_params, dg: ne_digits, planes: torch.Tensor, G: torch.T
         out = torch.empty((M, rows, cols), dtype=torch.int64, device=planes.device)
     _call("ne_gemm_digits", p, dg, _ptr(planes, torch.int8, "planes"), _ptr(G, torch.int8, "G"),
           _ptr(out, torch.int64, "out"), _ptr(flags, torch.int32, "flags", True),
-          _ptr(nflag, torch.int64, "nflag", True), rows, cols, k, fuse, r, _stream())
+          _ptr(nflag, torch.int64, "nflag", True), rows, cols, k, fuse, r, _faults_arg(faults), _stream())
     return out
 
 
-def ne_cconv(x: torch.Tensor, g: torch.Tensor, out: torch.Tensor | None = None, skip_mask: int = 0) -> torch.Tensor:
-    """x int64 [batch, P, N], g int8 [batch, N] -> int64 [batch, P, N]."""
-    batch, P, N = x.shape
-    if tuple(g.shape) != (batch, N):
-        raise ValueError("g must be [batch, N]")
+def ne_cconv(p: ne_params, eps: torch.Tensor, g: torch.Tensor, out: torch.Tensor | None = None,
+             flags: torch.Tensor | None = None, nflag: torch.Tensor | None = None, mode: int = NE_MODE_I64,
+             dg: ne_digits | None = None, fuse: int = NE_FUSE_EXTRACT_CHECK, r: int = 0, drop_mask: int = 0,
+             faults=None, status: torch.Tensor | None = None) -> torch.Tensor:
+    """eps int64 [batch, M, N], g int8 [batch, N] -> int64 [batch, M, N]:
+    delta (NE_FUSE_NONE) or d_hat; modes and faults as for ne_gemm."""
+    batch, M, N = eps.shape
+    if M != p.M or tuple(g.shape) != (batch, N):
+        raise ValueError("eps must be [batch, M, N] and g [batch, N]")
     if out is None:
-        out = torch.empty_like(x)
-    _call("ne_cconv", P, _ptr(x, torch.int64, "x"), _ptr(g, torch.int8, "g"), _ptr(out, torch.int64, "out"),
-          batch, N, skip_mask, _stream())
+        out = torch.empty_like(eps)
+    _call("ne_cconv", p, _ptr(eps, torch.int64, "eps"), _ptr(g, torch.int8, "g"), _ptr(out, torch.int64, "out"),
+          _ptr(flags, torch.int32, "flags", True), _ptr(nflag, torch.int64, "nflag", True), batch, N, mode,
+          dg if dg is not None else ne_digits(), fuse, r, drop_mask, _faults_arg(faults),
+          _ptr(status, torch.int32, "status", True), _stream())
     return out
+
+
+def planes_of(M: int) -> ne_params:
+    """The parameters of the bare operation on M planes (NE_FUSE_NONE, NE_MODE_I64:
+    l is not used): the plain operation or the checksum comparator."""
+    return ne_params(M, 1, 64)
 
 
 def ne_cconv_digits(p: ne_params, dg: ne_digits, planes: torch.Tensor, g: torch.Tensor,
                     out: torch.Tensor | None = None, flags: torch.Tensor | None = None,
-                    nflag: torch.Tensor | None = None, fuse: int = NE_FUSE_EXTRACT_CHECK, r: int = 0) -> torch.Tensor:
-    """planes int8 [batch, M, S, N]; g int8 [batch, N] -> int64 [batch, M, N]."""
+                    nflag: torch.Tensor | None = None, fuse: int = NE_FUSE_EXTRACT_CHECK, r: int = 0,
+                    faults=None) -> torch.Tensor:
+    """planes int8 [batch, M, S, N]; g int8 [batch, N] -> int64 [batch, M, N].
+    faults as for ne_gemm_digits (positions group * N + i)."""
     batch, M, S, N = planes.shape
     if M != p.M or S != dg.S or tuple(g.shape) != (batch, N):
         raise ValueError("planes / g shapes")
@@ -329,15 +373,21 @@ def ne_cconv_digits(p: ne_params, dg: ne_digits, planes: torch.Tensor, g: torch.
         out = torch.empty((batch, M, N), dtype=torch.int64, device=planes.device)
     _call("ne_cconv_digits", p, dg, _ptr(planes, torch.int8, "planes"), _ptr(g, torch.int8, "g"),
           _ptr(out, torch.int64, "out"), _ptr(flags, torch.int32, "flags", True),
-          _ptr(nflag, torch.int64, "nflag", True), batch, N, fuse, r, _stream())
+          _ptr(nflag, torch.int64, "nflag", True), batch, N, fuse, r, _faults_arg(faults), _stream())
     return out
+
+
+def ne_set_cconv_split(variant: int = -1):
+    """The tensor / dp4a split of the convolution tile (-1: the default)."""
+    _call("ne_set_cconv_split", variant)
 
 
 def ne_cconv_entangled(p: ne_params, dg: ne_digits, c: torch.Tensor, g: torch.Tensor,
                        out: torch.Tensor | None = None, flags: torch.Tensor | None = None,
                        nflag: torch.Tensor | None = None, fuse: int = NE_FUSE_EXTRACT_CHECK, r: int = 0,
-                       plain: bool = False, status: torch.Tensor | None = None) -> torch.Tensor:
-    """c int32 [batch, M, N] (raw streams); g int8 [batch, N] -> int64 [batch, M, N] (tensor path, one launch)."""
+                       plain: bool = False, status: torch.Tensor | None = None, faults=None) -> torch.Tensor:
+    """c int32 [batch, M, N] (raw streams); g int8 [batch, N] -> int64 [batch, M, N] (tensor path, one launch).
+    faults as for ne_cconv_digits."""
     batch, M, N = c.shape
     if M != p.M or tuple(g.shape) != (batch, N):
         raise ValueError("c / g shapes")
@@ -345,7 +395,7 @@ def ne_cconv_entangled(p: ne_params, dg: ne_digits, c: torch.Tensor, g: torch.Te
         out = torch.empty((batch, M, N), dtype=torch.int64, device=c.device)
     _call("ne_cconv_entangled", p, dg, _ptr(c, torch.int32, "c"), _ptr(g, torch.int8, "g"),
           _ptr(out, torch.int64, "out"), _ptr(flags, torch.int32, "flags", True),
-          _ptr(nflag, torch.int64, "nflag", True), batch, N, fuse, r, 1 if plain else 0,
+          _ptr(nflag, torch.int64, "nflag", True), batch, N, fuse, r, 1 if plain else 0, _faults_arg(faults),
           _ptr(status, torch.int32, "status", True), _stream())
     return out
 
@@ -354,8 +404,9 @@ def ne_cconv_ntt_any(p: ne_params, c: torch.Tensor, g: torch.Tensor, out: torch.
                      flags: torch.Tensor | None = None, nflag: torch.Tensor | None = None,
                      fuse: int = NE_FUSE_EXTRACT_CHECK, r: int = 0, plain: bool = False,
                      status: torch.Tensor | None = None, cmin: int = -128, cmax: int = 127,
-                     workspace: torch.Tensor | None = None) -> torch.Tensor:
-    """c int32 [batch, M, N] (raw streams, any N in [2, 65536]); g int8 [batch, N] -> int64 [batch, M, N]."""
+                     workspace: torch.Tensor | None = None, faults=None) -> torch.Tensor:
+    """c int32 [batch, M, N] (raw streams, any N in [2, 65536]); g int8 [batch, N] -> int64 [batch, M, N].
+    faults as for ne_cconv_digits."""
     batch, M, N = c.shape
     if M != p.M or tuple(g.shape) != (batch, N):
         raise ValueError("c / g shapes")
@@ -366,7 +417,7 @@ def ne_cconv_ntt_any(p: ne_params, c: torch.Tensor, g: torch.Tensor, out: torch.
         out = torch.empty((batch, M, N), dtype=torch.int64, device=c.device)
     _call("ne_cconv_ntt_any", p, cmin, cmax, _ptr(c, torch.int32, "c"), _ptr(g, torch.int8, "g"),
           _ptr(out, torch.int64, "out"), _ptr(flags, torch.int32, "flags", True),
-          _ptr(nflag, torch.int64, "nflag", True), batch, N, fuse, r, 1 if plain else 0,
+          _ptr(nflag, torch.int64, "nflag", True), batch, N, fuse, r, 1 if plain else 0, _faults_arg(faults),
           _ptr(status, torch.int32, "status", True), _ptr(workspace, torch.uint8, "workspace"),
           workspace.numel(), _stream())
     return out
@@ -375,8 +426,9 @@ def ne_cconv_ntt_any(p: ne_params, c: torch.Tensor, g: torch.Tensor, out: torch.
 def ne_cconv_ntt(p: ne_params, dg: ne_digits, c: torch.Tensor, g: torch.Tensor, out: torch.Tensor | None = None,
                  flags: torch.Tensor | None = None, nflag: torch.Tensor | None = None,
                  fuse: int = NE_FUSE_EXTRACT_CHECK, r: int = 0, plain: bool = False,
-                 status: torch.Tensor | None = None) -> torch.Tensor:
-    """c int32 [batch, M, N] (raw streams); g int8 [batch, N] -> int64 [batch, M, N]."""
+                 status: torch.Tensor | None = None, faults=None) -> torch.Tensor:
+    """c int32 [batch, M, N] (raw streams); g int8 [batch, N] -> int64 [batch, M, N].
+    faults as for ne_cconv_digits."""
     batch, M, N = c.shape
     if M != p.M or tuple(g.shape) != (batch, N):
         raise ValueError("c / g shapes")
@@ -384,7 +436,7 @@ def ne_cconv_ntt(p: ne_params, dg: ne_digits, c: torch.Tensor, g: torch.Tensor, 
         out = torch.empty((batch, M, N), dtype=torch.int64, device=c.device)
     _call("ne_cconv_ntt", p, dg, _ptr(c, torch.int32, "c"), _ptr(g, torch.int8, "g"),
           _ptr(out, torch.int64, "out"), _ptr(flags, torch.int32, "flags", True),
-          _ptr(nflag, torch.int64, "nflag", True), batch, N, fuse, r, 1 if plain else 0,
+          _ptr(nflag, torch.int64, "nflag", True), batch, N, fuse, r, 1 if plain else 0, _faults_arg(faults),
           _ptr(status, torch.int32, "status", True), _stream())
     return out
 
@@ -556,6 +608,11 @@ def ne_check(p: ne_params, delta: torch.Tensor, r: int = 0, flags: torch.Tensor 
     _call("ne_check", p, _ptr(delta, torch.int64, "delta"), batch, n, r, _ptr(flags, torch.int32, "flags", True),
           _ptr(nflag, torch.int64, "nflag", True), _ptr(status, torch.int32, "status", True), _stream())
     return flags
+
+
+def ne_check_set_wait_limit(polls: int = 1 << 22):
+    """Test support: polls of the first wait of each block of ne_check's staged kernel."""
+    _call("ne_check_set_wait_limit", polls)
 
 
 def ne_recover(p: ne_params, delta: torch.Tensor, r_lost: int, d_hat: torch.Tensor | None = None) -> torch.Tensor:

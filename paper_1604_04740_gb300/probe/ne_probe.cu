@@ -1,13 +1,26 @@
-// Throughput ceiling of the int8 tensor path on this GPU: every warp issues
+// Measurement probes of the benchmark (not part of the library's ABI): the
+// throughput ceilings the roofline fractions of the kernels are reported
+// against.  First the int8 tensor path on this GPU: every warp issues
 // independent mma.sync.m16n8k32 s8 instructions on register operands, so the
 // launch measures the instruction's peak rate, the denominator of the
 // roofline fraction reported for the digit-plane kernels.
-#include "ne_common.cuh"
+#include <cuda_runtime.h>
+
 #include "ne_mma.cuh"
+#include "ne_probe.h"
 
 namespace {
 
 using namespace ne;
+
+int sm_count() {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+}
+
+int32_t launched() { return cudaGetLastError() == cudaSuccess ? NE_PROBE_OK : NE_PROBE_ECUDA; }
 
 constexpr int kChains = 8;   // independent accumulators per warp
 
@@ -31,12 +44,12 @@ __global__ void __launch_bounds__(256) k_probe_mma(int iters) {
 
 }  // namespace
 
-extern "C" ne_status ne_probe_mma_peak(int32_t iters, int64_t* ops, cudaStream_t s) {
-    if (iters < 1 || !ops) return fail(NE_EINVAL, "ne_probe_mma_peak: bad arguments");
+extern "C" int32_t ne_probe_mma_peak(int32_t iters, int64_t* ops, cudaStream_t s) {
+    if (iters < 1 || !ops) return NE_PROBE_EINVAL;
     const int blocks = sm_count() * 8, threads = 256;
     k_probe_mma<<<blocks, threads, 0, s>>>(iters);
     *ops = (int64_t)blocks * (threads / 32) * (int64_t)iters * kChains * (16LL * 8 * 32 * 2);
-    return check_launch("ne_probe_mma_peak");
+    return launched();
 }
 
 // The CUDA-core counterpart: dp4a (four int8 products into an int32) on
@@ -60,12 +73,12 @@ __global__ void __launch_bounds__(256) k_probe_dp4a(int iters) {
 
 }  // namespace
 
-extern "C" ne_status ne_probe_dp4a_peak(int32_t iters, int64_t* ops, cudaStream_t s) {
-    if (iters < 1 || !ops) return fail(NE_EINVAL, "ne_probe_dp4a_peak: bad arguments");
+extern "C" int32_t ne_probe_dp4a_peak(int32_t iters, int64_t* ops, cudaStream_t s) {
+    if (iters < 1 || !ops) return NE_PROBE_EINVAL;
     const int blocks = sm_count() * 8, threads = 256;
     k_probe_dp4a<<<blocks, threads, 0, s>>>(iters);
     *ops = (int64_t)blocks * threads * (int64_t)iters * 8 * 8;   // 8 dp4a x 8 int8 operations each
-    return check_launch("ne_probe_dp4a_peak");
+    return launched();
 }
 
 // Both int8 pipes at once: in every block the first mma_warps warps run the
@@ -107,17 +120,17 @@ __global__ void __launch_bounds__(512) k_probe_mixed(int iters_mma, int iters_dp
 
 }  // namespace
 
-extern "C" ne_status ne_probe_mixed_peak(int32_t iters_mma, int32_t iters_dp4a, int32_t mma_warps,
+extern "C" int32_t ne_probe_mixed_peak(int32_t iters_mma, int32_t iters_dp4a, int32_t mma_warps,
                                          int32_t dp4a_warps, int32_t blocks_per_sm, int64_t* ops,
                                          cudaStream_t s) {
     if (iters_mma < 0 || iters_dp4a < 0 || mma_warps < 0 || dp4a_warps < 0 || mma_warps + dp4a_warps < 1 ||
         mma_warps + dp4a_warps > 16 || blocks_per_sm < 1 || blocks_per_sm > 8 || !ops)
-        return fail(NE_EINVAL, "ne_probe_mixed_peak: bad arguments");
+        return NE_PROBE_EINVAL;
     const int blocks = sm_count() * blocks_per_sm, threads = 32 * (mma_warps + dp4a_warps);
     k_probe_mixed<<<blocks, threads, 0, s>>>(iters_mma, iters_dp4a, mma_warps);
     *ops = (int64_t)blocks * ((int64_t)mma_warps * iters_mma * kChains * (16LL * 8 * 32 * 2) +
                               (int64_t)dp4a_warps * 32 * iters_dp4a * 8 * 8);
-    return check_launch("ne_probe_mixed_peak");
+    return launched();
 }
 
 // The 32-bit integer multiply-add rate of the CUDA cores (IMAD, the unit the
@@ -142,10 +155,10 @@ __global__ void __launch_bounds__(256) k_probe_imad(int iters) {
 
 }  // namespace
 
-extern "C" ne_status ne_probe_imad_peak(int32_t iters, int64_t* ops, cudaStream_t s) {
-    if (iters < 1 || !ops) return fail(NE_EINVAL, "ne_probe_imad_peak: bad arguments");
+extern "C" int32_t ne_probe_imad_peak(int32_t iters, int64_t* ops, cudaStream_t s) {
+    if (iters < 1 || !ops) return NE_PROBE_EINVAL;
     const int blocks = sm_count() * 8, threads = 256;
     k_probe_imad<<<blocks, threads, 0, s>>>(iters);
     *ops = (int64_t)blocks * threads * (int64_t)iters * 8;   // 32-bit multiply-adds
-    return check_launch("ne_probe_imad_peak");
+    return launched();
 }

@@ -37,6 +37,19 @@ def test_every_declared_symbol_is_exported(lib):
         assert hasattr(lib, s), f"{s} declared in include/ but not exported"
 
 
+def test_measurement_probes_live_outside_the_library_abi(lib):
+    from paper_1604_04740_gb300 import build
+    src = open(os.path.join(build.PROBE, "ne_probe.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    probes = set(re.findall(r"\b(ne_probe_[a-z0-9_]+)\s*\(", src))
+    assert len(probes) == 4
+    plib = ctypes.CDLL(build.PROBE_LIB)
+    for s in probes:
+        assert hasattr(plib, s), s
+        assert not hasattr(lib, s), f"{s} is exported by the library"
+        assert s not in declared_symbols()
+
+
 def _choose(lib, M, w, B, policy):
     l, k = ctypes.c_int32(), ctypes.c_int32()
     st = lib.ne_choose_l(M, w, ctypes.c_int64(B), policy, ctypes.byref(l), ctypes.byref(k))

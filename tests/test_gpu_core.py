@@ -217,7 +217,7 @@ def test_gemm_i64_matches_oracle(ne, P, rows, cols, k):
     rng = np.random.default_rng(rows + cols + k)
     x = rng.integers(-(2 ** 40), 2 ** 40, (P, rows, k), dtype=np.int64)
     G = rng.integers(-128, 128, (k, cols)).astype(np.int8)
-    got = host(ne.ne_gemm(dev(x), dev(G)))
+    got = host(ne.ne_gemm(ne.planes_of(P), dev(x), dev(G), fuse=ne.NE_FUSE_NONE))
     for q in range(P):
         assert (got[q] == oracle.gemm(x[q], G)).all()
 
@@ -226,7 +226,7 @@ def test_gemm_i64_skip_mask_leaves_plane_untouched(ne):
     x = np.ones((3, 16, 16), np.int64)
     G = np.ones((16, 16), np.int8)
     out = torch.full((3, 16, 16), 7, dtype=torch.int64, device=DEV)
-    ne.ne_gemm(dev(x), dev(G), out=out, skip_mask=0b010)
+    ne.ne_gemm(ne.planes_of(3), dev(x), dev(G), out=out, fuse=ne.NE_FUSE_NONE, drop_mask=0b010)
     o = host(out)
     assert (o[1] == 7).all() and (o[0] == 16).all() and (o[2] == 16).all()
 
@@ -236,7 +236,7 @@ def test_cconv_i64_matches_oracle(ne, batch, P, N):
     rng = np.random.default_rng(N + P)
     x = rng.integers(-(2 ** 35), 2 ** 35, (batch, P, N), dtype=np.int64)
     g = rng.integers(-128, 128, (batch, N)).astype(np.int8)
-    got = host(ne.ne_cconv(dev(x), dev(g)))
+    got = host(ne.ne_cconv(ne.planes_of(P), dev(x), dev(g), fuse=ne.NE_FUSE_NONE))
     assert (got == oracle.cconv(x, g)).all()
 
 
@@ -248,7 +248,7 @@ def test_cconv_pipeline_int64(ne):
     c = inputs.streams(0, (B, M, N))
     g = inputs.operator_int8(0, (B, N))
     p = ne.params(M, l)
-    delta = ne.ne_cconv(ne.ne_entangle(p, dev(c)), dev(g))
+    delta = ne.ne_cconv(p, ne.ne_entangle(p, dev(c)), dev(g), fuse=ne.NE_FUSE_NONE)
     nf = torch.zeros(1, dtype=torch.int64, device=DEV)
     dh = host(ne.ne_extract(p, delta, r=0, nflag=nf))
     assert (dh == oracle.cconv_direct(c, g)).all() and int(nf.item()) == 0
@@ -264,7 +264,7 @@ def test_gemm_pipeline_config1_int64(ne):
     assert l == 11
     p = ne.params(M, l)
     eps = ne.ne_entangle(p, dev(c).reshape(M, 64 * 64)).reshape(M, 64, 64)
-    delta = ne.ne_gemm(eps, dev(G)).reshape(1, M, 64 * 64)
+    delta = ne.ne_gemm(p, eps, dev(G), fuse=ne.NE_FUSE_NONE).reshape(1, M, 64 * 64)
     want = oracle.gemm_direct(c, G).reshape(1, M, -1)
     gi, pos, j, b = inputs.fault_list(1, 1, 64 * 64, M, 1)
     ne.ne_inject(delta, M, dev(gi), dev(pos), dev(j), dev(b))
@@ -285,7 +285,7 @@ def test_abft_pipeline(ne):
     xh = host(x)
     for b in range(B):
         assert (xh[b, M] == oracle.abft_encode(c[b])).all()
-    d = ne.ne_cconv(x, dev(g))
+    d = ne.ne_cconv(ne.planes_of(M + 1), x, dev(g), fuse=ne.NE_FUSE_NONE)
     nf = torch.zeros(1, dtype=torch.int64, device=DEV)
     ne.ne_abft_check(M, d, nflag=nf)
     assert int(nf.item()) == 0

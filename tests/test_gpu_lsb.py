@@ -192,6 +192,6 @@ def test_cross_correlation_through_the_reversed_operand(ne, M, N):
     assert (got == direct).all() and int(nflag.item()) == 0
     # int64 CUDA-core form on the entangled words, then extract
     eps = ne.ne_entangle(p, dev(c))
-    delta = ne.ne_cconv(eps, grev)
+    delta = ne.ne_cconv(p, eps, grev, fuse=ne.NE_FUSE_NONE)
     assert (host(delta) == oracle.cxcorr(oracle.entangle(c, l), g)).all()
     assert (host(ne.ne_extract(p, delta, r=2)) == direct).all()
