@@ -64,6 +64,8 @@ def _L():
         lib.or_extract.argtypes = [i32, i32, p, i64, i32, p, p]
         lib.or_inner.argtypes = [p, p, p, i64, i64, i64]
         lib.or_cconv_at.argtypes = [p, p, i64, i64, p, p, i64, p]
+        lib.or_lconv.argtypes = [p, p, p, i64, i64, i64, i64]
+        lib.or_lconv_at.argtypes = [p, p, i64, i64, i64, p, p, i64, p]
         lib.or_rc_encode.argtypes = [p, p, i64, i64, i64, p, p]
         lib.or_gemm64.argtypes = [p, p, p, i64, i64, i64]
         lib.or_rc_check.argtypes = [p, i64, i64, p, p]
@@ -74,7 +76,7 @@ def _L():
         lib.or_abft_encode.argtypes = [i32, p, i64, p]
         lib.or_abft_check.argtypes = [i32, p, i64, p]
         lib.or_abft_recover.argtypes = [i32, p, i64, i32]
-        for f in ("or_entangle", "or_gemm", "or_cconv", "or_elementwise", "or_entangle_kernel_self",
+        for f in ("or_entangle", "or_gemm", "or_cconv", "or_lconv", "or_lconv_at", "or_elementwise", "or_entangle_kernel_self",
                   "or_extract", "or_cconv_at", "or_rc_encode", "or_gemm64", "or_rc_check", "or_rc_correct", "or_inner", "or_outer", "or_permute", "or_cxcorr", "or_abft_encode", "or_abft_check", "or_abft_recover", "or_choose_l"):
             getattr(lib, f).restype = i32
         _lib = lib
@@ -169,6 +171,33 @@ def cconv_at(x, g, signal, pos):
     pos, pp = _arr(pos, np.int64)
     y = np.empty(sig.size, np.int64)
     _chk(_L().or_cconv_at(px, pg, S, N, ps, pp, sig.size, y.ctypes.data), "cconv_at")
+    return y
+
+
+def lconv(x, g):
+    """Full linear convolution y[.., i] = sum_t g[.., t] x[.., i - t], i < n + K - 1
+    (x zero outside [0, n)); x int64 [B, S, n], g int8 [B, K]."""
+    x, px = _arr(x, np.int64)
+    g, pg = _arr(g, np.int8)
+    B, S, n = x.shape
+    K = g.shape[1]
+    assert g.shape == (B, K)
+    y = np.empty((B, S, n + K - 1), np.int64)
+    _chk(_L().or_lconv(px, pg, y.ctypes.data, B, S, n, K), "lconv")
+    return y
+
+
+def lconv_at(x, g, signal, pos):
+    """Selected outputs y[signal[t], pos[t]] of lconv(x, g), one by one
+    (signal = b * S + s)."""
+    x, px = _arr(x, np.int64)
+    g, pg = _arr(g, np.int8)
+    B, S, n = x.shape
+    K = g.shape[1]
+    sig, ps = _arr(signal, np.int64)
+    pos, pp = _arr(pos, np.int64)
+    y = np.empty(sig.size, np.int64)
+    _chk(_L().or_lconv_at(px, pg, S, n, K, ps, pp, sig.size, y.ctypes.data), "lconv_at")
     return y
 
 
@@ -366,6 +395,20 @@ def cconv_entangled(c, g, l: int, r: int = 0):
     Returns (dhat [B, M, N], flags [B, N], delta [B, M, N])."""
     eps = entangle(c, l)
     delta = cconv(eps, g)
+    dhat, flags = extract(delta, l, r)
+    return dhat, flags, delta
+
+
+def lconv_direct(c, g):
+    """c int32 [B, M, n], g int8 [B, K] -> int64 [B, M, n + K - 1]."""
+    return lconv(np.asarray(c, np.int64), g)
+
+
+def lconv_entangled(c, g, l: int, r: int = 0):
+    """entangle each group -> linear convolution per stream -> extract/check.
+    Returns (dhat [B, M, n + K - 1], flags [B, n + K - 1], delta)."""
+    eps = entangle(c, l)
+    delta = lconv(eps, g)
     dhat, flags = extract(delta, l, r)
     return dhat, flags, delta
 

@@ -296,6 +296,71 @@ int or_cconv(const int64_t *x, const int8_t *g, int64_t *y, int64_t B, int64_t S
 }
 
 /*
+ * Linear (aperiodic) convolution of a long stream with a short kernel in its
+ * full form, the convolution of the paper's second experiment (Sec. V):
+ *     y[i] = sum_{t=0}^{K-1} g[t] x[i - t],   0 <= i < n + K - 1,
+ * with x taken as 0 outside [0, n).  Sec. IV-A processes such streams as
+ * overlapping blocks (overlap-save); the blocks reproduce exactly these
+ * outputs, so the oracle is the definition itself.
+ */
+static int lconv_one(const int64_t *x, const int8_t *g, int64_t *y, int64_t n, int64_t K) {
+    int err = OR_OK;
+    for (int64_t i = 0; i < n + K - 1; i++) {
+        const int64_t t0 = i - (n - 1) > 0 ? i - (n - 1) : 0;
+        const int64_t t1 = i < K - 1 ? i : K - 1;
+        i128 acc = 0;
+        for (int64_t t = t0; t <= t1; t++) {
+            acc = checked_add(acc, checked_mul((i128)x[i - t], (i128)g[t], &err), &err);
+            if (!fits_i64(acc)) err = OR_EOVERFLOW;
+        }
+        y[i] = low64(acc);
+    }
+    return err;
+}
+
+/* Batched: x [B][S][n] (B groups of S signals), g [B][K] (one kernel per
+ * group), y [B][S][n + K - 1]. */
+int or_lconv(const int64_t *x, const int8_t *g, int64_t *y, int64_t B, int64_t S, int64_t n, int64_t K) {
+    if (B < 0 || S < 0 || n < 1 || K < 1) return OR_EINVAL;
+    int err = OR_OK;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int64_t bs = 0; bs < B * S; bs++) {
+        int64_t b = bs / S;
+        int e = lconv_one(x + bs * n, g + b * K, y + bs * (n + K - 1), n, K);
+        if (e) set_err(&err, e);
+    }
+    return err;
+}
+
+/* Selected outputs y[bs[t]][pos[t]] of or_lconv, one by one (bs = b * S + s). */
+int or_lconv_at(const int64_t *x, const int8_t *g, int64_t S, int64_t n, int64_t K, const int64_t *bs,
+                const int64_t *pos, int64_t count, int64_t *y_at) {
+    if (S < 1 || n < 1 || K < 1 || count < 0) return OR_EINVAL;
+    int err = OR_OK;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+    for (int64_t q = 0; q < count; q++) {
+        const int64_t *xs = x + bs[q] * n;
+        const int8_t *gb = g + (bs[q] / S) * K;
+        const int64_t i = pos[q];
+        int e = OR_OK;
+        i128 acc = 0;
+        if (i < 0 || i >= n + K - 1) e = OR_EINVAL;
+        for (int64_t t = 0; e == OR_OK && t < K; t++) {
+            if (i - t < 0 || i - t >= n) continue;
+            acc = checked_add(acc, checked_mul((i128)xs[i - t], (i128)gb[t], &e), &e);
+            if (!fits_i64(acc)) e = OR_EOVERFLOW;
+        }
+        y_at[q] = low64(acc);
+        if (e) set_err(&err, e);
+    }
+    return err;
+}
+
+/*
  * Element-wise LSB operations of Eq. 2 on one stream, y[i] = x[i] op g[i]:
  *   op 0: addition, op 1: subtraction, op 2: multiplication.
  * (For op in {+,-} the entangled pipeline must first entangle g with itself,

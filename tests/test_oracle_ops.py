@@ -296,3 +296,83 @@ def test_cconv_at_equals_full_cconv_at_every_requested_output():
     e[0, 0, 0] = 1
     gg = np.arange(8, dtype=np.int8).reshape(1, 8)
     assert oracle.cconv_at(e, gg, [0, 0], [0, 5]).tolist() == [0, 5]
+
+
+# ---- linear convolution of long streams (Sec. IV-A blocking, Sec. V second experiment) ----
+
+def test_lconv_matches_numpy_convolve_and_brute_force():
+    rng = np.random.default_rng(31)
+    for n, K in [(1, 1), (5, 1), (1, 7), (37, 5), (200, 64), (1000, 129), (300, 450)]:
+        x = rng.integers(-(2 ** 30), 2 ** 30, (2, 3, n), dtype=np.int64)
+        g = rng.integers(-128, 128, (2, K)).astype(np.int8)
+        y = oracle.lconv(x, g)
+        assert y.shape == (2, 3, n + K - 1)
+        for b in range(2):
+            for s in range(3):
+                assert (y[b, s] == np.convolve(x[b, s], g[b].astype(np.int64))).all()
+        if n * K <= 400:     # the definition on Python integers
+            for b in range(2):
+                for i in range(n + K - 1):
+                    want = sum(int(g[b, t]) * int(x[b, 0, i - t]) for t in range(K) if 0 <= i - t < n)
+                    assert int(y[b, 0, i]) == want
+
+
+def test_lconv_is_a_zero_padded_circular_convolution_and_blocks_overlap_save():
+    # (i) the full linear convolution is the circular convolution of length
+    # L >= n + K - 1 of the zero-padded stream and kernel; (ii) overlap-save:
+    # blocks of L inputs that overlap by K - 1, each convolved circularly,
+    # reproduce the outputs from their position K - 1 on (Sec. IV-A)
+    rng = np.random.default_rng(32)
+    n, K, L = 500, 40, 128
+    x = rng.integers(-(2 ** 20), 2 ** 20, (1, 2, n), dtype=np.int64)
+    g = rng.integers(-128, 128, (1, K)).astype(np.int8)
+    y = oracle.lconv(x, g)
+    Lf = n + K - 1
+    xp = np.zeros((1, 2, Lf), np.int64)
+    xp[..., :n] = x
+    gp = np.zeros((1, Lf), np.int8)
+    gp[:, :K] = g
+    assert (oracle.cconv(xp, gp) == y).all()
+    B = L - K + 1
+    gL = np.zeros((1, L), np.int8)
+    gL[:, :K] = g
+    out = np.zeros_like(y)
+    for j0 in range(0, Lf, B):
+        seg = np.zeros((1, 2, L), np.int64)
+        lo = j0 - (K - 1)
+        for q in range(L):
+            if 0 <= lo + q < n:
+                seg[..., q] = x[..., lo + q]
+        blk = oracle.cconv(seg, gL)
+        take = min(B, Lf - j0)
+        out[..., j0:j0 + take] = blk[..., K - 1:K - 1 + take]
+    assert (out == y).all()
+
+
+@pytest.mark.parametrize("M,l", [(3, 16), (4, 16), (8, 8)])
+def test_lconv_pipeline_equals_direct_flags_and_recovers(M, l):
+    rng = np.random.default_rng(33 + M)
+    n, K = 700, 90
+    c = rng.integers(-128, 128, (2, M, n)).astype(np.int32)
+    g = rng.integers(-128, 128, (2, K)).astype(np.int8)
+    direct = oracle.lconv_direct(c, g)
+    dhat, flags, delta = oracle.lconv_entangled(c, g, l, r=M - 1)
+    assert (dhat == direct).all() and not flags.any()
+    bad = delta.copy()
+    bad[1, 2, 333] ^= np.int64(1 << 37)
+    _, f = oracle.extract(bad, l, 0)
+    assert f.sum() == 1 and f[1, 333] == 1
+    assert (oracle.recover(bad, l, 2) == direct).all()
+
+
+def test_lconv_at_equals_full_lconv_at_every_requested_output():
+    rng = np.random.default_rng(34)
+    n, K = 400, 77
+    x = rng.integers(-(2 ** 30), 2 ** 30, (3, 2, n), dtype=np.int64)
+    g = rng.integers(-128, 128, (3, K)).astype(np.int8)
+    y = oracle.lconv(x, g)
+    sig = rng.integers(0, 6, 300)
+    pos = rng.integers(0, n + K - 1, 300)
+    pos[:3] = [0, n + K - 2, n - 1]
+    got = oracle.lconv_at(x, g, sig, pos)
+    assert (got == y.reshape(6, -1)[sig, pos]).all()
