@@ -1284,6 +1284,66 @@ def run_serve(args, rank, world, local_rank):
     return None
 
 
+def lconv_summary(local_rank):
+    """The paper's second experiment on this GPU: streams of 10^6 samples
+    convolved (full linear convolution) with kernels of 100 and 4500 taps,
+    M = 3 and 8, entangled (one fused launch with extract/check) against the
+    plain operation on the same kernel (same digit set, and one digit)."""
+    import torch
+    from paper_1604_04740_gb300 import inputs
+    from paper_1604_04740_gb300 import ne
+    from paper_1604_04740_gb300 import probe
+    dev = torch.device("cuda", local_rank)
+    flush = L2Flush(torch, dev)
+    n, K_, W = 10 ** 6, 10, 3
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    probe.mma_peak(64)
+    e0.record(stream)
+    pk = probe.mma_peak(4096)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    peak = pk / (e0.elapsed_time(e1) * 1e-3) / 1e12
+    out = {"n": n, "peak_mma_TOPs": peak}
+    for M in (3, 8):
+        c = torch.from_numpy(inputs.streams(0, (1, M, n))).to(dev)
+        for K in (100, 4500):
+            l, k = ne.ne_choose_l(M, 64, K * 2 ** 14, ne.NE_L_BYTE)
+            p = ne.params(M, l)
+            dg = ne.ne_plan_digits(l, -128, 127)
+            g = torch.from_numpy(inputs.operator_int8(0, (1, K))).to(dev)
+            no = n + K - 1
+            o = torch.empty((1, M, no), dtype=torch.int64, device=dev)
+            fl = torch.empty((no + 31) // 32, dtype=torch.int32, device=dev)
+            nf = torch.zeros(1, dtype=torch.int64, device=dev)
+            st = torch.zeros(1, dtype=torch.int32, device=dev)
+            runs = {"entangled": lambda ev: ne.ne_lconv(p, dg, c, g, o, fl, nf, ne.NE_FUSE_EXTRACT_CHECK, 0, status=st),
+                    "plain_same_digits": lambda ev: ne.ne_lconv(p, dg, c, g, o, None, None, ne.NE_FUSE_NONE, 0,
+                                                                plain=True),
+                    "plain_one_digit": lambda ev: ne.ne_lconv(p, ne.raw_digits(), c, g, o, None, None,
+                                                              ne.NE_FUSE_NONE, 0, plain=True)}
+            ms = {}
+            for name, fn in runs.items():
+                t, _ = timed_steps(torch, fn, K_, W, flush)
+                ms[name] = t / K_
+            ne.ne_lconv(p, dg, c, g, o, fl, nf, ne.NE_FUSE_EXTRACT_CHECK, 0, status=st)
+            torch.cuda.synchronize()
+            assert int(nf.item()) == 0 and int(st.item()) == 0, "clean linear convolution flagged"
+            NU = (K + 62) // 64 + 1
+            tiles = -(-(-(-no // 64)) // 16)
+            mma = 2 * M * dg.S * tiles * 1024 * NU * 64
+            out[f"M{M}_K{K}"] = {
+                "l": l, "digits": list(dg.shifts), "ms": ms,
+                "useful_Gop_s": 2 * M * n * K / (ms["entangled"] * 1e-3) / 1e9,
+                "tensor_frac": mma / (ms["entangled"] * 1e-3) / 1e12 / peak,
+                "overhead_pct": {"vs_plain_same_kernel_same_digits": 100 * (ms["entangled"] / ms["plain_same_digits"] - 1),
+                                 "vs_plain_fewest_digits": 100 * (ms["entangled"] / ms["plain_one_digit"] - 1)}}
+            del o, fl
+        del c
+        torch.cuda.empty_cache()
+    return out
+
+
 def other_configs(args, rank, world, local_rank):
     """Summaries of the other workloads for the default line, each measured
     here with fewer steps: the small int64 product (with its fault and dropped
@@ -1299,6 +1359,10 @@ def other_configs(args, rank, world, local_rank):
     keep = ("value", "unit", "ms_per_step", "steps", "warmup", "dtype", "config", "digit_plan", "roofline",
             "overhead_pct", "ms", "fault_injection", "fault_and_drop", "int64_outputs_equal_tensor_path",
             "cpu_baseline", "e2e", "clocks", "gpu_launches", "jobs_per_s", "detection", "serving")
+    try:
+        out["lconv_1e6"] = lconv_summary(local_rank)
+    except Exception as e:
+        out["lconv_1e6"] = {"error": f"{type(e).__name__}: {e}"}
     for name, wl, over in runs:
         a = copy.copy(args)
         a.workload = wl

@@ -79,12 +79,18 @@ struct TileArgs {
     // (y & w_nsmask) != w_nswant is outside the plan and sets *status = NE_ERANGE
     const int64_t* cwords;
     uint64_t w_nsmask, w_nswant;
+    // linear form (LD_LINEAR): the raw streams craw are [M][lin_n], g has
+    // lin_K taps, and the outputs [M][N] are the full linear convolution,
+    // N = lin_n + lin_K - 1 (inputs outside [0, lin_n) and taps outside
+    // [0, lin_K) are zero)
+    int lin_n, lin_K;
 };
 
 // where a tile's digit rows come from
 constexpr int LD_PLANES = 0;   // digit planes in memory (cp.async)
 constexpr int LD_RAW = 1;      // the raw int32 streams: Eq. 16 and the split while loading
 constexpr int LD_WORDS = 2;    // the entangled int64 words: the split while loading
+constexpr int LD_LINEAR = 3;   // as LD_RAW, for the linear convolution of long streams
 
 __device__ __forceinline__ int64_t shl64(int64_t x, int s) { return (int64_t)((uint64_t)x << s); }
 
@@ -120,7 +126,10 @@ __device__ __forceinline__ void epilogue_l(const TileArgs& a, const int32_t* sta
         const int i = base + lane;
         const int pr = i / T, q = i % T;
         const int32_t* sp = stash + pr * SP + q;
+        // the last block of a linear convolution ends inside the tile
+        const bool valid = i0 + i < a.N;
         if (a.fuse == NE_FUSE_NONE) {
+            if (!valid) continue;
             for (int m = 0; m < M; m++) {
                 int64_t v = digits(sp, m);
                 if (f1 > f0) v = apply_faults(v, a.fault_pos, a.fault_stream, a.fault_bit, f0, f1, key0 + i, m);
@@ -128,6 +137,7 @@ __device__ __forceinline__ void epilogue_l(const TileArgs& a, const int32_t* sta
             }
             continue;
         }
+        if (i0 + base >= a.N) continue;                  // warp-uniform: the whole warp is past the end
         int64_t rot[MT ? MT : 32], res[MT ? MT : 32];
 #pragma unroll
         for (int j = 0; j < (MT ? MT : 32); j++) {
@@ -135,19 +145,19 @@ __device__ __forceinline__ void epilogue_l(const TileArgs& a, const int32_t* sta
             int m = a.r + j;
             if (m >= M) m -= M;
             int64_t v = 0;
-            if (j > 0 || need_r) {
+            if (valid && (j > 0 || need_r)) {
                 v = digits(sp, m);
                 if (f1 > f0) v = apply_faults(v, a.fault_pos, a.fault_stream, a.fault_bit, f0, f1, key0 + i, m);
             }
             rot[j] = v;
         }
-        const bool flag = extract_rot<MT>(rot, M, l, check, res);
+        const bool flag = extract_rot<MT>(rot, M, l, check, res) && valid;
 #pragma unroll
         for (int j = 0; j < (MT ? MT : 32); j++) {
             if (!MT && j >= M) break;
             int m = a.r + j;
             if (m >= M) m -= M;
-            a.out[(int64_t)m * a.N + i0 + i] = res[j];
+            if (valid) a.out[(int64_t)m * a.N + i0 + i] = res[j];
         }
         if (check) {
             const uint32_t w = __ballot_sync(0xffffffffu, flag);
@@ -297,14 +307,98 @@ __device__ __forceinline__ void load_window(const TileArgs& a, uint8_t* sig, int
     }
 }
 
+// The linear form's window: input blocks first .. first + WB - 1 of the raw
+// streams (no wrap), every position outside [0, lin_n) zero.  Work items as
+// in load_window<LD_RAW>; an item entirely inside a stream whose rows start
+// 16-byte aligned takes the vector loads, the others element by element.
+__device__ __forceinline__ void load_window_linear(const TileArgs& a, uint8_t* sig, int WB, int first, int nthr) {
+    const int M = a.M, S = a.S, MS = a.MS, n = a.lin_n;
+    const bool vec_ok = (n & 3) == 0;
+    uint32_t worst = 0;
+    for (int e = threadIdx.x; e < WB * M * 4; e += nthr) {
+        const int c16 = e & 3, rowm = e >> 2;
+        const int blk_rel = rowm / M, m = rowm - blk_rel * M;
+        uint8_t* dst = sig + (blk_rel * MS + m * S) * ROWB + c16 * 16;
+        const int64_t pos = (int64_t)(first + blk_rel) * T + c16 * 16;
+        if ((a.fuse == NE_FUSE_RECOVER && m == a.r) || pos + 16 <= 0 || pos >= n) {
+            for (int s = 0; s < S; s++) *reinterpret_cast<uint4*>(dst + s * ROWB) = make_uint4(0u, 0u, 0u, 0u);
+            continue;
+        }
+        const int mp = m == 0 ? M - 1 : m - 1;
+        const bool check_prev = a.fuse == NE_FUSE_RECOVER && mp == a.r;
+        const int32_t* xm = a.craw + (int64_t)m * n;
+        const int32_t* xp = a.craw + (int64_t)mp * n;
+        uint32_t y[16];
+        if (vec_ok && pos >= 0 && pos + 16 <= n) {
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const int4 v = __ldg(reinterpret_cast<const int4*>(xm + pos) + q);
+                y[4 * q] = (uint32_t)v.x;
+                y[4 * q + 1] = (uint32_t)v.y;
+                y[4 * q + 2] = (uint32_t)v.z;
+                y[4 * q + 3] = (uint32_t)v.w;
+            }
+#pragma unroll
+            for (int k = 0; k < 16; k++) {
+                worst = max(worst, y[k] - (uint32_t)a.raw_lo);
+                y[k] += a.raw_off;
+            }
+            if (!a.raw_plain) {
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const int4 v = __ldg(reinterpret_cast<const int4*>(xp + pos) + q);
+                    const uint32_t w[4] = {(uint32_t)v.x, (uint32_t)v.y, (uint32_t)v.z, (uint32_t)v.w};
+#pragma unroll
+                    for (int k = 0; k < 4; k++) {
+                        y[4 * q + k] += w[k] << a.l;
+                        if (check_prev) worst = max(worst, w[k] - (uint32_t)a.raw_lo);
+                    }
+                }
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 16; k++) {
+                const int64_t i = pos + k;
+                uint32_t v = 0;                       // zero padding: the word 0, every digit 0
+                if (i >= 0 && i < n) {
+                    const uint32_t x = (uint32_t)__ldg(xm + i);
+                    worst = max(worst, x - (uint32_t)a.raw_lo);
+                    v = x;
+                    if (!a.raw_plain) {
+                        const uint32_t w = (uint32_t)__ldg(xp + i);
+                        if (check_prev) worst = max(worst, w - (uint32_t)a.raw_lo);
+                        v += w << a.l;
+                    }
+                }
+                y[k] = v + a.raw_off;
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < 4; s++) {
+            if (s >= S) break;
+            const uint32_t t = (uint32_t)a.raw_byte[s];
+            *reinterpret_cast<uint4*>(dst + s * ROWB) =
+                make_uint4(pick4(y[0], y[1], y[2], y[3], t), pick4(y[4], y[5], y[6], y[7], t),
+                           pick4(y[8], y[9], y[10], y[11], t), pick4(y[12], y[13], y[14], y[15], t));
+        }
+    }
+    if (worst > (uint32_t)a.raw_hi - (uint32_t)a.raw_lo && a.status) atomicExch(a.status, (int32_t)NE_ERANGE);
+}
+
 // The tile of output blocks [p0, p0 + npb) of one group; all 256 threads of
 // the block take part.  smem: smem_bytes(MS) bytes, 128-byte aligned.
+// LD_LINEAR: the shifts u run over the kernel's NU = (K + 62) / 64 + 1 blocks
+// of G_u[q][t] = g[T u + q - t] (zero outside [0, K)) and input block p - u
+// is zero outside the stream, so each output block sums NU products instead
+// of NB (Sec. IV-A: a long stream needs only the blocks the kernel reaches).
 template <int NTW, int MT, int LD = LD_PLANES>
 __device__ __forceinline__ void tile(const TileArgs& a, uint8_t* smem, int p0, int npb) {
     const int MS = a.MS;
     const int N = a.N;
     const int NB = N / T;
-    const int uch = min(UCH, NB);
+    constexpr bool LIN = LD == LD_LINEAR;
+    const int NU = LIN ? (a.lin_K + 62) / T + 1 : NB;   // shifts u
+    const int uch = min(UCH, NU);
     const int WB = npb + uch - 1;
     const int cols = npb * MS;
     const int NT = (cols + 7) / 8;
@@ -328,21 +422,31 @@ __device__ __forceinline__ void tile(const TileArgs& a, uint8_t* smem, int p0, i
 #pragma unroll
     for (int j = 0; j < NTW; j++) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0;
 
-    for (int u0 = 0; u0 < NB; u0 += uch) {
-        const int uc = min(uch, NB - u0);
-        // digit rows of input blocks (p0 - (u0 + uch - 1) + blk_rel) mod NB
-        load_window<LD>(a, sig, WB, p0 - (u0 + uch - 1), NB, THREADS);
+    for (int u0 = 0; u0 < NU; u0 += uch) {
+        const int uc = min(uch, NU - u0);
+        // digit rows of input blocks (p0 - (u0 + uch - 1) + blk_rel), mod NB for
+        // the circular convolution
+        if constexpr (LIN) load_window_linear(a, sig, WB, p0 - (u0 + uch - 1), THREADS);
+        else load_window<LD>(a, sig, WB, p0 - (u0 + uch - 1), NB, THREADS);
         cp_async_commit();
         // g copies: copy rr, byte z holds g[(T (u0 + uch) - (z + rr - PADB)) mod N]
+        // (linear: g at that index, 0 outside [0, K))
         const int top = T * (u0 + uch);
         for (int e = tid; e < 4 * (GW / 4); e += THREADS) {
             const int rr = e / (GW / 4), zw = e - rr * (GW / 4);
             uint32_t w = 0;
 #pragma unroll
             for (int k = 0; k < 4; k++) {
-                int idx = (top - (4 * zw + k + rr - PADB)) % N;
-                if (idx < 0) idx += N;
-                w |= (uint32_t)(uint8_t)__ldg(a.g + idx) << (8 * k);
+                int idx = top - (4 * zw + k + rr - PADB);
+                uint32_t gv;
+                if constexpr (LIN) {
+                    gv = (idx >= 0 && idx < a.lin_K) ? (uint32_t)(uint8_t)__ldg(a.g + idx) : 0u;
+                } else {
+                    idx %= N;
+                    if (idx < 0) idx += N;
+                    gv = (uint32_t)(uint8_t)__ldg(a.g + idx);
+                }
+                w |= gv << (8 * k);
             }
             *reinterpret_cast<uint32_t*>(gcp + rr * GW + 4 * zw) = w;
         }

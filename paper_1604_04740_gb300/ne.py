@@ -153,6 +153,7 @@ def _load():
         "ne_copy_regions_h2d": [P, P, P, P, P, i64, P],
         "ne_cconv_entangled": [ne_params, ne_digits, P, P, P, P, P, i64, i64, i32, i32, i32, ne_faults, P, P],
         "ne_set_cconv_split": [i32],
+        "ne_lconv": [ne_params, ne_digits, P, P, P, P, P, i64, i64, i64, i32, i32, i32, ne_faults, P, P],
         "ne_cconv_ntt_any": [ne_params, i32, i32, P, P, P, P, P, i64, i64, i32, i32, i32, ne_faults, P, P, i64, P],
         "ne_cconv_ntt": [ne_params, ne_digits, P, P, P, P, P, i64, i64, i32, i32, i32, ne_faults, P, P],
         "ne_abft_rc_encode": [P, P, P, P, i64, i64, i64, i64, P],
@@ -397,6 +398,26 @@ def ne_cconv_entangled(p: ne_params, dg: ne_digits, c: torch.Tensor, g: torch.Te
           _ptr(out, torch.int64, "out"), _ptr(flags, torch.int32, "flags", True),
           _ptr(nflag, torch.int64, "nflag", True), batch, N, fuse, r, 1 if plain else 0, _faults_arg(faults),
           _ptr(status, torch.int32, "status", True), _stream())
+    return out
+
+
+def ne_lconv(p: ne_params, dg: ne_digits, c: torch.Tensor, g: torch.Tensor, out: torch.Tensor | None = None,
+             flags: torch.Tensor | None = None, nflag: torch.Tensor | None = None,
+             fuse: int = NE_FUSE_EXTRACT_CHECK, r: int = 0, plain: bool = False,
+             status: torch.Tensor | None = None, faults=None) -> torch.Tensor:
+    """Full linear convolution of long streams: c int32 [batch, M, n] (raw),
+    g int8 [batch, K] -> int64 [batch, M, n + K - 1]."""
+    batch, M, n = c.shape
+    if M != p.M or g.dim() != 2 or g.shape[0] != batch:
+        raise ValueError("c must be [batch, M, n] and g [batch, K]")
+    K = g.shape[1]
+    if out is None:
+        out = torch.empty((batch, M, n + K - 1), dtype=torch.int64, device=c.device)
+    if tuple(out.shape) != (batch, M, n + K - 1):
+        raise ValueError("out must be [batch, M, n + K - 1]")
+    _call("ne_lconv", p, dg, _ptr(c, torch.int32, "c"), _ptr(g, torch.int8, "g"), _ptr(out, torch.int64, "out"),
+          _ptr(flags, torch.int32, "flags", True), _ptr(nflag, torch.int64, "nflag", True), batch, n, K, fuse, r,
+          1 if plain else 0, _faults_arg(faults), _ptr(status, torch.int32, "status", True), _stream())
     return out
 
 
