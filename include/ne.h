@@ -195,8 +195,7 @@ ne_status ne_split_digits(ne_digits dg, const int64_t* x, int8_t* planes, int64_
 /* Matrix product (the GEMM experiment of Sec. V): out[m] = eps[m] * G.
  * eps: int64 [M][rows][k]; G: int8 [k][cols]; out: int64 [M][rows][cols]
  * (must not overlap eps); positions i * cols + j for flags [ceil(rows cols /
- * 32)] and faults.  NE_MODE_S8SLICE: k a multiple of 16, cols of 8, M * dg.S
- * <= 16, eps 16-byte aligned. */
+ * 32)] and faults.  NE_MODE_S8SLICE: k <= 131056, M * dg.S <= 16. */
 ne_status ne_gemm(ne_params p, const int64_t* eps, const int8_t* G, int64_t* out, uint32_t* flags, uint64_t* nflag,
                   int32_t rows, int32_t cols, int32_t k, int32_t mode, ne_digits dg, int32_t fuse, int32_t r,
                   uint32_t drop_mask, ne_faults faults, int32_t* status, cudaStream_t s);
@@ -224,7 +223,8 @@ ne_status ne_cconv(ne_params p, const int64_t* eps, const int8_t* g, int64_t* ou
  *        from the other M-1 streams (Prop. 3); flags ignored.
  * faults: transient faults XORed into delta before the epilogue (see
  * ne_faults; positions i * cols + j).
- * rows, cols >= 1; k >= 1 and a multiple of 16; cols a multiple of 8. */
+ * rows, cols, k >= 0, k <= 131056; any sizes (a k that is not a multiple of
+ * 16, or cols not of 4, take element-wise loads). */
 ne_status ne_gemm_digits(ne_params p, ne_digits dg, const int8_t* planes, const int8_t* G,
                          int64_t* out, uint32_t* flags, uint64_t* nflag,
                          int32_t rows, int32_t cols, int32_t k,
@@ -259,6 +259,27 @@ ne_status ne_cconv_digits(ne_params p, ne_digits dg, const int8_t* planes, const
 ne_status ne_cconv_entangled(ne_params p, ne_digits dg, const int32_t* c, const int8_t* g, int64_t* out,
                              uint32_t* flags, uint64_t* nflag, int64_t batch, int64_t N, int32_t fuse,
                              int32_t r, int32_t plain, ne_faults faults, int32_t* status, cudaStream_t s);
+
+/* Linear convolution of long streams with a short kernel, the convolution of
+ * the paper's second experiment (Sec. V; long streams processed as
+ * overlapping blocks of about the kernel's length, Sec. IV-A), fused from the
+ * raw streams to the extracted outputs in one launch on the int8 tensor path:
+ *     out[b][m][i] = sum_{t<K} g[b][t] w[b][m][i - t],  0 <= i < n + K - 1,
+ * with w the words of Eq. 16 (plain = 1: the raw values c) and w = 0 outside
+ * [0, n) -- the full linear convolution of every entangled stream, then the
+ * epilogue of ne_cconv_digits (fuse, r, flags/nflag, faults at positions
+ * b * (n + K - 1) + i).  Every tile of 1024 outputs reads the K + 1023 inputs
+ * it reaches (the overlap of overlap-save is the kernel's K - 1) and sums
+ * only the kernel's Toeplitz blocks.  c: int32 [batch][M][n], 16-byte
+ * aligned; g: int8 [batch][K]; out: int64 [batch][M][n + K - 1]; flags:
+ * uint32 [batch][ceil((n + K - 1) / 32)].  1 <= K <= 131071, n + K - 1 <=
+ * 2^30, M * dg.S <= 16.  dg and plain as for ne_cconv_entangled (an input
+ * outside [lo, hi] sets *status = NE_ERANGE, the lost stream's included under
+ * NE_FUSE_RECOVER); l must give an Eq. 14 range that covers the outputs'
+ * bound K max|c| 128. */
+ne_status ne_lconv(ne_params p, ne_digits dg, const int32_t* c, const int8_t* g, int64_t* out, uint32_t* flags,
+                   uint64_t* nflag, int64_t batch, int64_t n, int64_t K, int32_t fuse, int32_t r, int32_t plain,
+                   ne_faults faults, int32_t* status, cudaStream_t s);
 
 /* Tuning knob (no counterpart in the paper; process-wide, for calls made
  * after it): how ne_cconv_digits and ne_cconv_entangled split a group of at
@@ -513,9 +534,10 @@ typedef struct {
     int32_t kind;              /* NE_JOB_GEMM or NE_JOB_CCONV                                 */
     int32_t M;                 /* streams, 3..5                                               */
     int32_t l;                 /* shift; 0: chosen by the plan's l_policy from the job's bound */
-    int32_t rows, cols, k;     /* GEMM: (rows x k) streams times a (k x cols) operator;
-                                  k a multiple of 16, cols a multiple of 8                    */
-    int32_t N;                 /* CCONV: signal length, a multiple of 64 in [64, 65536]       */
+    int32_t rows, cols, k;     /* GEMM: (rows x k) streams times a (k x cols) operator,
+                                  any sizes >= 1 with k <= 131056                             */
+    int32_t N;                 /* CCONV: signal length in [2, 65536]; a length that is not a
+                                  multiple of 64 runs on the exact transforms                */
     int32_t r;                 /* checked stream (EXTRACT_CHECK) or lost stream (RECOVER)     */
     int32_t fuse;              /* NE_FUSE_EXTRACT_CHECK, NE_FUSE_RECOVER, or NE_FUSE_NONE
                                   (outputs are the words delta_m; no check)                  */
@@ -538,7 +560,8 @@ typedef struct {
     int32_t l_policy;          /* NE_L_BYTE or NE_L_SMALLEST for jobs with l = 0              */
     int32_t ntt_min_n;         /* convolutions with N >= this (and outputs inside the two-prime
                                   range) run as exact transforms (ne_cconv_ntt_any's kernels)
-                                  instead of tensor tiles; 0: never                            */
+                                  instead of tensor tiles; 0: only those whose N is not a
+                                  multiple of 64 (the tiles take whole blocks of 64)           */
 } ne_batch_config;
 
 typedef struct {               /* what ne_batch_run needs to know on the host                 */
@@ -598,18 +621,27 @@ ne_status ne_batch_run(ne_batch_info info, const int32_t* c, const int8_t* ops, 
  * is not acceptable -- and therefore cannot hand ne_batch_run a workspace.
  *
  * ne_batch_run_static plans the batch (as ne_batch_plan) and runs it (as
- * ne_batch_run) with the scratch memory -- the plan's tables and every job's
- * digit planes -- in one static device array of NE_STATIC_WORKSPACE_BYTES
- * bytes that the library owns.  That array exists on every GPU the library
- * is loaded on, from the first use until the process exits.  The caller
- * still passes every input and output (device pointers, as for
+ * ne_batch_run) with the scratch memory -- the plan's tables, every job's
+ * digit planes and the transform jobs' table and scratch -- in one static
+ * device array of NE_STATIC_WORKSPACE_BYTES bytes that the library owns.
+ * The caller still passes every input and output (device pointers, as for
  * ne_batch_run; jobs and cfg are host data).  The call allocates no device
  * memory.
+ *  - The array is part of the batch code's device module: it is held on
+ *    every GPU where that module is loaded -- from the first launch of any
+ *    batch kernel (ne_batch_run included) with CUDA's lazy module loading,
+ *    or from the library's load with CUDA_MODULE_LOADING=EAGER -- until the
+ *    process exits, whether or not ne_batch_run_static is ever called.
  *  - A batch whose scratch exceeds the array is rejected with NE_ENOMEM
  *    before any device work.
  *  - The first call on a device looks up the array's device address (one
- *    runtime query with that device current); make that first call before
- *    any stream capture.
+ *    runtime query with that device current), and the first call that holds
+ *    a transform job also fills the library's twiddle tables and
+ *    synchronises s.
+ *  - Do not call it under stream capture: every call plans the batch, which
+ *    copies the tables from host memory that lives only during the call.
+ *    To replay a batch from a CUDA graph, plan it with ne_batch_plan into a
+ *    caller workspace and capture ne_batch_run.
  *  - The planning's table copy is ordered on s, before the run; consecutive
  *    calls on one stream therefore never see each other's tables.
  *  - All calls share the one array: calls whose work overlaps on the GPU

@@ -52,15 +52,11 @@ class JobSpec:
         return 2 * self.M * self.N * self.N
 
 
-def _round_to(x, q, lo):
-    return max(lo, int(round(x / q)) * q)
-
-
 def mixed_jobs(seed: int, njobs: int = 2048, mnk=(32, 2048), conv=(256, 65536), recover_frac: float = 0.0):
     """The ragged job mix: M uniform in {3, 4, 5}; half products with m, n, k
     log-uniform in [mnk], half circular convolutions with N log-uniform in
-    [conv].  Sizes are rounded to the kernels' granularity (k to 16, n to 8,
-    N to 64).  A fraction recover_frac of jobs loses one stream (uniform)."""
+    [conv], every size used exactly as drawn.  A fraction recover_frac of
+    jobs loses one stream (uniform)."""
     T = inputs.TAG_JOBS
     Ms = (inputs.u64(seed, T, 0, njobs) % np.uint64(3)).astype(np.int64) + 3
     keys = inputs.u64(seed, T, njobs, njobs)
@@ -78,10 +74,10 @@ def mixed_jobs(seed: int, njobs: int = 2048, mnk=(32, 2048), conv=(256, 65536), 
         fuse = ne.NE_FUSE_RECOVER if lost[i] else ne.NE_FUSE_EXTRACT_CHECK
         r = int(lost_r[i] % np.uint64(M)) if lost[i] else 0
         if kinds[i] == ne.NE_JOB_GEMM:
-            specs.append(JobSpec(ne.NE_JOB_GEMM, M, rows=int(rows[i]), cols=_round_to(cols[i], 8, 8),
-                                 k=_round_to(ks[i], 16, 16), fuse=fuse, r=r))
+            specs.append(JobSpec(ne.NE_JOB_GEMM, M, rows=int(rows[i]), cols=int(cols[i]), k=int(ks[i]), fuse=fuse,
+                                 r=r))
         else:
-            specs.append(JobSpec(ne.NE_JOB_CCONV, M, N=min(conv[1], _round_to(Ns[i], 64, 64)), fuse=fuse, r=r))
+            specs.append(JobSpec(ne.NE_JOB_CCONV, M, N=int(Ns[i]), fuse=fuse, r=r))
     return specs
 
 

@@ -37,7 +37,9 @@ constexpr int SEG = 8192;        // positions per entangle segment
 constexpr int MS_MAX = 10;       // M <= 5 streams x S <= 2 digits
 
 struct DevJob {
-    int32_t kind, M, l, S, MS, rows, cols, k, N, r, fuse, pad;
+    int32_t kind, M, l, S, MS, rows, cols, k, N, r, fuse;
+    int32_t kc;                  // products: the inputs' k; k itself is the digit planes' and
+                                 // G^T's row length, kc rounded up to 16 (zero padded)
     int32_t shift[NE_MAX_DIGITS];
     FastPlan fp;
     int64_t c_off, op_off, out_off, flag_off, plane_off, npos, nout, fault_begin, fault_end;
@@ -49,13 +51,15 @@ struct DevTile {
 };
 
 constexpr int SEG_ENTANGLE = 0, SEG_TRANSPOSE = 1;
+constexpr int SEG_ROWS = 2;      // a product whose k is not a multiple of 16: whole rows, padded
 constexpr int TT = 64;           // G transpose tiles: TT k x TT columns
 constexpr int TT_PER_SEG = 16;
 constexpr int TT_ROUND = 4;      // transpose tiles loaded together
 
 struct DevSeg {
     int32_t job, kind;
-    int64_t start, count;        // entangle: positions of every stream of the job; transpose: tiles
+    int64_t start, count;        // entangle: positions of every stream of the job; transpose: tiles;
+                                 // rows: rows of every stream
 };
 
 struct Layout {
@@ -394,12 +398,68 @@ __device__ __forceinline__ bool entangle_segment(const BatchK& k, const DevJob* 
     return worst <= (uint32_t)F.hi - (uint32_t)F.lo;
 }
 
+// Rows [start, start + count) of a product job whose k is not a multiple of
+// 16: the digit planes keep rows of k = kc rounded up to 16 so that the tiles
+// stream them in 16-byte pieces; positions kc .. k - 1 hold the word 0 (every
+// digit 0), which adds nothing to the products.  Inputs are read element by
+// element (a row of kc int32 values need not start 16-byte aligned); each
+// thread forms 8 positions of one row of every stream and stores 8 bytes per
+// digit plane.
+template <int MT>
+__device__ __forceinline__ bool entangle_rows(const BatchK& k, const DevJob* J, const DevSeg& sg) {
+    const int kc = J->kc, kp = J->k;
+    const int64_t nin = (int64_t)J->rows * kc, npl = (int64_t)J->rows * kp;
+    const int32_t* cb = k.c + J->c_off;
+    int8_t* pb = k.planes + J->plane_off;
+    const FastPlan F = J->fp;
+    const int l = J->l;
+    const bool plain = F.pmask == 0;
+    uint32_t worst = 0;
+    const int cpr = kp / 8;
+    const int64_t nch = sg.count * cpr;
+    for (int64_t q = threadIdx.x; q < nch; q += THREADS) {
+        const int64_t row = sg.start + q / cpr;
+        const int t0 = (int)(q % cpr) * 8;
+        uint32_t v[MT][8];
+#pragma unroll
+        for (int m = 0; m < MT; m++)
+#pragma unroll
+            for (int e = 0; e < 8; e++) {
+                const int t = t0 + e;
+                v[m][e] = 0;
+                if (t < kc) {
+                    v[m][e] = (uint32_t)__ldg(cb + m * nin + row * kc + t);
+                    worst = max(worst, v[m][e] - (uint32_t)F.lo);
+                }
+            }
+#pragma unroll
+        for (int m = 0; m < MT; m++) {
+            const int pm = (m + MT - 1) % MT;
+            uint32_t y[8];
+#pragma unroll
+            for (int e = 0; e < 8; e++) y[e] = v[m][e] + (plain ? 0u : v[pm][e] << l) + F.off;
+#pragma unroll
+            for (int s = 0; s < 4; s++) {
+                if (s >= F.S) break;
+                const uint32_t t = (uint32_t)F.byte_of[s];
+                const uint32_t sel = t | ((t + 4) << 4);
+                const uint32_t w0 = __byte_perm(__byte_perm(y[0], y[1], sel), __byte_perm(y[2], y[3], sel), 0x5410);
+                const uint32_t w1 = __byte_perm(__byte_perm(y[4], y[5], sel), __byte_perm(y[6], y[7], sel), 0x5410);
+                *reinterpret_cast<uint2*>(pb + (m * F.S + s) * npl + row * kp + t0) =
+                    make_uint2(w0 ^ 0x80808080u, w1 ^ 0x80808080u);
+            }
+        }
+    }
+    return worst <= (uint32_t)F.hi - (uint32_t)F.lo;
+}
+
 // tiles [start, start + count) of G^T = the transpose of a product job's G
 // ([k][cols] -> [cols][k], so the product tiles stream both operands k-major),
 // TT_ROUND tiles per round so that each thread has 4 TT_ROUND loads in flight
 __device__ __forceinline__ void transpose_segment(const BatchK& k, const DevJob* J, const DevSeg& sg,
                                                   uint8_t (*tile)[TT][TT + 4]) {
-    const int K = J->k, cols = J->cols;
+    const int K = J->kc, KP = J->k, cols = J->cols;
+    const bool words = (cols & 3) == 0;        // rows of G start 4-byte aligned
     const int nct = (cols + TT - 1) / TT;
     const uint8_t* G = reinterpret_cast<const uint8_t*>(k.ops + J->op_off);
     uint8_t* GT = reinterpret_cast<uint8_t*>(k.planes + J->gt_off);
@@ -416,8 +476,17 @@ __device__ __forceinline__ void transpose_segment(const BatchK& k, const DevJob*
                 const int e = threadIdx.x + i * THREADS;
                 const int kr = e / (TT / 4), cw = e % (TT / 4);
                 const int gk = k0 + kr, gc = c0 + 4 * cw;
-                w[h][i] = (h < nt && gk < K && gc < cols)
-                              ? __ldg(reinterpret_cast<const uint32_t*>(G + (int64_t)gk * cols + gc)) : 0u;
+                uint32_t x = 0;
+                if (h < nt && gk < K && gc < cols) {
+                    if (words) {
+                        x = __ldg(reinterpret_cast<const uint32_t*>(G + (int64_t)gk * cols + gc));
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 4; q++)
+                            if (gc + q < cols) x |= (uint32_t)__ldg(G + (int64_t)gk * cols + gc + q) << (8 * q);
+                    }
+                }
+                w[h][i] = x;
             }
         }
 #pragma unroll
@@ -428,21 +497,22 @@ __device__ __forceinline__ void transpose_segment(const BatchK& k, const DevJob*
                 *reinterpret_cast<uint32_t*>(&tile[h][e / (TT / 4)][4 * (e % (TT / 4))]) = w[h][i];
             }
         __syncthreads();
-        // rows c0 .. c0 + 63 of G^T, 16 bytes (16 k) per thread and step (k is a multiple of 16)
+        // rows c0 .. c0 + 63 of G^T, 16 bytes (16 k) per thread and step; rows of KP
+        // (a multiple of 16) bytes, the padding kc .. KP - 1 zero
         for (int h = 0; h < nt; h++) {
             const int64_t t = t0 + h;
             const int k0 = (int)(t / nct) * TT, c0 = (int)(t % nct) * TT;
             for (int e = threadIdx.x; e < TT * TT / 16; e += THREADS) {
                 const int n = e / (TT / 16), kc = e % (TT / 16);
                 const int gc = c0 + n, gk = k0 + 16 * kc;
-                if (gc < cols && gk < K) {
+                if (gc < cols && gk < KP) {
                     uint32_t o[4];
 #pragma unroll
                     for (int q = 0; q < 4; q++)
                         o[q] = (uint32_t)tile[h][16 * kc + 4 * q][n] | ((uint32_t)tile[h][16 * kc + 4 * q + 1][n] << 8) |
                                ((uint32_t)tile[h][16 * kc + 4 * q + 2][n] << 16) |
                                ((uint32_t)tile[h][16 * kc + 4 * q + 3][n] << 24);
-                    *reinterpret_cast<uint4*>(GT + (int64_t)gc * K + gk) = make_uint4(o[0], o[1], o[2], o[3]);
+                    *reinterpret_cast<uint4*>(GT + (int64_t)gc * KP + gk) = make_uint4(o[0], o[1], o[2], o[3]);
                 }
             }
         }
@@ -458,6 +528,14 @@ __global__ void __launch_bounds__(THREADS) k_batch_entangle(BatchK k) {
         const DevJob* J = k.jobs + sg.job;
         if (sg.kind == SEG_TRANSPOSE) {
             transpose_segment(k, J, sg, tile);
+            continue;
+        }
+        if (sg.kind == SEG_ROWS) {
+            switch (J->M) {
+                case 3: ok &= entangle_rows<3>(k, J, sg); break;
+                case 4: ok &= entangle_rows<4>(k, J, sg); break;
+                default: ok &= entangle_rows<5>(k, J, sg); break;
+            }
             continue;
         }
         switch (J->M) {
@@ -655,12 +733,12 @@ static ne_status plan_batch(const ne_job* jobs, int32_t njobs, ne_batch_config c
         if (j.fault_begin < 0 || j.fault_end < j.fault_begin) return fail(NE_EINVAL, "job %d: fault range", i);
         int64_t K;
         if (j.kind == NE_JOB_GEMM) {
-            if (j.rows < 1 || j.cols < 8 || j.cols % 8 || j.k < 16 || j.k % 16 || j.k > 131056)
-                return fail(NE_EINVAL, "job %d: GEMM %dx%dx%d (k multiple of 16, cols multiple of 8)", i, j.rows, j.cols, j.k);
+            if (j.rows < 1 || j.cols < 1 || j.k < 1 || j.k > 131056)
+                return fail(NE_EINVAL, "job %d: GEMM %dx%dx%d (1 <= k <= 131056)", i, j.rows, j.cols, j.k);
             if (j.op_off % 4) return fail(NE_EINVAL, "job %d: op_off must be a multiple of 4", i);
             K = j.k;
         } else {
-            if (j.N < 64 || j.N % 64 || j.N > 65536) return fail(NE_EINVAL, "job %d: N=%d", i, j.N);
+            if (j.N < 2 || j.N > 65536) return fail(NE_EINVAL, "job %d: N=%d (2 <= N <= 65536)", i, j.N);
             K = j.N;
         }
         const int64_t amax = std::max((int64_t)std::abs((int64_t)j.cmin), (int64_t)std::abs((int64_t)j.cmax));
@@ -692,7 +770,8 @@ static ne_status plan_batch(const ne_job* jobs, int32_t njobs, ne_batch_config c
         d.MS = j.M * dg.S;
         d.rows = j.rows;
         d.cols = j.cols;
-        d.k = j.k;
+        d.k = j.kind == NE_JOB_GEMM ? (j.k + 15) / 16 * 16 : j.k;
+        d.kc = j.k;
         d.N = j.N;
         d.r = j.r;
         d.fuse = j.fuse;
@@ -703,12 +782,18 @@ static ne_status plan_batch(const ne_job* jobs, int32_t njobs, ne_batch_config c
         d.flag_off = j.flag_off;
         d.fault_begin = j.fault_begin;
         d.fault_end = j.fault_end;
-        d.npos = j.kind == NE_JOB_GEMM ? (int64_t)j.rows * j.k : (int64_t)j.N;
+        d.npos = j.kind == NE_JOB_GEMM ? (int64_t)j.rows * d.k : (int64_t)j.N;
         d.nout = j.kind == NE_JOB_GEMM ? (int64_t)j.rows * j.cols : (int64_t)j.N;
         flag_words = std::max(flag_words, j.flag_off + (d.nout + 31) / 32);
         const int32_t cabs = (int32_t)amax;
-        if (j.kind == NE_JOB_CCONV && cfg.ntt_min_n > 0 && j.N >= cfg.ntt_min_n &&
-            ntt_any_exact(j.M, j.plain ? 0 : l, j.N, cabs, j.plain != 0)) {
+        // the tensor tiles take whole Toeplitz blocks of 64: any other length
+        // runs on the exact transforms, as do lengths from ntt_min_n on
+        const bool ragged_n = j.kind == NE_JOB_CCONV && j.N % cconv::T != 0;
+        const bool exact = j.kind == NE_JOB_CCONV && ntt_any_exact(j.M, j.plain ? 0 : l, j.N, cabs, j.plain != 0);
+        if (ragged_n && !exact)
+            return fail(NE_ERANGE, "job %d: N=%d is not a multiple of 64 and its outputs leave the exact transforms' "
+                                   "range", i, j.N);
+        if (j.kind == NE_JOB_CCONV && exact && (ragged_n || (cfg.ntt_min_n > 0 && j.N >= cfg.ntt_min_n))) {
             // the exact transform path: no digit planes, segments or tiles
             NJob t;
             std::memset(&t, 0, sizeof(t));
@@ -743,23 +828,32 @@ static ne_status plan_batch(const ne_job* jobs, int32_t njobs, ne_batch_config c
         }
         d.plane_off = plane_bytes;
         plane_bytes = align256(plane_bytes + (int64_t)d.MS * d.npos);
-        n_segs += (d.npos + SEG - 1) / SEG;
-        if (build)
-            for (int64_t s0 = 0; s0 < d.npos; s0 += SEG)
-                segs.push_back(DevSeg{i, SEG_ENTANGLE, s0, std::min<int64_t>(SEG, d.npos - s0)});
+        if (j.kind == NE_JOB_GEMM && d.k != d.kc) {
+            // rows padded to 16: entangled row by row
+            const int64_t rps = std::max<int64_t>(1, SEG / d.k);
+            n_segs += (j.rows + rps - 1) / rps;
+            if (build)
+                for (int64_t r0 = 0; r0 < j.rows; r0 += rps)
+                    segs.push_back(DevSeg{i, SEG_ROWS, r0, std::min<int64_t>(rps, j.rows - r0)});
+        } else {
+            n_segs += (d.npos + SEG - 1) / SEG;
+            if (build)
+                for (int64_t s0 = 0; s0 < d.npos; s0 += SEG)
+                    segs.push_back(DevSeg{i, SEG_ENTANGLE, s0, std::min<int64_t>(SEG, d.npos - s0)});
+        }
         if (j.kind == NE_JOB_GEMM) {
             d.gt_off = plane_bytes;
-            plane_bytes = align256(plane_bytes + (int64_t)j.cols * j.k);
-            const int64_t ntt = (int64_t)((j.k + TT - 1) / TT) * ((j.cols + TT - 1) / TT);
+            plane_bytes = align256(plane_bytes + (int64_t)j.cols * d.k);
+            const int64_t ntt = (int64_t)((d.k + TT - 1) / TT) * ((j.cols + TT - 1) / TT);
             n_segs += (ntt + TT_PER_SEG - 1) / TT_PER_SEG;
             const int rt = (j.rows + bgemm::BM - 1) / bgemm::BM, ct = (j.cols + bgemm::BN - 1) / bgemm::BN;
             n_tiles_g += (int64_t)rt * ct;
             if (build) {
                 for (int64_t s0 = 0; s0 < ntt; s0 += TT_PER_SEG)
                     segs.push_back(DevSeg{i, SEG_TRANSPOSE, s0, std::min<int64_t>(TT_PER_SEG, ntt - s0)});
-                gjobs.push_back(GemmJob{i, rt, ct, (int64_t)d.MS * bgemm::BM * bgemm::BN * j.k});
+                gjobs.push_back(GemmJob{i, rt, ct, (int64_t)d.MS * bgemm::BM * bgemm::BN * d.k});
             }
-            mma_ops += 2LL * d.MS * rt * bgemm::BM * ct * bgemm::BN * j.k;
+            mma_ops += 2LL * d.MS * rt * bgemm::BM * ct * bgemm::BN * d.k;
             useful += 2LL * j.M * j.rows * j.cols * j.k;
         } else {
             const int NB = j.N / cconv::T;

@@ -53,7 +53,8 @@ __device__ __forceinline__ void raw_fields(const CconvArgs& a, int64_t b, cconv:
     for (int i = 0; i < 4; i++) t.raw_byte[i] = a.raw_byte[i];
 }
 
-template <int NTW, int MT, int LD>
+// IX: cconv::IX_CIRC for N a multiple of 64, cconv::IX_RAGGED otherwise
+template <int NTW, int MT, int LD, int IX>
 __global__ void __launch_bounds__(cconv::THREADS, (NTW <= 6 ? 4 : (NTW <= 10 ? 3 : 2)))
     k_cconv_digits(CconvArgs a, int64_t b_off) {
     extern __shared__ __align__(128) uint8_t smem[];
@@ -63,7 +64,7 @@ __global__ void __launch_bounds__(cconv::THREADS, (NTW <= 6 ? 4 : (NTW <= 10 ? 3
     t.planes = a.planes + b * a.MS * N;
     t.g = a.g + b * N;
     t.out = a.out + b * a.M * N;
-    t.flags = a.flags ? a.flags + b * (N / 32) : nullptr;
+    t.flags = a.flags ? a.flags + b * ((N + 31) / 32) : nullptr;
     t.nflag = a.nflag;
     fault_fields(a, b, t);
     t.N = (int)N;
@@ -77,9 +78,10 @@ __global__ void __launch_bounds__(cconv::THREADS, (NTW <= 6 ? 4 : (NTW <= 10 ? 3
 #pragma unroll
     for (int i = 0; i < NE_MAX_DIGITS; i++) t.shift[i] = a.shift[i];
     raw_fields(a, b, t);
-    const int NB = (int)(N / cconv::T);
+    t.lin_n = t.lin_K = (int)N;
+    const int NB = (int)((N + cconv::T - 1) / cconv::T);
     const int p0 = blockIdx.x * cconv::NPB;
-    cconv::tile<NTW, MT, LD>(t, smem, p0, min(cconv::NPB, NB - p0));
+    cconv::tile<NTW, MT, LD, IX>(t, smem, p0, min(cconv::NPB, NB - p0));
 }
 
 // The hybrid tile (tensor pipe + dp4a pipe) for groups of 9..16 blocks.
@@ -167,34 +169,46 @@ ne_status launch_hybrid_variant(int var, const CconvArgs& a, int64_t batch, cuda
     }
 }
 
-template <int NTW, int MT, int LD>
-ne_status launch(const CconvArgs& a, int64_t batch, cudaStream_t s) {
+template <int NTW, int MT, int LD, int IX>
+ne_status launch_ix(const CconvArgs& a, int64_t batch, cudaStream_t s) {
     const int smem = cconv::smem_bytes(a.MS);
     static bool attr_set[64] = {false};
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-        if (cudaFuncSetAttribute(k_cconv_digits<NTW, MT, LD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if (cudaFuncSetAttribute(k_cconv_digits<NTW, MT, LD, IX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  cconv::smem_bytes(16)) != cudaSuccess)
             return check_launch("ne_cconv_digits: shared-memory attribute");
         attr_set[dev] = true;
     }
-    const int NB = (int)(a.N / cconv::T);
+    const int NB = (int)((a.N + cconv::T - 1) / cconv::T);
     for (int64_t b0 = 0; b0 < batch; b0 += 65535) {
         const int64_t nb = batch - b0 < 65535 ? batch - b0 : 65535;
         dim3 grid((NB + cconv::NPB - 1) / cconv::NPB, (unsigned)nb);
-        k_cconv_digits<NTW, MT, LD><<<grid, cconv::THREADS, smem, s>>>(a, b0);
+        k_cconv_digits<NTW, MT, LD, IX><<<grid, cconv::THREADS, smem, s>>>(a, b0);
         ne_status st = check_launch("ne_cconv_digits");
         if (st) return st;
     }
     return NE_OK;
 }
 
+// the aligned block form when N is a multiple of 64 and the streams start
+// 16-byte aligned, else the ragged form
+template <int NTW, int MT, int LD>
+ne_status launch(const CconvArgs& a, int64_t batch, cudaStream_t s) {
+    const void* src = LD == cconv::LD_PLANES ? (const void*)a.planes
+                      : (LD == cconv::LD_RAW ? (const void*)a.craw : (const void*)a.cwords);
+    if (a.N % cconv::T == 0 && aligned(src, 16)) return launch_ix<NTW, MT, LD, cconv::IX_CIRC>(a, batch, s);
+    return launch_ix<NTW, MT, LD, cconv::IX_RAGGED>(a, batch, s);
+}
+
 template <int LD>
 ne_status dispatch(const CconvArgs& a, int64_t batch, cudaStream_t s) {
     const int64_t NB = a.N / cconv::T;
     const int var = hybrid_variant(NB, a.MS);
-    if (var && NB <= 16) {
+    const void* src = LD == cconv::LD_PLANES ? (const void*)a.planes
+                      : (LD == cconv::LD_RAW ? (const void*)a.craw : (const void*)a.cwords);
+    if (var && NB <= 16 && a.N % cconv::T == 0 && aligned(src, 16)) {
         ne_status hs = NE_EINVAL;
         if (a.M == 3 && a.MS == 6) hs = launch_hybrid_variant<3, 6, LD>(var, a, batch, s);
         else if (a.M == 4 && a.MS == 8) hs = launch_hybrid_variant<4, 8, LD>(var, a, batch, s);
@@ -227,8 +241,7 @@ ne_status common_args(const ne_params& p, const ne_digits& dg, int64_t batch, in
     if ((st = validate_digits(dg))) return st;
     if ((st = validate_faults(faults, who))) return st;
     if (batch < 0) return fail(NE_EINVAL, "%s: batch < 0", who);
-    if (N < 64 || N % 64 != 0 || N > 65536)
-        return fail(NE_EINVAL, "%s: N=%lld must be a multiple of 64 in [64, 65536]", who, (long long)N);
+    if (N < 1 || N > 65536) return fail(NE_EINVAL, "%s: N=%lld must be in [1, 65536]", who, (long long)N);
     if (fuse < NE_FUSE_NONE || fuse > NE_FUSE_RECOVER) return fail(NE_EINVAL, "%s: fuse=%d", who, fuse);
     if (r < 0 || r >= p.M) return fail(NE_EINVAL, "%s: r=%d", who, r);
     if (p.M * dg.S > 16) return fail(NE_EINVAL, "%s: M*S=%d exceeds 16 planes", who, p.M * dg.S);
@@ -271,7 +284,7 @@ extern "C" ne_status ne_cconv_digits(ne_params p, ne_digits dg, const int8_t* pl
     if (nf && cudaMemsetAsync(nf, 0, sizeof(*nf), s) != cudaSuccess) return check_launch("ne_cconv_digits: reset");
     if (batch == 0) return NE_OK;
     if (!planes || !g || !out) return fail(NE_EINVAL, "ne_cconv_digits: null pointer");
-    if (!aligned(planes, 16) || !aligned(out, 8)) return fail(NE_EINVAL, "ne_cconv_digits: planes must be 16-byte aligned");
+    if (!aligned(out, 8)) return fail(NE_EINVAL, "ne_cconv_digits: out must be 8-byte aligned");
     CconvArgs a;
     fill_args(a, p, dg, g, out, flags, nf, N, fuse, r, faults);
     a.planes = planes;
@@ -311,7 +324,7 @@ extern "C" ne_status ne_cconv_entangled(ne_params p, ne_digits dg, const int32_t
     if (nf && cudaMemsetAsync(nf, 0, sizeof(*nf), s) != cudaSuccess) return check_launch("ne_cconv_entangled: reset");
     if (batch == 0) return NE_OK;
     if (!c || !g || !out) return fail(NE_EINVAL, "ne_cconv_entangled: null pointer");
-    if (!aligned(c, 16) || !aligned(out, 8)) return fail(NE_EINVAL, "ne_cconv_entangled: c must be 16-byte aligned");
+    if (!aligned(c, 4) || !aligned(out, 8)) return fail(NE_EINVAL, "ne_cconv_entangled: c, out must be aligned");
     CconvArgs a;
     fill_args(a, p, dg, g, out, flags, nf, N, fuse, r, faults);
     a.craw = c;
@@ -346,7 +359,7 @@ ne_status cconv_s8slice(ne_params p, ne_digits dg, const int64_t* words, const i
     if (nf && cudaMemsetAsync(nf, 0, sizeof(*nf), s) != cudaSuccess) return check_launch("ne_cconv: reset");
     if (batch == 0) return NE_OK;
     if (!words || !g || !out) return fail(NE_EINVAL, "ne_cconv: null pointer");
-    if (!aligned(words, 16) || !aligned(out, 8)) return fail(NE_EINVAL, "ne_cconv: eps must be 16-byte aligned");
+    if (!aligned(words, 8) || !aligned(out, 8)) return fail(NE_EINVAL, "ne_cconv: eps and out must be 8-byte aligned");
     CconvArgs a;
     fill_args(a, p, dg, g, out, flags, nf, N, fuse, r, faults);
     uint64_t stored = 0;

@@ -79,10 +79,11 @@ struct TileArgs {
     // (y & w_nsmask) != w_nswant is outside the plan and sets *status = NE_ERANGE
     const int64_t* cwords;
     uint64_t w_nsmask, w_nswant;
-    // linear form (LD_LINEAR): the raw streams craw are [M][lin_n], g has
-    // lin_K taps, and the outputs [M][N] are the full linear convolution,
-    // N = lin_n + lin_K - 1 (inputs outside [0, lin_n) and taps outside
-    // [0, lin_K) are zero)
+    // bounded indexing (IX_LINEAR, IX_RAGGED): the inputs are [M][lin_n]
+    // (inputs outside [0, lin_n) zero) and g has lin_K taps; IX_LINEAR: the
+    // outputs [M][N] are the full linear convolution, N = lin_n + lin_K - 1;
+    // IX_RAGGED: the circular convolution of length N = lin_n = lin_K, N not
+    // a multiple of T
     int lin_n, lin_K;
 };
 
@@ -90,7 +91,12 @@ struct TileArgs {
 constexpr int LD_PLANES = 0;   // digit planes in memory (cp.async)
 constexpr int LD_RAW = 1;      // the raw int32 streams: Eq. 16 and the split while loading
 constexpr int LD_WORDS = 2;    // the entangled int64 words: the split while loading
-constexpr int LD_LINEAR = 3;   // as LD_RAW, for the linear convolution of long streams
+
+// how output blocks meet input blocks
+constexpr int IX_CIRC = 0;     // circular, N a multiple of T: input block (p - u) mod NB, u < NB
+constexpr int IX_LINEAR = 1;   // linear: input block p - u, G_u[q][t] = g[T u + q - t] (0 outside [0, K))
+constexpr int IX_RAGGED = 2;   // circular, any N: input block p - d for the signed block offsets d
+                               // the tile needs, G_d[q][t] = g[(T d + q - t) mod N]
 
 __device__ __forceinline__ int64_t shl64(int64_t x, int s) { return (int64_t)((uint64_t)x << s); }
 
@@ -307,13 +313,86 @@ __device__ __forceinline__ void load_window(const TileArgs& a, uint8_t* sig, int
     }
 }
 
-// The linear form's window: input blocks first .. first + WB - 1 of the raw
-// streams (no wrap), every position outside [0, lin_n) zero.  Work items as
-// in load_window<LD_RAW>; an item entirely inside a stream whose rows start
-// 16-byte aligned takes the vector loads, the others element by element.
-__device__ __forceinline__ void load_window_linear(const TileArgs& a, uint8_t* sig, int WB, int first, int nthr) {
-    const int M = a.M, S = a.S, MS = a.MS, n = a.lin_n;
-    const bool vec_ok = (n & 3) == 0;
+// The window of the bounded indexings: input blocks first .. first + WB - 1
+// (no wrap), every position outside [0, n) zero -- for the raw streams the
+// word 0, for words and digit planes digits 0.  An item (block, stream or
+// plane, 16 positions) entirely inside its stream whose row starts aligned
+// takes the vector loads, the others element by element.
+template <int LD>
+__device__ __forceinline__ void load_window_bounded(const TileArgs& a, uint8_t* sig, int WB, int first, int n,
+                                                    int nthr) {
+    const int M = a.M, S = a.S, MS = a.MS;
+    auto al16 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
+    if constexpr (LD == LD_PLANES) {
+        const bool vec_ok = (n & 15) == 0 && al16(a.planes);
+        for (int e = threadIdx.x; e < WB * MS * 4; e += nthr) {
+            const int c16 = e & 3, row = e >> 2;
+            const int blk_rel = row / MS, ms = row - blk_rel * MS;
+            const int64_t pos = (int64_t)(first + blk_rel) * T + c16 * 16;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            const bool lost = a.fuse == NE_FUSE_RECOVER && ms / S == a.r;
+            if (!lost && pos + 16 > 0 && pos < n) {
+                const int8_t* src = a.planes + (int64_t)ms * n + pos;
+                if (vec_ok && pos >= 0 && pos + 16 <= n) {
+                    v = __ldg(reinterpret_cast<const uint4*>(src));
+                } else {
+                    uint32_t w[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+                    for (int b = 0; b < 16; b++)
+                        if (pos + b >= 0 && pos + b < n) w[b >> 2] |= (uint32_t)(uint8_t)__ldg(src + b) << (8 * (b & 3));
+                    v = make_uint4(w[0], w[1], w[2], w[3]);
+                }
+            }
+            *reinterpret_cast<uint4*>(sig + row * ROWB + c16 * 16) = v;
+        }
+        return;
+    } else if constexpr (LD == LD_WORDS) {
+        const bool vec_ok = (n & 1) == 0 && al16(a.cwords);
+        bool bad = false;
+        for (int e = threadIdx.x; e < WB * M * 4; e += nthr) {
+            const int c16 = e & 3, rowm = e >> 2;
+            const int blk_rel = rowm / M, m = rowm - blk_rel * M;
+            uint8_t* dst = sig + (blk_rel * MS + m * S) * ROWB + c16 * 16;
+            const int64_t pos = (int64_t)(first + blk_rel) * T + c16 * 16;
+            uint64_t y[16];
+#pragma unroll
+            for (int q = 0; q < 16; q++) y[q] = 0x8080808080808080ull;     // the word 0: digits 0
+            const bool lost = a.fuse == NE_FUSE_RECOVER && m == a.r;
+            if (!lost && pos + 16 > 0 && pos < n) {
+                const int64_t* src = a.cwords + (int64_t)m * n + pos;
+                if (vec_ok && pos >= 0 && pos + 16 <= n) {
+#pragma unroll
+                    for (int q = 0; q < 8; q++) {
+                        const longlong2 v = __ldg(reinterpret_cast<const longlong2*>(src) + q);
+                        y[2 * q] += (uint64_t)v.x;
+                        y[2 * q + 1] += (uint64_t)v.y;
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 16; q++)
+                        if (pos + q >= 0 && pos + q < n) y[q] += (uint64_t)__ldg(src + q);
+                }
+#pragma unroll
+                for (int q = 0; q < 16; q++) bad |= (y[q] & a.w_nsmask) != a.w_nswant;
+            }
+#pragma unroll
+            for (int s = 0; s < NE_MAX_DIGITS; s++) {
+                if (s >= S) break;
+                const int sh = a.shift[s];
+                uint32_t w[4];
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const uint32_t v0 = (uint32_t)(y[4 * q] >> sh), v1 = (uint32_t)(y[4 * q + 1] >> sh);
+                    const uint32_t v2 = (uint32_t)(y[4 * q + 2] >> sh), v3 = (uint32_t)(y[4 * q + 3] >> sh);
+                    w[q] = __byte_perm(__byte_perm(v0, v1, 0x0040), __byte_perm(v2, v3, 0x0040), 0x5410) ^ 0x80808080u;
+                }
+                *reinterpret_cast<uint4*>(dst + s * ROWB) = make_uint4(w[0], w[1], w[2], w[3]);
+            }
+        }
+        if (bad && a.status) atomicExch(a.status, (int32_t)NE_ERANGE);
+        return;
+    } else {
+    const bool vec_ok = (n & 3) == 0 && al16(a.craw);
     uint32_t worst = 0;
     for (int e = threadIdx.x; e < WB * M * 4; e += nthr) {
         const int c16 = e & 3, rowm = e >> 2;
@@ -383,21 +462,25 @@ __device__ __forceinline__ void load_window_linear(const TileArgs& a, uint8_t* s
         }
     }
     if (worst > (uint32_t)a.raw_hi - (uint32_t)a.raw_lo && a.status) atomicExch(a.status, (int32_t)NE_ERANGE);
+    }
 }
 
 // The tile of output blocks [p0, p0 + npb) of one group; all 256 threads of
 // the block take part.  smem: smem_bytes(MS) bytes, 128-byte aligned.
-// LD_LINEAR: the shifts u run over the kernel's NU = (K + 62) / 64 + 1 blocks
+// IX_LINEAR: the shifts u run over the kernel's NU = (K + 62) / 64 + 1 blocks
 // of G_u[q][t] = g[T u + q - t] (zero outside [0, K)) and input block p - u
 // is zero outside the stream, so each output block sums NU products instead
 // of NB (Sec. IV-A: a long stream needs only the blocks the kernel reaches).
-template <int NTW, int MT, int LD = LD_PLANES>
+// IX_RAGGED: the block offsets d = p - p' of the tile's outputs and every
+// input block, d = ubase + u with ubase = p0 - NB + 1 and u < NB + npb - 1
+// (each output block meets NB of them; the others are zero rows).
+template <int NTW, int MT, int LD = LD_PLANES, int IX = IX_CIRC>
 __device__ __forceinline__ void tile(const TileArgs& a, uint8_t* smem, int p0, int npb) {
     const int MS = a.MS;
     const int N = a.N;
-    const int NB = N / T;
-    constexpr bool LIN = LD == LD_LINEAR;
-    const int NU = LIN ? (a.lin_K + 62) / T + 1 : NB;   // shifts u
+    const int NB = IX == IX_RAGGED ? (N + T - 1) / T : N / T;
+    const int NU = IX == IX_LINEAR ? (a.lin_K + 62) / T + 1 : (IX == IX_RAGGED ? NB + npb - 1 : NB);   // shifts u
+    const int ubase = IX == IX_RAGGED ? p0 - NB + 1 : 0;
     const int uch = min(UCH, NU);
     const int WB = npb + uch - 1;
     const int cols = npb * MS;
@@ -426,12 +509,12 @@ __device__ __forceinline__ void tile(const TileArgs& a, uint8_t* smem, int p0, i
         const int uc = min(uch, NU - u0);
         // digit rows of input blocks (p0 - (u0 + uch - 1) + blk_rel), mod NB for
         // the circular convolution
-        if constexpr (LIN) load_window_linear(a, sig, WB, p0 - (u0 + uch - 1), THREADS);
-        else load_window<LD>(a, sig, WB, p0 - (u0 + uch - 1), NB, THREADS);
+        if constexpr (IX == IX_CIRC) load_window<LD>(a, sig, WB, p0 - (u0 + uch - 1), NB, THREADS);
+        else load_window_bounded<LD>(a, sig, WB, p0 - ubase - (u0 + uch - 1), a.lin_n, THREADS);
         cp_async_commit();
-        // g copies: copy rr, byte z holds g[(T (u0 + uch) - (z + rr - PADB)) mod N]
+        // g copies: copy rr, byte z holds g[(T (ubase + u0 + uch) - (z + rr - PADB)) mod N]
         // (linear: g at that index, 0 outside [0, K))
-        const int top = T * (u0 + uch);
+        const int top = T * (ubase + u0 + uch);
         for (int e = tid; e < 4 * (GW / 4); e += THREADS) {
             const int rr = e / (GW / 4), zw = e - rr * (GW / 4);
             uint32_t w = 0;
@@ -439,7 +522,7 @@ __device__ __forceinline__ void tile(const TileArgs& a, uint8_t* smem, int p0, i
             for (int k = 0; k < 4; k++) {
                 int idx = top - (4 * zw + k + rr - PADB);
                 uint32_t gv;
-                if constexpr (LIN) {
+                if constexpr (IX == IX_LINEAR) {
                     gv = (idx >= 0 && idx < a.lin_K) ? (uint32_t)(uint8_t)__ldg(a.g + idx) : 0u;
                 } else {
                     idx %= N;

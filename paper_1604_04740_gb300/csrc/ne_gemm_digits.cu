@@ -170,7 +170,9 @@ __device__ __forceinline__ void gemm_epilogue(const GemmArgs& a, const int32_t* 
     }
 }
 
-template <int MT, bool WORDS>
+// RAGGED: k not a multiple of 16, cols not of 4, or an operand not aligned for
+// the vector loads; the loads then go element by element
+template <int MT, bool WORDS, bool RAGGED>
 __global__ void __launch_bounds__(512, 1) k_gemm_digits(GemmArgs a) {
     extern __shared__ __align__(128) uint8_t smem[];
     const int MS = a.MS;
@@ -198,7 +200,15 @@ __global__ void __launch_bounds__(512, 1) k_gemm_digits(GemmArgs a) {
                 const int gi = row0 + r, gk = k0 + 16 * c16;
                 const bool ok = gi < rows && gk < K && !((a.fuse == NE_FUSE_RECOVER) && m == a.r);
                 uint64_t y[16];
-                if (ok) {
+                if (ok && RAGGED) {
+                    // rows of any length: word by word, past k the word 0
+                    const int64_t* src = a.words + ((int64_t)m * rows + gi) * K + gk;
+#pragma unroll
+                    for (int q = 0; q < 16; q++) {
+                        y[q] = (gk + q < K ? (uint64_t)__ldg(src + q) : 0ull) + 0x8080808080808080ull;
+                        bad |= (y[q] & a.ns_mask) != a.ns_want;
+                    }
+                } else if (ok) {
                     const longlong2* src =
                         reinterpret_cast<const longlong2*>(a.words + ((int64_t)m * rows + gi) * K + gk);
 #pragma unroll
@@ -224,7 +234,19 @@ __global__ void __launch_bounds__(512, 1) k_gemm_digits(GemmArgs a) {
             const int gi = row0 + r, gk = k0 + 16 * c16;
             const bool ok = gi < rows && gk < K && !((a.fuse == NE_FUSE_RECOVER) && (pl / a.S == a.r));
             const int8_t* src = a.planes + ((int64_t)pl * rows + (ok ? gi : 0)) * K + (ok ? gk : 0);
-            cp_async16(As_s + ((stage * MS + pl) * BM + r) * RB + 16 * c16, src, ok ? 16 : 0);
+            if constexpr (RAGGED) {
+                // rows that do not start 16-byte aligned: byte by byte, past k zero
+                uint32_t w[4] = {0u, 0u, 0u, 0u};
+                if (ok) {
+#pragma unroll
+                    for (int b = 0; b < 16; b++)
+                        if (gk + b < K) w[b >> 2] |= (uint32_t)(uint8_t)__ldg(src + b) << (8 * (b & 3));
+                }
+                *reinterpret_cast<uint4*>(As + ((stage * MS + pl) * BM + r) * RB + 16 * c16) =
+                    make_uint4(w[0], w[1], w[2], w[3]);
+            } else {
+                cp_async16(As_s + ((stage * MS + pl) * BM + r) * RB + 16 * c16, src, ok ? 16 : 0);
+            }
         }
     };
     // G loads: 4x4 byte blocks (kb, nb) -> registers
@@ -242,8 +264,18 @@ __global__ void __launch_bounds__(512, 1) k_gemm_digits(GemmArgs a) {
 #pragma unroll
                 for (int q = 0; q < 4; q++) {
                     const int gk = k0 + 4 * kb + q;
-                    if (gk < K && gn < cols)
-                        reg[h][q] = __ldg(reinterpret_cast<const uint32_t*>(a.G + (int64_t)gk * cols + gn));
+                    if (gk < K && gn < cols) {
+                        if constexpr (RAGGED) {
+                            // rows of G of any length: byte by byte, past cols zero
+                            uint32_t x = 0;
+#pragma unroll
+                            for (int c = 0; c < 4; c++)
+                                if (gn + c < cols) x |= (uint32_t)(uint8_t)__ldg(a.G + (int64_t)gk * cols + gn + c) << (8 * c);
+                            reg[h][q] = x;
+                        } else {
+                            reg[h][q] = __ldg(reinterpret_cast<const uint32_t*>(a.G + (int64_t)gk * cols + gn));
+                        }
+                    }
                 }
             }
         }
@@ -333,30 +365,37 @@ __global__ void __launch_bounds__(512, 1) k_gemm_digits(GemmArgs a) {
     gemm_epilogue<MT>(a, stash, row0, col0);
 }
 
-template <int MT, bool WORDS>
+template <int MT, bool WORDS, bool RAGGED>
 ne_status launch(const GemmArgs& a, cudaStream_t s) {
     static bool attr_set[64] = {false};
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-        if (cudaFuncSetAttribute(k_gemm_digits<MT, WORDS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if (cudaFuncSetAttribute(k_gemm_digits<MT, WORDS, RAGGED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  smem_bytes(16)) != cudaSuccess)
             return check_launch("ne_gemm_digits: shared-memory attribute");
         attr_set[dev] = true;
     }
     dim3 grid((a.cols + BN - 1) / BN, (a.rows + BM - 1) / BM);
-    k_gemm_digits<MT, WORDS><<<grid, a.MS * 32, smem_bytes(a.MS), s>>>(a);
+    k_gemm_digits<MT, WORDS, RAGGED><<<grid, a.MS * 32, smem_bytes(a.MS), s>>>(a);
     return check_launch("ne_gemm_digits");
+}
+
+template <bool WORDS, bool RAGGED>
+ne_status dispatch_m(const GemmArgs& a, cudaStream_t s) {
+    switch (a.M) {
+        case 3: return launch<3, WORDS, RAGGED>(a, s);
+        case 4: return launch<4, WORDS, RAGGED>(a, s);
+        case 5: return launch<5, WORDS, RAGGED>(a, s);
+        default: return launch<0, WORDS, RAGGED>(a, s);
+    }
 }
 
 template <bool WORDS>
 ne_status dispatch(const GemmArgs& a, cudaStream_t s) {
-    switch (a.M) {
-        case 3: return launch<3, WORDS>(a, s);
-        case 4: return launch<4, WORDS>(a, s);
-        case 5: return launch<5, WORDS>(a, s);
-        default: return launch<0, WORDS>(a, s);
-    }
+    const void* A = WORDS ? (const void*)a.words : (const void*)a.planes;
+    const bool ragged = a.k % 16 != 0 || a.cols % 4 != 0 || !aligned(A, 16) || !aligned(a.G, 4);
+    return ragged ? dispatch_m<WORDS, true>(a, s) : dispatch_m<WORDS, false>(a, s);
 }
 
 
@@ -370,8 +409,7 @@ ne_status gemm_tensor(const char* who, ne_params p, ne_digits dg, const int8_t* 
     if ((st = validate_digits(dg))) return st;
     if ((st = validate_faults(faults, who))) return st;
     if (rows < 0 || cols < 0 || k < 0) return fail(NE_EINVAL, "%s: negative size", who);
-    if (k % 16 != 0 || k > KMAX) return fail(NE_EINVAL, "%s: k=%d must be a multiple of 16, <= %d", who, k, KMAX);
-    if (cols % 8 != 0) return fail(NE_EINVAL, "%s: cols=%d must be a multiple of 8", who, cols);
+    if (k > KMAX) return fail(NE_EINVAL, "%s: k=%d exceeds %d", who, k, KMAX);
     if (fuse < NE_FUSE_NONE || fuse > NE_FUSE_RECOVER) return fail(NE_EINVAL, "%s: fuse=%d", who, fuse);
     if (r < 0 || r >= p.M) return fail(NE_EINVAL, "%s: r=%d", who, r);
     const int MS = p.M * dg.S;
@@ -382,8 +420,8 @@ ne_status gemm_tensor(const char* who, ne_params p, ne_digits dg, const int8_t* 
         return check_launch("digit-plane product: reset count");
     if (rows == 0 || cols == 0) return NE_OK;
     if ((!planes && !words) || !G || !out) return fail(NE_EINVAL, "%s: null pointer", who);
-    if (!aligned(planes ? (const void*)planes : (const void*)words, 16) || !aligned(G, 4) || !aligned(out, 8))
-        return fail(NE_EINVAL, "%s: the streams must be 16-byte and G 4-byte aligned", who);
+    if (!aligned(out, 8) || (words && !aligned(words, 8)))
+        return fail(NE_EINVAL, "%s: out (and eps) must be 8-byte aligned", who);
     GemmArgs a;
     a.planes = planes;
     a.G = G;

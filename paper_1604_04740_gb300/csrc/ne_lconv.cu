@@ -10,7 +10,7 @@
 // the kernel blocks G_u[q][t] = g[64 u + q - t], so no output is computed
 // twice and nothing is discarded; Eq. 16 and the digit split are done while
 // the window loads and the extraction/check of Eq. 17-20 / Eq. 24 runs in
-// the epilogue (ne_cconv_tile.cuh, LD_LINEAR).
+// the epilogue (ne_cconv_tile.cuh, IX_LINEAR).
 #include "ne_cconv_tile.cuh"
 #include "ne_entangle.cuh"
 
@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(cconv::THREADS, (NTW <= 6 ? 4 : (NTW <= 10 ? 3
     t.lin_K = a.K;
     const int NBo = (a.n_out + cconv::T - 1) / cconv::T;
     const int p0 = blockIdx.x * cconv::NPB;
-    cconv::tile<NTW, MT, cconv::LD_LINEAR>(t, smem, p0, min(cconv::NPB, NBo - p0));
+    cconv::tile<NTW, MT, cconv::LD_RAW, cconv::IX_LINEAR>(t, smem, p0, min(cconv::NPB, NBo - p0));
 }
 
 template <int NTW, int MT>

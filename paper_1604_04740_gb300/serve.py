@@ -102,8 +102,8 @@ def work_estimate(T, ntt_min_n: int) -> np.ndarray:
     """Rough device work of each request of table T, in int8 tensor-op
     equivalents: 2 M S m n k for a product and 2 M S N^2 for a convolution on
     tensor tiles (S = 2 digit planes per stream for the entangled form, 1 for
-    the plain one), and 280 (2 M + 1) N log2 N for a convolution of N >=
-    ntt_min_n on the transform path (the factor from the ragged batch, where
+    the plain one), and 280 (2 M + 1) N log2 N for a convolution on the
+    transform path (N >= ntt_min_n, or N not a multiple of 64) (the factor from the ragged batch, where
     528 such convolutions take as long as 4.1e11 tile ops)."""
     S = np.where(T.plain != 0, 1.0, 2.0)
     M = T.M.astype(np.float64)
@@ -111,7 +111,7 @@ def work_estimate(T, ntt_min_n: int) -> np.ndarray:
     gemm = 2.0 * M * S * T.rows * T.cols * T.k
     tiles = 2.0 * M * S * N * N
     ntt = 280.0 * (2.0 * M + 1.0) * N * np.log2(np.maximum(N, 2.0))
-    conv = np.where((ntt_min_n > 0) & (T.N >= ntt_min_n), ntt, tiles)
+    conv = np.where(((ntt_min_n > 0) & (T.N >= ntt_min_n)) | (T.N % 64 != 0), ntt, tiles)
     return np.where(T.kind == ne.NE_JOB_GEMM, gemm, conv)
 
 

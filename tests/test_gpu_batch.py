@@ -229,11 +229,37 @@ def test_out_of_range_inputs_are_reported(mods):
 
 def test_plan_rejects_bad_jobs(mods):
     B, ne = mods
-    for bad in (B.JobSpec(ne.NE_JOB_GEMM, 3, rows=8, cols=12, k=16), B.JobSpec(ne.NE_JOB_GEMM, 3, rows=8, cols=16, k=20),
-                B.JobSpec(ne.NE_JOB_CCONV, 3, N=100), B.JobSpec(ne.NE_JOB_CCONV, 6, N=64)):
+    for bad in (B.JobSpec(ne.NE_JOB_GEMM, 3, rows=0, cols=12, k=16), B.JobSpec(ne.NE_JOB_GEMM, 3, rows=8, cols=16, k=131057),
+                B.JobSpec(ne.NE_JOB_CCONV, 3, N=1), B.JobSpec(ne.NE_JOB_CCONV, 3, N=65537),
+                B.JobSpec(ne.NE_JOB_CCONV, 6, N=64)):
         b = B.Batch([bad], generate=False)
         with pytest.raises(ne.NEError):
             b.plan(B.default_config())
+
+
+def test_ragged_sizes_run_as_drawn(mods):
+    """Products with k not a multiple of 16 and cols of any size (rows padded
+    to 16 in the digit planes) and convolutions whose N is not a multiple of
+    64 (on the exact transforms), against the oracle under faults."""
+    B, ne = mods
+    G, C, R = ne.NE_JOB_GEMM, ne.NE_JOB_CCONV, ne.NE_FUSE_RECOVER
+    specs = [B.JobSpec(G, 3, rows=17, cols=13, k=37), B.JobSpec(G, 4, rows=40, cols=70, k=100),
+             B.JobSpec(G, 5, rows=1, cols=1, k=1), B.JobSpec(G, 3, rows=33, cols=5, k=250, fuse=R, r=2),
+             B.JobSpec(G, 4, rows=64, cols=64, k=48), B.JobSpec(C, 3, N=100), B.JobSpec(C, 4, N=1000),
+             B.JobSpec(C, 5, N=3, fuse=R, r=1), B.JobSpec(C, 3, N=4099), B.JobSpec(C, 3, N=256)]
+    specs += B.mixed_jobs(31, 24, mnk=(8, 300), conv=(2, 3000), recover_frac=0.2)
+    assert any(s.kind == G and s.k % 16 for s in specs) and any(s.kind == C and s.N % 64 for s in specs)
+    b = B.Batch(specs, seed=12, fault_rate=3e-3)
+    b.plan(B.default_config())
+    b.run()
+    torch.cuda.synchronize()
+    assert int(b.status.item()) == 0
+    for j, s in enumerate(b.specs):
+        dh, fl = oracle_job(b, j, ne)
+        got = b.job_output(j).cpu().numpy().reshape(s.M, -1)
+        assert (got == dh).all(), f"job {j} ({s})"
+        if fl is not None:
+            assert (unpack_flags(b.job_flags(j).cpu().numpy(), 1, s.positions_out)[0] == fl).all(), f"job {j}"
 
 
 def test_staged_plan_uploads_the_same_tables(mods):
@@ -245,7 +271,8 @@ def test_staged_plan_uploads_the_same_tables(mods):
     torch.cuda.synchronize()
     out0, fl0, nf0 = b.out.clone(), b.flags.clone(), int(b.nflag.item())
     info = ne.ne_batch_plan(b.jobs, cfg)
-    assert info.table_bytes > 0 and info.ntransform == 1
+    on_transforms = sum(1 for s in b.specs if s.kind == ne.NE_JOB_CCONV and (s.N % 64 or s.N >= 4096))
+    assert info.table_bytes > 0 and info.ntransform == on_transforms >= 2
     with pytest.raises(ne.NEError):
         ne.ne_batch_plan(b.jobs, cfg, b.ws_view, staging=torch.empty(info.table_bytes - 1, dtype=torch.uint8).pin_memory())
     with pytest.raises(ValueError):

@@ -105,10 +105,15 @@ def test_cconv_digits_extreme_values(ne):
 def test_cconv_digits_rejects_bad_sizes(ne):
     p = ne.params(3, 16)
     dg = ne.ne_plan_digits(16)
-    planes = torch.zeros((1, 3, dg.S, 100), dtype=torch.int8, device=DEV)
-    g = torch.zeros((1, 100), dtype=torch.int8, device=DEV)
+    N = 65537                                   # beyond the int32 accumulation bound of the tiles
+    planes = torch.zeros((1, 3, dg.S, N), dtype=torch.int8, device=DEV)
+    g = torch.zeros((1, N), dtype=torch.int8, device=DEV)
     with pytest.raises(ne.NEError):
         ne.ne_cconv_digits(p, dg, planes, g)
+    dg6 = ne.digits((0, 8, 16, 24, 32, 40))      # 3 x 6 = 18 digit planes, above the 16 a tile holds
+    planes = torch.zeros((1, 3, 6, 128), dtype=torch.int8, device=DEV)
+    with pytest.raises(ne.NEError):
+        ne.ne_cconv_digits(p, dg6, planes, torch.zeros((1, 128), dtype=torch.int8, device=DEV))
 
 
 # ---- matrix product ---------------------------------------------------------------------
