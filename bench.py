@@ -355,7 +355,8 @@ def run_ours(args, rank, world, local_rank):
         launches_per_step = 1
         mma_ops_per_launch = 2 * G * M * dg.S * N * N
         dominant = "ne_cconv_entangled"
-        dom_src = ("ne_cconv_digits.cu", "ne_cconv_tile.cuh", "ne_extract.cuh", "ne_mma.cuh", "ne_entangle.cuh")
+        dom_src = ("ne_cconv_digits.cu", "ne_cconv_tile.cuh", "ne_extract.cuh", "ne_mma.cuh", "ne_entangle.cuh",
+                   "ne_faults.cuh")
         h2d = wl.c.nbytes + wl.g.nbytes
         d2h = out.numel() * 8 + flags.numel() * 4 + 8
         cfg = workload_config(wl, l, k, world)
@@ -387,7 +388,7 @@ def run_ours(args, rank, world, local_rank):
         mma_ops_per_launch = None
         imad_per_launch = G * ntt_imad_per_group(M * dg.S, N)
         dominant = "ne_cconv_ntt"
-        dom_src = ("ne_ntt.cu", "ne_entangle.cuh", "ne_extract.cuh")
+        dom_src = ("ne_ntt.cu", "ne_entangle.cuh", "ne_extract.cuh", "ne_faults.cuh")
         h2d = wl.c.nbytes + wl.g.nbytes
         d2h = out.numel() * 8 + flags.numel() * 4 + 8
         cfg = workload_config(wl, l, k, world)
@@ -421,7 +422,7 @@ def run_ours(args, rank, world, local_rank):
         launches_per_step = 2
         mma_ops_per_launch = 2 * M * dg.S * n ** 3
         dominant = "ne_gemm_digits"
-        dom_src = ("ne_gemm_digits.cu", "ne_extract.cuh", "ne_mma.cuh")
+        dom_src = ("ne_gemm_digits.cu", "ne_extract.cuh", "ne_mma.cuh", "ne_faults.cuh")
         h2d = wl.c.nbytes + wl.Gm.nbytes
         d2h = out.numel() * 8 + flags.numel() * 4 + 8
         cfg = workload_config(wl, l, k, world)
