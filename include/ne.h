@@ -546,7 +546,8 @@ typedef struct {
                                   entanglement, outputs d_m; requires NE_FUSE_NONE) -- the
                                   unprotected path entanglement is compared with             */
     int64_t c_off;             /* int32 element offset of the job's streams [M][positions]    */
-    int64_t op_off;            /* byte offset of the job's operator: G [k][cols] or g [N]     */
+    int64_t op_off;            /* byte offset of the job's operator: G [k][cols] or g [N], a
+                                  multiple of 4                                               */
     int64_t out_off;           /* int64 element offset of the job's outputs [M][positions]    */
     int64_t flag_off;          /* uint32 word offset of the job's check bitmap                */
     int64_t fault_begin;       /* the job's range [begin, end) in the fault lists             */

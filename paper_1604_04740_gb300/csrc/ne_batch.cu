@@ -739,6 +739,7 @@ static ne_status plan_batch(const ne_job* jobs, int32_t njobs, ne_batch_config c
             K = j.k;
         } else {
             if (j.N < 2 || j.N > 65536) return fail(NE_EINVAL, "job %d: N=%d (2 <= N <= 65536)", i, j.N);
+            if (j.op_off % 4) return fail(NE_EINVAL, "job %d: op_off must be a multiple of 4", i);
             K = j.N;
         }
         const int64_t amax = std::max((int64_t)std::abs((int64_t)j.cmin), (int64_t)std::abs((int64_t)j.cmax));

@@ -198,7 +198,8 @@ template <int NTW, int MT, int LD>
 ne_status launch(const CconvArgs& a, int64_t batch, cudaStream_t s) {
     const void* src = LD == cconv::LD_PLANES ? (const void*)a.planes
                       : (LD == cconv::LD_RAW ? (const void*)a.craw : (const void*)a.cwords);
-    if (a.N % cconv::T == 0 && aligned(src, 16)) return launch_ix<NTW, MT, LD, cconv::IX_CIRC>(a, batch, s);
+    if (a.N % cconv::T == 0 && aligned(src, 16) && aligned(a.g, 4))
+        return launch_ix<NTW, MT, LD, cconv::IX_CIRC>(a, batch, s);
     return launch_ix<NTW, MT, LD, cconv::IX_RAGGED>(a, batch, s);
 }
 
@@ -208,7 +209,7 @@ ne_status dispatch(const CconvArgs& a, int64_t batch, cudaStream_t s) {
     const int var = hybrid_variant(NB, a.MS);
     const void* src = LD == cconv::LD_PLANES ? (const void*)a.planes
                       : (LD == cconv::LD_RAW ? (const void*)a.craw : (const void*)a.cwords);
-    if (var && NB <= 16 && a.N % cconv::T == 0 && aligned(src, 16)) {
+    if (var && NB <= 16 && a.N % cconv::T == 0 && aligned(src, 16) && aligned(a.g, 4)) {
         ne_status hs = NE_EINVAL;
         if (a.M == 3 && a.MS == 6) hs = launch_hybrid_variant<3, 6, LD>(var, a, batch, s);
         else if (a.M == 4 && a.MS == 8) hs = launch_hybrid_variant<4, 8, LD>(var, a, batch, s);

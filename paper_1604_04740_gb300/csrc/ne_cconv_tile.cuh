@@ -518,18 +518,30 @@ __device__ __forceinline__ void tile(const TileArgs& a, uint8_t* smem, int p0, i
         for (int e = tid; e < 4 * (GW / 4); e += THREADS) {
             const int rr = e / (GW / 4), zw = e - rr * (GW / 4);
             uint32_t w = 0;
+            if constexpr (IX == IX_CIRC) {
+                // N a multiple of 64: the bytes g[v], g[v-1], g[v-2], g[v-3] (mod N)
+                // are one funnel shift of two aligned filter words, byte-reversed
+                int v = (top - (4 * zw + rr - PADB)) % N;
+                if (v < 0) v += N;
+                int u = v - 3;
+                if (u < 0) u += N;
+                const uint32_t* g32 = reinterpret_cast<const uint32_t*>(a.g);
+                const int q = u >> 2, q1 = q + 1 == N / 4 ? 0 : q + 1;
+                w = __byte_perm(__funnelshift_r(__ldg(g32 + q), __ldg(g32 + q1), 8 * (u & 3)), 0u, 0x0123);
+            } else {
 #pragma unroll
-            for (int k = 0; k < 4; k++) {
-                int idx = top - (4 * zw + k + rr - PADB);
-                uint32_t gv;
-                if constexpr (IX == IX_LINEAR) {
-                    gv = (idx >= 0 && idx < a.lin_K) ? (uint32_t)(uint8_t)__ldg(a.g + idx) : 0u;
-                } else {
-                    idx %= N;
-                    if (idx < 0) idx += N;
-                    gv = (uint32_t)(uint8_t)__ldg(a.g + idx);
+                for (int k = 0; k < 4; k++) {
+                    int idx = top - (4 * zw + k + rr - PADB);
+                    uint32_t gv;
+                    if constexpr (IX == IX_LINEAR) {
+                        gv = (idx >= 0 && idx < a.lin_K) ? (uint32_t)(uint8_t)__ldg(a.g + idx) : 0u;
+                    } else {
+                        idx %= N;
+                        if (idx < 0) idx += N;
+                        gv = (uint32_t)(uint8_t)__ldg(a.g + idx);
+                    }
+                    w |= gv << (8 * k);
                 }
-                w |= gv << (8 * k);
             }
             *reinterpret_cast<uint32_t*>(gcp + rr * GW + 4 * zw) = w;
         }
@@ -634,23 +646,27 @@ __device__ __forceinline__ void tile_hybrid(const TileArgs& a, uint8_t* smem) {
     // -- loads (every thread) --
     load_window<LD>(a, sig, WB, -(uch - 1), NB, NTHR);
     cp_async_commit();
-    // the filter, staged once in the stash's space (free until the stash is
-    // written): 4-byte loads instead of a global byte load per copied byte
-    uint8_t* gs = reinterpret_cast<uint8_t*>(stash);
-    for (int e = tid; e < N / 4; e += NTHR)
-        *reinterpret_cast<uint32_t*>(gs + 4 * e) = __ldg(reinterpret_cast<const uint32_t*>(a.g) + e);
+    // The reversed filter rev[j] = g[(N - j) mod N] as words, staged once in the
+    // stash's space (free until the stash is written), with one wrap word at
+    // the end: word i is byte 0 of filter word (N/4 - i) mod (N/4) followed by
+    // bytes 3, 2, 1 of the word before it (N is a multiple of 64 here).  Every
+    // copy word below holds 4 consecutive bytes of rev, g[(v - k) mod N] =
+    // rev[(s + k) mod N] with s = -v mod N: one funnel shift of two staged words.
+    uint32_t* revw = reinterpret_cast<uint32_t*>(stash);
+    const int NW = N / 4;
+    for (int i = tid; i <= NW; i += NTHR) {
+        const int a0 = i % NW == 0 ? 0 : NW - i % NW;
+        const int a1 = a0 == 0 ? NW - 1 : a0 - 1;
+        const uint32_t* gw = reinterpret_cast<const uint32_t*>(a.g);
+        revw[i] = __byte_perm(__ldg(gw + a0), __ldg(gw + a1), 0x5670);
+    }
     __syncthreads();
-    // the word of filter bytes g[(v - k) mod N], k = 0..3 (v reduced once)
+    // the word of filter bytes g[(v - k) mod N], k = 0..3
     auto gword = [&](int v) {
-        while (v < 0) v += N;
-        while (v >= N) v -= N;
-        uint32_t w = 0;
-#pragma unroll
-        for (int k = 0; k < 4; k++) {
-            const int idx = v - k < 0 ? v - k + N : v - k;
-            w |= (uint32_t)gs[idx] << (8 * k);
-        }
-        return w;
+        int sidx = (-v) % N;
+        if (sidx < 0) sidx += N;
+        const int q = sidx >> 2, b = sidx & 3;
+        return __funnelshift_r(revw[q], revw[q + 1], 8 * b);
     };
     const int top = T * uch;
     for (int e = tid; e < 4 * (GW / 4); e += NTHR) {
