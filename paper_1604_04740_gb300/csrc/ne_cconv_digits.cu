@@ -230,6 +230,9 @@ ne_status dispatch(const CconvArgs& a, int64_t batch, cudaStream_t s) {
             if (MS <= 6) return launch<6, 5, LD>(a, batch, s);
             if (MS <= 10) return launch<10, 5, LD>(a, batch, s);
             return launch<16, 5, LD>(a, batch, s);
+        case 8:   // the paper's other stream count (Sec. V: M in {3, 8})
+            if (MS <= 8) return launch<8, 8, LD>(a, batch, s);
+            return launch<16, 8, LD>(a, batch, s);
         default:
             return launch<16, 0, LD>(a, batch, s);
     }

@@ -100,9 +100,9 @@ constexpr int IX_RAGGED = 2;   // circular, any N: input block p - d for the sig
 
 __device__ __forceinline__ int64_t shl64(int64_t x, int s) { return (int64_t)((uint64_t)x << s); }
 
-// LT: the job's l when it is 16 (every shift below is then a constant; with
-// the two digits at shifts 0 and 16 of the byte-aligned plan of int8-valued
-// streams, the recombination is one shift-add), else 0
+// LT: the job's l when it is 16 or 8 (every shift below is then a constant;
+// with the two digits at shifts 0 and LT of the byte-aligned plan of
+// int8-valued streams, the recombination is one shift-add), else 0
 template <int MT, int LT>
 __device__ __forceinline__ void epilogue_l(const TileArgs& a, const int32_t* stash, int p0, int npb, int nthreads) {
     const int M = MT ? MT : a.M;
@@ -184,6 +184,7 @@ template <int MT>
 __device__ __forceinline__ void epilogue(const TileArgs& a, const int32_t* stash, int p0, int npb,
                                          int nthreads = THREADS) {
     if (a.l == 16) epilogue_l<MT, 16>(a, stash, p0, npb, nthreads);
+    else if (a.l == 8) epilogue_l<MT, 8>(a, stash, p0, npb, nthreads);
     else epilogue_l<MT, 0>(a, stash, p0, npb, nthreads);
 }
 
@@ -256,14 +257,21 @@ __device__ __forceinline__ void load_window(const TileArgs& a, uint8_t* sig, int
     } else {
     const int M = a.M, S = a.S;
     uint32_t worst = 0;
-    for (int e = tid; e < WB * M * 4; e += nthr) {
+    // a window longer than the group holds block (first + b) mod NB twice, at
+    // rows b and b + NB (WB < 2 NB): each block is formed once and stored twice
+    const int WU = WB < NB ? WB : NB;
+    for (int e = tid; e < WU * M * 4; e += nthr) {
         const int c16 = e & 3, rowm = e >> 2;
         const int blk_rel = rowm / M, m = rowm - blk_rel * M;
         int ab = (first + blk_rel) % NB;
         if (ab < 0) ab += NB;
         uint8_t* dst = sig + (blk_rel * MS + m * S) * ROWB + c16 * 16;
+        uint8_t* dst2 = blk_rel + NB < WB ? dst + NB * MS * ROWB : nullptr;
         if (a.fuse == NE_FUSE_RECOVER && m == a.r) {
-            for (int s = 0; s < S; s++) *reinterpret_cast<uint4*>(dst + s * ROWB) = make_uint4(0u, 0u, 0u, 0u);
+            for (int s = 0; s < S; s++) {
+                *reinterpret_cast<uint4*>(dst + s * ROWB) = make_uint4(0u, 0u, 0u, 0u);
+                if (dst2) *reinterpret_cast<uint4*>(dst2 + s * ROWB) = make_uint4(0u, 0u, 0u, 0u);
+            }
             continue;
         }
         const int64_t pos = (int64_t)ab * T + c16 * 16;
@@ -304,9 +312,10 @@ __device__ __forceinline__ void load_window(const TileArgs& a, uint8_t* sig, int
         for (int s = 0; s < 4; s++) {
             if (s >= S) break;
             const uint32_t t = (uint32_t)a.raw_byte[s];
-            *reinterpret_cast<uint4*>(dst + s * ROWB) =
-                make_uint4(pick4(y[0], y[1], y[2], y[3], t), pick4(y[4], y[5], y[6], y[7], t),
-                           pick4(y[8], y[9], y[10], y[11], t), pick4(y[12], y[13], y[14], y[15], t));
+            const uint4 d = make_uint4(pick4(y[0], y[1], y[2], y[3], t), pick4(y[4], y[5], y[6], y[7], t),
+                                       pick4(y[8], y[9], y[10], y[11], t), pick4(y[12], y[13], y[14], y[15], t));
+            *reinterpret_cast<uint4*>(dst + s * ROWB) = d;
+            if (dst2) *reinterpret_cast<uint4*>(dst2 + s * ROWB) = d;
         }
     }
     if (worst > (uint32_t)a.raw_hi - (uint32_t)a.raw_lo && a.status) atomicExch(a.status, (int32_t)NE_ERANGE);

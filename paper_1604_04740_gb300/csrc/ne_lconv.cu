@@ -118,6 +118,9 @@ ne_status dispatch(const LconvArgs& a, int64_t batch, cudaStream_t s) {
             if (MS <= 6) return launch<6, 5>(a, batch, s);
             if (MS <= 10) return launch<10, 5>(a, batch, s);
             return launch<16, 5>(a, batch, s);
+        case 8:   // the paper's other stream count (Sec. V: M in {3, 8})
+            if (MS <= 8) return launch<8, 8>(a, batch, s);
+            return launch<16, 8>(a, batch, s);
         default:
             return launch<16, 0>(a, batch, s);
     }

@@ -87,6 +87,8 @@ CCONV_CASES = [
     ("entangled", 5, 4, 1024),      # hybrid tile of 8 planes
     ("entangled", 3, 3, 2048),      # two chunks of shifts, two tiles per group
     ("entangled", 4, 5, 576),       # generic tile, ragged chunk
+    ("entangled", 2, 8, 1024),      # eight streams (l = 8, 16 digit planes)
+    ("digits", 2, 6, 512),          # a stream count without its own instantiation
     ("digits", 9, 3, 1024),
     ("digits", 3, 4, 1088),
     ("ntt", 7, 3, 1024),

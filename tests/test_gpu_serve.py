@@ -94,8 +94,8 @@ def test_pool_allocator_coalesces(mods):
 
 @pytest.mark.parametrize("count", [1, 7, 300])
 def test_copy_regions_gathers_every_byte(mods, count):
-    # regions of odd sizes at odd offsets (and empty ones), more than one
-    # gather launch for 300 regions; bytes outside the regions stay untouched
+    # regions of odd sizes at odd offsets (and empty ones), one copy per
+    # region; bytes outside the regions stay untouched
     _, ne, _ = mods
     rng = np.random.default_rng(count)
     src = torch.from_numpy(rng.integers(0, 256, 1 << 20, dtype=np.uint8)).pin_memory()
