@@ -84,8 +84,9 @@ __global__ void __launch_bounds__(cconv::THREADS, (NTW <= 6 ? 4 : (NTW <= 10 ? 3
     cconv::tile<NTW, MT, LD, IX>(t, smem, p0, min(cconv::NPB, NB - p0));
 }
 
-// The hybrid tile (tensor pipe + dp4a pipe) for groups of 9..16 blocks.
-template <int MT, int MSC, int HW, int R, int LD>
+// The hybrid tile (tensor pipe + dp4a pipe) for groups of 9..16 blocks
+// (NBC: 16 for groups of exactly 16 blocks, compiled for that size; 0: any).
+template <int MT, int MSC, int HW, int R, int LD, int NBC>
 __global__ void __launch_bounds__(cconv::hybrid_threads(HW), cconv::hybrid_threads(HW) <= 384 ? 3 : 2)
     k_cconv_digits_hybrid(CconvArgs a, int64_t b_off) {
     extern __shared__ __align__(128) uint8_t smem[];
@@ -109,10 +110,10 @@ __global__ void __launch_bounds__(cconv::hybrid_threads(HW), cconv::hybrid_threa
 #pragma unroll
     for (int i = 0; i < NE_MAX_DIGITS; i++) t.shift[i] = a.shift[i];
     raw_fields(a, b, t);
-    cconv::tile_hybrid<MT, MSC, HW, R, LD>(t, smem);
+    cconv::tile_hybrid<MT, MSC, HW, R, LD, NBC>(t, smem);
 }
 
-template <int MT, int MSC, int HW, int R, int LD>
+template <int MT, int MSC, int HW, int R, int LD, int NBC>
 ne_status launch_hybrid(const CconvArgs& a, int64_t batch, cudaStream_t s) {
     if (a.N / cconv::T <= 32 * HW * R / cconv::T) return NE_EINVAL;   // needs a block left for the tensor pipe
     const int smem = cconv::hybrid_smem_bytes(MSC);
@@ -120,14 +121,14 @@ ne_status launch_hybrid(const CconvArgs& a, int64_t batch, cudaStream_t s) {
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-        if (cudaFuncSetAttribute(k_cconv_digits_hybrid<MT, MSC, HW, R, LD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if (cudaFuncSetAttribute(k_cconv_digits_hybrid<MT, MSC, HW, R, LD, NBC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  smem) != cudaSuccess)
             return check_launch("ne_cconv_digits: shared-memory attribute");
         attr_set[dev] = true;
     }
     for (int64_t b0 = 0; b0 < batch; b0 += 65535) {
         const int64_t nb = batch - b0 < 65535 ? batch - b0 : 65535;
-        k_cconv_digits_hybrid<MT, MSC, HW, R, LD><<<dim3(1, (unsigned)nb), cconv::hybrid_threads(HW), smem, s>>>(a, b0);
+        k_cconv_digits_hybrid<MT, MSC, HW, R, LD, NBC><<<dim3(1, (unsigned)nb), cconv::hybrid_threads(HW), smem, s>>>(a, b0);
         ne_status st = check_launch("ne_cconv_digits (hybrid)");
         if (st) return st;
     }
@@ -135,36 +136,39 @@ ne_status launch_hybrid(const CconvArgs& a, int64_t batch, cudaStream_t s) {
 }
 
 // Split of a group between the tensor pipe and the dp4a pipe (variant -1:
-// the default).  Default for groups of 16 blocks (the fastest splits measured
-// on GB300, 4096 groups, N = 1024): 6 planes (M = 3, two digits) put 6 blocks
-// on 4 dp4a warps of 3 outputs per thread (variant 43, 3/8 of the work;
-// 0.303 ms against 0.319 ms with 2 warps of 6 and 0.32 ms with half of the
-// blocks on dp4a, although the two-pipe probe peaks at that half); 8 planes
-// put 4 blocks on 2 warps (variant 24, 0.392 ms; 43: 0.412 ms).
-// ne_set_cconv_split overrides it: 0 tensor pipe only; HR (22..26, 34,
-// 42..44, 52, 62) H dp4a warps of R outputs per thread (H * R / 2 blocks on
-// dp4a), for any group of at most 16 blocks.
+// the default).  Default for groups of 16 blocks, 6 or 8 planes (M = 3 or 4,
+// two digits): 6 blocks on 4 dp4a warps of 3 outputs per thread (variant 43,
+// 3/8 of the work; measured on GB300 at 4096 groups of N = 1024: M = 3
+// 0.271 ms against 0.272 ms for 44 and 0.279 ms for 34, M = 4 0.338 ms
+// against 0.383 ms for 24).
+// ne_set_cconv_split overrides it: 0 tensor pipe only; HR (23, 24, 34, 42,
+// 43, 44) H dp4a warps of R outputs per thread (H * R / 2 blocks on dp4a),
+// for any group of at most 16 blocks.
 int g_split = -1;
 
 int hybrid_variant(int64_t NB, int MS) {
-    if (g_split == -1) return NB == 16 ? (MS == 6 ? 43 : 24) : 0;
+    if (g_split == -1) return NB == 16 ? 43 : 0;
     return g_split;
+}
+
+// groups of 16 blocks from raw streams or planes take the tile compiled for that size
+template <int MT, int MSC, int HW, int R, int LD>
+ne_status launch_hybrid_n(const CconvArgs& a, int64_t batch, cudaStream_t s) {
+    if constexpr (LD != cconv::LD_WORDS) {
+        if (a.N == 16 * cconv::T) return launch_hybrid<MT, MSC, HW, R, LD, 16>(a, batch, s);
+    }
+    return launch_hybrid<MT, MSC, HW, R, LD, 0>(a, batch, s);
 }
 
 template <int MT, int MSC, int LD>
 ne_status launch_hybrid_variant(int var, const CconvArgs& a, int64_t batch, cudaStream_t s) {
     switch (var) {
-        case 22: return launch_hybrid<MT, MSC, 2, 2, LD>(a, batch, s);
-        case 23: return launch_hybrid<MT, MSC, 2, 3, LD>(a, batch, s);
-        case 24: return launch_hybrid<MT, MSC, 2, 4, LD>(a, batch, s);
-        case 25: return launch_hybrid<MT, MSC, 2, 5, LD>(a, batch, s);
-        case 26: return launch_hybrid<MT, MSC, 2, 6, LD>(a, batch, s);
-        case 42: return launch_hybrid<MT, MSC, 4, 2, LD>(a, batch, s);
-        case 34: return launch_hybrid<MT, MSC, 3, 4, LD>(a, batch, s);
-        case 43: return launch_hybrid<MT, MSC, 4, 3, LD>(a, batch, s);
-        case 44: return launch_hybrid<MT, MSC, 4, 4, LD>(a, batch, s);
-        case 52: return launch_hybrid<MT, MSC, 5, 2, LD>(a, batch, s);
-        case 62: return launch_hybrid<MT, MSC, 6, 2, LD>(a, batch, s);
+        case 23: return launch_hybrid_n<MT, MSC, 2, 3, LD>(a, batch, s);
+        case 24: return launch_hybrid_n<MT, MSC, 2, 4, LD>(a, batch, s);
+        case 34: return launch_hybrid_n<MT, MSC, 3, 4, LD>(a, batch, s);
+        case 42: return launch_hybrid_n<MT, MSC, 4, 2, LD>(a, batch, s);
+        case 43: return launch_hybrid_n<MT, MSC, 4, 3, LD>(a, batch, s);
+        case 44: return launch_hybrid_n<MT, MSC, 4, 4, LD>(a, batch, s);
         default: return NE_EINVAL;
     }
 }
@@ -342,7 +346,7 @@ extern "C" ne_status ne_cconv_entangled(ne_params p, ne_digits dg, const int32_t
 }
 
 extern "C" ne_status ne_set_cconv_split(int32_t variant) {
-    static const int ok[] = {-1, 0, 22, 23, 24, 25, 26, 34, 42, 43, 44, 52, 62};
+    static const int ok[] = {-1, 0, 23, 24, 34, 42, 43, 44};
     for (int v : ok)
         if (v == variant) {
             g_split = variant;

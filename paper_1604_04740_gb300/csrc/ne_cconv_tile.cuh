@@ -610,17 +610,29 @@ __device__ __forceinline__ void tile(const TileArgs& a, uint8_t* smem, int p0, i
 // hybrid tile gives the last HW * R / 2 output blocks to HW extra warps that
 // compute them with dp4a, while the 8 MMA warps compute the other blocks as
 // tile() does; both finish into the same stash and the same epilogue.  A
-// dp4a thread owns R outputs (stride 32 HW) for every digit plane: per 4
-// inputs it loads each plane's digit word once (a broadcast) and one word
-// of the reversed filter per output, from four byte-shifted copies so that
-// every read is aligned and the 32 lanes hit 32 distinct banks.
+// dp4a thread owns R outputs 4 apart, i0 + 4 r, for every digit plane.  The
+// filter word that output i0 + 4 r needs at input chunk J (positions 4 J ..
+// 4 J + 3) is the one output i0 needs at chunk J - r, so per 4 inputs a
+// thread loads one new filter word (from four byte-shifted copies of the
+// reversed filter, so that every read is aligned) and each plane's digit
+// word (a broadcast, 8 inputs per load), for R x planes dp4a.
 __host__ __device__ constexpr int hybrid_threads(int HW) { return THREADS + 32 * HW; }
-constexpr int GDP = 2144;                     // bytes per filter copy slot: >= 2 * 1024 + 8 + 68
+constexpr int GDP = 2192;                     // bytes per filter copy slot: >= 2 * 1024 + 8 + 4 * 31
 constexpr int GDPW = 514;                     // words of a copy the dp4a reads reach: (2 * 1024 + 8) / 4
-// Byte offset of dp4a filter copy rr.  A warp's 32 lanes read through the four
-// copies with 8 consecutive lanes per copy; the extra word offsets 0, 17, 1, 17
-// put the four groups on disjoint sets of 8 banks (with GDP = 24 words mod 32).
-__host__ __device__ constexpr int gdp_off(int rr) { return rr * GDP + 4 * ((rr & 1) ? 17 : (rr == 2 ? 1 : 0)); }
+// Byte offset of dp4a filter copy rr for R outputs per thread (R = 2, 3, 4).
+// The 8 lanes that read copy rr (the same rho) are R words apart, so their
+// banks are D_rr - R k, k = 0..7, with D_rr = the copy's word offset (+1 for
+// copy 0, whose reads start one word later).  D_rr = rr (R = 4), 0, 1, 16, 17
+// (R = 2) or 5, 13, 21, 29 (R = 3: times 11 = 3^-1 mod 32 the sets become
+// intervals of 8 banks ending at 23, 15, 7, 31) puts the four copies' lanes on
+// disjoint banks.
+__host__ __device__ constexpr int gdp_bank(int rr, int R) {
+    return R == 4 ? rr
+                  : (R == 3 ? 5 + 8 * rr : (rr == 0 ? 0 : (rr == 1 ? 1 : (rr == 2 ? 16 : 17))));
+}
+__host__ __device__ constexpr int gdp_off(int rr, int R) {
+    return rr * GDP + 4 * (((gdp_bank(rr, R) - (rr * GDP / 4 + (rr == 0 ? 1 : 0))) % 32 + 32) % 32);
+}
 
 // [digit-plane window + tensor-pipe filter window][dp4a filter copies][stash]:
 // the stash has its own space, so a warp may write its results as soon as it
@@ -629,13 +641,17 @@ __host__ __device__ constexpr int hybrid_smem_bytes(int MS) {
     return WBMAX * MS * ROWB + 4 * GW + 4 * GDP + MS * NPB * SP * 4;
 }
 
-template <int MT, int MSC, int HW, int R, int LD = LD_PLANES>
+// NBC: the group's block count when the caller fixes it at compile time (every
+// size below and the shape of the tensor warps' loop are then constants), else 0
+template <int MT, int MSC, int HW, int R, int LD = LD_PLANES, int NBC = 0>
 __device__ __forceinline__ void tile_hybrid(const TileArgs& a, uint8_t* smem) {
     constexpr int MS = MSC;
     constexpr int NTHR = hybrid_threads(HW);
     constexpr int DT = 32 * HW;           // dp4a threads
     static_assert((DT * R) % T == 0, "dp4a outputs must be whole blocks");
-    const int N = a.N;
+    static_assert(R >= 2 && R <= 4, "the dp4a filter copies are laid out for 2 to 4 outputs per thread");
+    static_assert(NBC == 0 || (NBC > DT * R / T && NBC <= NPB), "a compile-time group size must leave tensor blocks");
+    const int N = NBC ? NBC * T : a.N;
     const int NB = N / T;                 // DT * R / T + 1 .. 16
     const int uch = NB;                   // a single chunk of shifts
     const int npb = NB - DT * R / T;      // output blocks on the tensor pipe
@@ -686,7 +702,7 @@ __device__ __forceinline__ void tile_hybrid(const TileArgs& a, uint8_t* smem) {
     // reversed filter at offset y = z + rr - N - 4
     for (int e = tid; e < 4 * GDPW; e += NTHR) {
         const int rr = e / GDPW, zw = e - rr * GDPW;
-        *reinterpret_cast<uint32_t*>(gdp + gdp_off(rr) + 4 * zw) = gword(N + 4 - 4 * zw - rr);
+        *reinterpret_cast<uint32_t*>(gdp + gdp_off(rr, R) + 4 * zw) = gword(N + 4 - 4 * zw - rr);
     }
     cp_async_wait<0>();
     __syncthreads();
@@ -696,33 +712,42 @@ __device__ __forceinline__ void tile_hybrid(const TileArgs& a, uint8_t* smem) {
         const int mt = warp & 3, half = warp >> 2;
         const int gq = lane >> 2, tq = lane & 3;
         const int tile0 = half * NTH;
-        const int ntile = max(0, min(NT, tile0 + NTH) - tile0);
+        // both halves hold NTH column tiles when NT is even
+        const int ntile = NT == 2 * NTH ? NTH : max(0, min(NT, tile0 + NTH) - tile0);
         const int kh = (lane >> 3) & 1;
         const int rho = (4 - (gq & 3)) & 3;
-        const uint32_t gcp_s = smem_u32(gcp) + rho * GW + PADB - rho;
         constexpr int NTW = (16 * MS / 8 + 1) / 2;
         int acc[NTW][4];
 #pragma unroll
         for (int j = 0; j < NTW; j++) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0;
+        // loop-invariant per lane: the ldmatrix row of each column-tile pair
+        // (a padding column reads row 0, its result is dropped) and the A words
+        uint32_t bbase[(NTW + 1) / 2];
+#pragma unroll
+        for (int jj = 0; jj < NTW; jj += 2) {
+            int c = 8 * (tile0 + jj + (lane >> 4)) + (lane & 7);
+            if (c >= cols) c = 0;
+            bbase[jj / 2] = sig_s + c * ROWB + 16 * kh;
+        }
+        // shift u: A words at ya - T u, B rows of window block uch - 1 - u
+        const uint32_t ya0 = smem_u32(gcp) + rho * GW + PADB - rho + T * uch - 16 * mt - gq + 4 * tq;
+        const uint32_t boff0 = (uch - 1) * MS * ROWB;
+#pragma unroll 2
         for (int u = 0; u < uch; u++) {
-            const int ushift = uch - 1 - u;
-            const int Y0 = T * (uch - u) - 16 * mt - gq;
+            const uint32_t ya = ya0 - T * u;
+            const uint32_t boff = boff0 - u * (MS * ROWB);
 #pragma unroll
             for (int ks = 0; ks < 2; ks++) {
-                const int t0 = 32 * ks;
-                const uint32_t ya = gcp_s + Y0 + t0 + 4 * tq;
                 uint32_t af[4];
-                af[0] = lds32(ya);
-                af[1] = lds32(ya - 8);
-                af[2] = lds32(ya + 16);
-                af[3] = lds32(ya + 8);
+                af[0] = lds32(ya + 32 * ks);
+                af[1] = lds32(ya + 32 * ks - 8);
+                af[2] = lds32(ya + 32 * ks + 16);
+                af[3] = lds32(ya + 32 * ks + 8);
 #pragma unroll
                 for (int jj = 0; jj < NTW; jj += 2) {
                     if (jj >= ntile) break;
-                    int c = 8 * (tile0 + jj + (lane >> 4)) + (lane & 7);
-                    if (c >= cols) c = 0;
                     uint32_t bf[4];
-                    ldsm_x4(bf, sig_s + (c + MS * ushift) * ROWB + t0 + 16 * kh);
+                    ldsm_x4(bf, bbase[jj / 2] + boff + 32 * ks);
                     mma_s8(acc[jj], af, bf[0], bf[1]);
                     if (jj + 1 < ntile) mma_s8(acc[jj + 1], af, bf[2], bf[3]);
                 }
@@ -742,45 +767,51 @@ __device__ __forceinline__ void tile_hybrid(const TileArgs& a, uint8_t* smem) {
             }
         }
     } else {
-        // -- dp4a pipe: outputs i = npb * T + t + 64 r, r = 0..7, every plane --
+        // -- dp4a pipe: thread t = 4 k + rho owns outputs i0 + 4 r, i0 = npb T + rho + 4 R k --
         const int t = tid - THREADS;               // 0 .. DT - 1
-        const int i_base = npb * T + t;
-        const int rho = (4 - (t & 3)) & 3;         // byte shift of this thread's filter reads
-        const uint32_t gd = smem_u32(gdp) + gdp_off(rho) + N + 4 - rho - i_base;
+        const int rho = t & 3, k = t >> 2;
+        const int rr = (4 - rho) & 3;              // the copy whose words start at i0's byte shift
+        const int i0 = npb * T + rho + 4 * R * k;
+        // F(m), the word of filter bytes g[(i0 - 4 m - e) mod N], e = 0..3, sits at
+        // byte gd + 4 m of copy rr (m >= 1 - R keeps every read inside the copy)
+        const uint32_t gd = smem_u32(gdp) + gdp_off(rr, R) + N + 4 - rr - i0;
         int acc[R][MS];
 #pragma unroll
         for (int r = 0; r < R; r++)
 #pragma unroll
             for (int ms = 0; ms < MS; ms++) acc[r][ms] = 0;
+        // f[w] = F(J0 - (R - 1) + w): output i0 + 4 r at chunk J0 + e takes f[R - 1 + e - r]
+        uint32_t f[R + 1];
+#pragma unroll
+        for (int w = 0; w < R - 1; w++) f[w] = lds32(gd + 4 * (w - (R - 1)));
         for (int jb = 0; jb < NB; jb++) {
             const int blk_rel = (jb + uch - 1) % NB;     // where input block jb sits in the window
             const uint32_t srow = sig_s + blk_rel * MS * ROWB;
-            // 8 input positions per step: the digit-plane words are the same for
-            // every lane (one 8-byte broadcast load per plane), the filter words
-            // per lane and output
-#pragma unroll 2
-            for (int jj = 0; jj < T; jj += 8) {
-                const int j = jb * T + jj;
-                uint2 s[MS];
+            // 8 inputs (chunks J0, J0 + 1) per step: every accumulator takes two
+            // dependent dp4a, the R x planes accumulators are independent
 #pragma unroll
-                for (int ms = 0; ms < MS; ms++) s[ms] = lds64(srow + ms * ROWB + jj);
-                uint32_t gw[2][R];
+            for (int jh = 0; jh < T / 8; jh++) {
+                const int J0 = jb * (T / 4) + 2 * jh;
+                f[R - 1] = lds32(gd + 4 * J0);
+                f[R] = lds32(gd + 4 * (J0 + 1));
+                uint2 x[MS];
 #pragma unroll
-                for (int h = 0; h < 2; h++)
+                for (int ms = 0; ms < MS; ms++) x[ms] = lds64(srow + ms * ROWB + 8 * jh);   // the same for every lane
 #pragma unroll
-                    for (int r = 0; r < R; r++) gw[h][r] = lds32(gd + j + 4 * h - DT * r);
+                for (int ms = 0; ms < MS; ms++)
 #pragma unroll
-                for (int r = 0; r < R; r++)
+                    for (int r = 0; r < R; r++) acc[r][ms] = __dp4a((int)x[ms].x, (int)f[R - 1 - r], acc[r][ms]);
 #pragma unroll
-                    for (int ms = 0; ms < MS; ms++) {
-                        acc[r][ms] = __dp4a((int)s[ms].x, (int)gw[0][r], acc[r][ms]);
-                        acc[r][ms] = __dp4a((int)s[ms].y, (int)gw[1][r], acc[r][ms]);
-                    }
+                for (int ms = 0; ms < MS; ms++)
+#pragma unroll
+                    for (int r = 0; r < R; r++) acc[r][ms] = __dp4a((int)x[ms].y, (int)f[R - r], acc[r][ms]);
+#pragma unroll
+                for (int w = 0; w < R - 1; w++) f[w] = f[w + 2];
             }
         }
 #pragma unroll
         for (int r = 0; r < R; r++) {
-            const int o = t + DT * r;              // output index - npb * T
+            const int o = rho + 4 * (R * k + r);   // output index - npb * T
 #pragma unroll
             for (int ms = 0; ms < MS; ms++) stash[(ms * NPB + npb + o / T) * SP + o % T] = acc[r][ms];
         }
