@@ -358,8 +358,8 @@ def run_ours(args, rank, world, local_rank):
         launches_per_step = 1
         mma_ops_per_launch = 2 * G * M * dg.S * N * N
         dominant = "ne_cconv_entangled"
-        dom_src = ("ne_cconv_digits.cu", "ne_cconv_tile.cuh", "ne_extract.cuh", "ne_mma.cuh", "ne_entangle.cuh",
-                   "ne_faults.cuh")
+        dom_src = ("ne_cconv_raw.cu", "ne_cconv_launch.cuh", "ne_cconv_tile.cuh", "ne_extract.cuh", "ne_mma.cuh",
+                   "ne_entangle.cuh", "ne_faults.cuh")
         h2d = wl.c.nbytes + wl.g.nbytes
         d2h = out.numel() * 8 + flags.numel() * 4 + 8
         cfg = workload_config(wl, l, k, world)
@@ -510,7 +510,7 @@ def run_ours(args, rank, world, local_rank):
         if hybrid:
             # both int8 pipes in the convolution kernel's warp layout (8 tensor + 4 dp4a warps,
             # 3 blocks per SM), swept over the share of the work given to dp4a; the ceiling
-            # is the best split (the kernel gives dp4a 6 of 16 output blocks, 3/8)
+            # is the best split (the kernel gives dp4a 8 of 16 output blocks, 1/2)
             I, DW = 2048, 4
             for num, den in ((0, 1), (1, 8), (1, 4), (3, 8), (1, 2)):
                 idp = (256 * I * num) // (DW * (den - num))
@@ -522,8 +522,8 @@ def run_ours(args, rank, world, local_rank):
                 peak_mixed[f"{num}/{den}"] = ops / (e0.elapsed_time(e1) * 1e-3) / 1e12
         peak = max(peak_mixed.values()) if hybrid else peak_mma
         src = ("measured in this run: mma.sync.m16n8k32 s8 register-resident probe (probe/ne_probe.h, ne_probe_mma_peak)"
-               + ("; the kernel splits each group between the two int8 pipes (10 of 16 blocks on 8 tensor "
-                  "warps, 6 on 4 dp4a warps), so the peak is the best of ne_probe_mixed_peak (both pipes in "
+               + ("; the kernel splits each group between the two int8 pipes (8 of 16 blocks on 8 tensor "
+                  "warps, 8 on 4 dp4a warps), so the peak is the best of ne_probe_mixed_peak (both pipes in "
                   "the kernel's warp layout) over the dp4a work shares in peak_mixed" if hybrid else "")
                + "; MEASURED_PEAKS.json has no int8 figure and sm_103a has no tcgen05 integer MMA")
         roof = {"bound": "tensor", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "TOP/s",

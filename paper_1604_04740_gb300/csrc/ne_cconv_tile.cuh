@@ -102,90 +102,129 @@ __device__ __forceinline__ int64_t shl64(int64_t x, int s) { return (int64_t)((u
 
 // LT: the job's l when it is 16 or 8 (every shift below is then a constant;
 // with the two digits at shifts 0 and LT of the byte-aligned plan of
-// int8-valued streams, the recombination is one shift-add), else 0
-template <int MT, int LT>
+// int8-valued streams, the recombination is one shift-add), else 0.
+// P: positions per lane and pass, lane + 32 p (P = 2 needs npb T to be a
+// multiple of 64); the stream order of the rotation and the output rows are
+// formed once per thread.
+template <int MT, int LT, int P>
 __device__ __forceinline__ void epilogue_l(const TileArgs& a, const int32_t* stash, int p0, int npb, int nthreads) {
+    constexpr int MX = MT ? MT : 32;
     const int M = MT ? MT : a.M;
     const int S = a.S;
     const int l = LT ? LT : a.l;
     const bool two = LT && S == 2 && a.shift[0] == 0 && a.shift[1] == LT;
-    auto digits = [&](const int32_t* sp, int m) {
-        if (two) return (int64_t)sp[2 * m * NPB * SP] + (int64_t)((uint64_t)(int64_t)sp[(2 * m + 1) * NPB * SP] << LT);
-        int64_t v = 0;
-#pragma unroll
-        for (int s = 0; s < NE_MAX_DIGITS; s++)
-            if (s < S) v += shl64(sp[(m * S + s) * NPB * SP], a.shift[s]);
-        return v;
-    };
     const int lane = threadIdx.x & 31;
     const int npos = npb * T;
     const int64_t i0 = (int64_t)p0 * T;
     const bool check = (a.fuse == NE_FUSE_EXTRACT_CHECK);
     const bool need_r = (a.fuse != NE_FUSE_RECOVER);
+    // slot j holds stream (r + j) mod M: its first plane in the stash and its
+    // output row, kept per thread when M is a compile-time constant
+    auto stream_of = [&](int j) {
+        int m = a.r + j;
+        return m >= M ? m - M : m;
+    };
+    int soff_k[MT ? MT : 1];
+    int64_t* orow_k[MT ? MT : 1];
+    if constexpr (MT != 0) {
+#pragma unroll
+        for (int j = 0; j < MT; j++) {
+            soff_k[j] = stream_of(j) * S * NPB * SP;
+            orow_k[j] = a.out + (int64_t)stream_of(j) * a.N + i0;
+        }
+    }
+    auto soff = [&](int j) {
+        if constexpr (MT != 0) return soff_k[j];
+        else return stream_of(j) * S * NPB * SP;
+    };
+    auto orow = [&](int j) -> int64_t* {
+        if constexpr (MT != 0) return orow_k[j];
+        else return a.out + (int64_t)stream_of(j) * a.N + i0;
+    };
+    auto digits = [&](const int32_t* sp, int j) {
+        const int o = soff(j);
+        if (two) return (int64_t)sp[o] + (int64_t)((uint64_t)(int64_t)sp[o + NPB * SP] << LT);
+        int64_t v = 0;
+#pragma unroll
+        for (int s = 0; s < NE_MAX_DIGITS; s++)
+            if (s < S) v += shl64(sp[o + s * NPB * SP], a.shift[s]);
+        return v;
+    };
     int64_t f0 = 0, f1 = 0;
     const int64_t key0 = a.fault_base + i0;
     if (a.nfault > 0) {
         f0 = fault_lower_bound(a.fault_pos, 0, a.nfault, key0);
         f1 = fault_lower_bound(a.fault_pos, f0, a.nfault, key0 + npos);
     }
-    for (int base = threadIdx.x & ~31; base < npos; base += nthreads) {
-        const int i = base + lane;
-        const int pr = i / T, q = i % T;
-        const int32_t* sp = stash + pr * SP + q;
-        // the last block of a linear convolution ends inside the tile
-        const bool valid = i0 + i < a.N;
-        if (a.fuse == NE_FUSE_NONE) {
-            if (!valid) continue;
-            for (int m = 0; m < M; m++) {
-                int64_t v = digits(sp, m);
-                if (f1 > f0) v = apply_faults(v, a.fault_pos, a.fault_stream, a.fault_bit, f0, f1, key0 + i, m);
-                a.out[(int64_t)m * a.N + i0 + i] = v;
-            }
-            continue;
-        }
-        if (i0 + base >= a.N) continue;                  // warp-uniform: the whole warp is past the end
-        int64_t rot[MT ? MT : 32], res[MT ? MT : 32];
+    for (int base = (threadIdx.x & ~31) * P; base < npos; base += nthreads * P) {
+        bool flag[P];
 #pragma unroll
-        for (int j = 0; j < (MT ? MT : 32); j++) {
-            if (!MT && j >= M) break;
-            int m = a.r + j;
-            if (m >= M) m -= M;
-            int64_t v = 0;
-            if (valid && (j > 0 || need_r)) {
-                v = digits(sp, m);
-                if (f1 > f0) v = apply_faults(v, a.fault_pos, a.fault_stream, a.fault_bit, f0, f1, key0 + i, m);
-            }
-            rot[j] = v;
-        }
-        const bool flag = extract_rot<MT>(rot, M, l, check, res) && valid;
+        for (int p = 0; p < P; p++) {
+            flag[p] = false;
+            const int bp = base + 32 * p;
+            if (bp >= npos || i0 + bp >= a.N) continue;      // warp-uniform: past the end
+            const int i = bp + lane;
+            const int pr = i / T, q = i % T;
+            const int32_t* sp = stash + pr * SP + q;
+            // the last block of a linear convolution ends inside the tile
+            const bool valid = i0 + i < a.N;
+            if (a.fuse == NE_FUSE_NONE) {
+                if (!valid) continue;
 #pragma unroll
-        for (int j = 0; j < (MT ? MT : 32); j++) {
-            if (!MT && j >= M) break;
-            int m = a.r + j;
-            if (m >= M) m -= M;
-            if (valid) a.out[(int64_t)m * a.N + i0 + i] = res[j];
+                for (int j = 0; j < MX; j++) {
+                    if (!MT && j >= M) break;
+                    int64_t v = digits(sp, j);
+                    if (f1 > f0) v = apply_faults(v, a.fault_pos, a.fault_stream, a.fault_bit, f0, f1, key0 + i, stream_of(j));
+                    orow(j)[i] = v;
+                }
+                continue;
+            }
+            int64_t rot[MX], res[MX];
+#pragma unroll
+            for (int j = 0; j < MX; j++) {
+                if (!MT && j >= M) break;
+                int64_t v = 0;
+                if (valid && (j > 0 || need_r)) {
+                    v = digits(sp, j);
+                    if (f1 > f0) v = apply_faults(v, a.fault_pos, a.fault_stream, a.fault_bit, f0, f1, key0 + i, stream_of(j));
+                }
+                rot[j] = v;
+            }
+            flag[p] = extract_rot<MT>(rot, M, l, check, res) && valid;
+            if (valid) {
+#pragma unroll
+                for (int j = 0; j < MX; j++) {
+                    if (!MT && j >= M) break;
+                    orow(j)[i] = res[j];
+                }
+            }
         }
         if (check) {
-            const uint32_t w = __ballot_sync(0xffffffffu, flag);
-            if (lane == 0 && w) {
-                if (a.flags) {
-                    if (a.flags_atomic) atomicOr(&a.flags[(i0 + base) / 32], w);
-                    else a.flags[(i0 + base) / 32] = w;
+#pragma unroll
+            for (int p = 0; p < P; p++) {
+                const int bp = base + 32 * p;
+                if (bp >= npos || i0 + bp >= a.N) continue;
+                const uint32_t w = __ballot_sync(0xffffffffu, flag[p]);
+                if (lane == 0 && w) {
+                    if (a.flags) {
+                        if (a.flags_atomic) atomicOr(&a.flags[(i0 + bp) / 32], w);
+                        else a.flags[(i0 + bp) / 32] = w;
+                    }
+                    if (a.nflag) atomicAdd(a.nflag, (unsigned long long)__popc(w));
+                } else if (lane == 0 && a.flags && !a.flags_atomic) {
+                    a.flags[(i0 + bp) / 32] = 0u;
                 }
-                if (a.nflag) atomicAdd(a.nflag, (unsigned long long)__popc(w));
-            } else if (lane == 0 && a.flags && !a.flags_atomic) {
-                a.flags[(i0 + base) / 32] = 0u;
             }
         }
     }
 }
 
-template <int MT>
+template <int MT, int P = 1>
 __device__ __forceinline__ void epilogue(const TileArgs& a, const int32_t* stash, int p0, int npb,
                                          int nthreads = THREADS) {
-    if (a.l == 16) epilogue_l<MT, 16>(a, stash, p0, npb, nthreads);
-    else if (a.l == 8) epilogue_l<MT, 8>(a, stash, p0, npb, nthreads);
-    else epilogue_l<MT, 0>(a, stash, p0, npb, nthreads);
+    if (a.l == 16) epilogue_l<MT, 16, P>(a, stash, p0, npb, nthreads);
+    else if (a.l == 8) epilogue_l<MT, 8, P>(a, stash, p0, npb, nthreads);
+    else epilogue_l<MT, 0, P>(a, stash, p0, npb, nthreads);
 }
 
 // bytes t of four words, XOR 0x80: four consecutive positions of one digit plane
@@ -617,7 +656,7 @@ __device__ __forceinline__ void tile(const TileArgs& a, uint8_t* smem, int p0, i
 // reversed filter, so that every read is aligned) and each plane's digit
 // word (a broadcast, 8 inputs per load), for R x planes dp4a.
 __host__ __device__ constexpr int hybrid_threads(int HW) { return THREADS + 32 * HW; }
-constexpr int GDP = 2192;                     // bytes per filter copy slot: >= 2 * 1024 + 8 + 4 * 31
+constexpr int GDP = 2192;                     // bytes per filter copy slot: >= 2 * 1024 + 16 + 4 * 31
 constexpr int GDPW = 514;                     // words of a copy the dp4a reads reach: (2 * 1024 + 8) / 4
 // Byte offset of dp4a filter copy rr for R outputs per thread (R = 2, 3, 4).
 // The 8 lanes that read copy rr (the same rho) are R words apart, so their
@@ -686,23 +725,37 @@ __device__ __forceinline__ void tile_hybrid(const TileArgs& a, uint8_t* smem) {
         revw[i] = __byte_perm(__ldg(gw + a0), __ldg(gw + a1), 0x5670);
     }
     __syncthreads();
-    // the word of filter bytes g[(v - k) mod N], k = 0..3
-    auto gword = [&](int v) {
-        int sidx = (-v) % N;
-        if (sidx < 0) sidx += N;
-        const int q = sidx >> 2, b = sidx & 3;
-        return __funnelshift_r(revw[q], revw[q + 1], 8 * b);
-    };
-    const int top = T * uch;
-    for (int e = tid; e < 4 * (GW / 4); e += NTHR) {
-        const int rr = e / (GW / 4), zw = e - rr * (GW / 4);
-        *reinterpret_cast<uint32_t*>(gcp + rr * GW + 4 * zw) = gword(top - (4 * zw + rr - PADB));
-    }
-    // dp4a copies: copy rr, byte z holds g[(N + 4 - z - rr) mod N], i.e. the
-    // reversed filter at offset y = z + rr - N - 4
-    for (int e = tid; e < 4 * GDPW; e += NTHR) {
-        const int rr = e / GDPW, zw = e - rr * GDPW;
-        *reinterpret_cast<uint32_t*>(gdp + gdp_off(rr, R) + 4 * zw) = gword(N + 4 - 4 * zw - rr);
+    // Both filter windows are the reversed filter shifted by rr bytes: word w of
+    // tensor-pipe copy rr (byte z: g[(N - (z + rr - PADB)) mod N]) is the funnel
+    // shift by 8 rr of staged words (w - 4) mod NW and the one after it, word w
+    // of dp4a copy rr (byte z: g[(N + 4 - z - rr) mod N]) that of staged words
+    // (w - 1) mod NW and the one after it (word NW is word 0 again).  An item
+    // forms 4 consecutive words of one copy from 5 staged words.
+    constexpr int GQ = GW / 16, DQ = (GDPW + 3) / 4;      // items per copy
+    static_assert(GW % 16 == 0 && 16 * DQ + 4 * 31 <= GDP, "filter copies must hold whole items");
+    for (int e = tid; e < 4 * (GQ + DQ); e += NTHR) {
+        const bool tens = e < 4 * GQ;
+        const int e2 = tens ? e : e - 4 * GQ;
+        const int rr = tens ? e2 / GQ : e2 / DQ;
+        const int j = tens ? e2 - rr * GQ : e2 - rr * DQ;
+        int b4 = (4 * j - (tens ? 4 : 0)) % NW;
+        if (b4 < 0) b4 += NW;
+        const uint4 q = *reinterpret_cast<const uint4*>(revw + b4);
+        const uint32_t w0 = tens ? q.x : revw[b4 == 0 ? NW - 1 : b4 - 1];
+        const uint32_t w1 = tens ? q.y : q.x, w2 = tens ? q.z : q.y, w3 = tens ? q.w : q.z;
+        const uint32_t w4 = tens ? revw[b4 + 4] : q.w;
+        const int sh = 8 * rr;
+        const uint4 o = make_uint4(__funnelshift_r(w0, w1, sh), __funnelshift_r(w1, w2, sh),
+                                   __funnelshift_r(w2, w3, sh), __funnelshift_r(w3, w4, sh));
+        if (tens) {
+            *reinterpret_cast<uint4*>(gcp + rr * GW + 16 * j) = o;
+        } else {
+            uint32_t* d = reinterpret_cast<uint32_t*>(gdp + gdp_off(rr, R) + 16 * j);
+            d[0] = o.x;
+            d[1] = o.y;
+            d[2] = o.z;
+            d[3] = o.w;
+        }
     }
     cp_async_wait<0>();
     __syncthreads();
@@ -817,7 +870,7 @@ __device__ __forceinline__ void tile_hybrid(const TileArgs& a, uint8_t* smem) {
         }
     }
     __syncthreads();
-    epilogue<MT>(a, stash, 0, NB, NTHR);
+    epilogue<MT, 2>(a, stash, 0, NB, NTHR);
 }
 
 }  // namespace cconv
