@@ -190,7 +190,8 @@ __device__ __forceinline__ void epilogue_l(const TileArgs& a, const int32_t* sta
                 }
                 rot[j] = v;
             }
-            flag[p] = extract_rot<MT>(rot, M, l, check, res) && valid;
+            if constexpr (MT == 3 && LT != 0) flag[p] = extract_rot3<LT>(rot, check, res) && valid;
+            else flag[p] = extract_rot<MT>(rot, M, l, check, res) && valid;
             if (valid) {
 #pragma unroll
                 for (int j = 0; j < MX; j++) {

@@ -53,5 +53,27 @@ __device__ __forceinline__ bool extract_rot(const int64_t* rot, int M, int l, bo
     return flag;
 }
 
+// M = 3 with l = LT (8 or 16) in 64-bit arithmetic, the same bits as
+// extract_rot<3>.  With A1 = a_hi 2^l + a_lo and A2 = b_hi 2^(2l) + b_lo
+// (a_lo, b_lo the unsigned low parts), Eq. 19's exact quotient is
+//     d_r = a_hi - b_hi + (a_lo 2^l - b_lo + d_{r-1}) / 2^(2l),
+// every term of which fits 64 bits for l <= 30 (the last quotient is one of
+// -2..2), and Eq. 24's d_r + 2^l d_{r-1} fits 64 bits for l <= 20, so the
+// check compares exact values.
+template <int LT>
+__device__ __forceinline__ bool extract_rot3(const int64_t* rot, bool check, int64_t* out) {
+    static_assert(LT >= 1 && LT <= 20, "64-bit bounds hold for l <= 20");
+    constexpr int L = 2 * LT;
+    const int64_t A1 = rot[1], A2 = rot[2];
+    // Eq. 17-18: T = A2 - 2^l A1 (M = 3), d_{r-1} its low L bits sign-extended
+    const int64_t d_last = (int64_t)(((uint64_t)A2 - ((uint64_t)A1 << LT)) << (64 - L)) >> (64 - L);
+    const int64_t a_hi = A1 >> LT, a_lo = (int64_t)((uint64_t)A1 & ((1ull << LT) - 1));
+    const int64_t b_hi = A2 >> L, b_lo = (int64_t)((uint64_t)A2 & ((1ull << L) - 1));
+    const int64_t d_r = a_hi - b_hi + (((a_lo << LT) - b_lo + d_last) >> L);   // Eq. 19
+    out[0] = d_r;
+    out[2] = d_last;
+    out[1] = (int64_t)((uint64_t)A1 - ((uint64_t)d_r << LT));                // Eq. 20
+    return check && rot[0] != d_r + (int64_t)((uint64_t)d_last << LT);        // Eq. 24
+}
 
 }  // namespace ne
