@@ -553,6 +553,11 @@ __device__ __forceinline__ void tile(const TileArgs& a, uint8_t* smem, int p0, i
     int acc[NTW][4];
 #pragma unroll
     for (int j = 0; j < NTW; j++) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0;
+    // this lane's ldmatrix row of column tile tile0 (+ 8 rows per further
+    // tile).  A padding column (c >= cols, last tile only) reads a row past
+    // the window's used rows, still inside the shared memory of the window and
+    // the filter copies after it; its result is dropped at the stash.
+    const uint32_t bbase = sig_s + (8 * (tile0 + (lane >> 4)) + (lane & 7)) * ROWB + 16 * kh;
 
     for (int u0 = 0; u0 < NU; u0 += uch) {
         const int uc = min(uch, NU - u0);
@@ -599,23 +604,20 @@ __device__ __forceinline__ void tile(const TileArgs& a, uint8_t* smem, int p0, i
 
         for (int u = u0; u < u0 + uc; u++) {
             const int ushift = u0 + uch - 1 - u;
-            const int Y0 = T * (u0 + uch - u) - 16 * mt - gq;
+            const uint32_t ya = gcp_s + T * (u0 + uch - u) - 16 * mt - gq + 4 * tq;
+            const uint32_t yb = bbase + MS * ushift * ROWB;
 #pragma unroll
             for (int ks = 0; ks < 2; ks++) {
-                const int t0 = 32 * ks;
-                const uint32_t ya = gcp_s + Y0 + t0 + 4 * tq;
                 uint32_t af[4];
-                af[0] = lds32(ya);
-                af[1] = lds32(ya - 8);
-                af[2] = lds32(ya + 16);
-                af[3] = lds32(ya + 8);
+                af[0] = lds32(ya + 32 * ks);
+                af[1] = lds32(ya + 32 * ks - 8);
+                af[2] = lds32(ya + 32 * ks + 16);
+                af[3] = lds32(ya + 32 * ks + 8);
 #pragma unroll
                 for (int jj = 0; jj < NTW; jj += 2) {
                     if (jj >= ntile) break;
-                    int c = 8 * (tile0 + jj + (lane >> 4)) + (lane & 7);
-                    if (c >= cols) c = 0;    // padding column: any valid row, result dropped
                     uint32_t bf[4];
-                    ldsm_x4(bf, sig_s + (c + MS * ushift) * ROWB + t0 + 16 * kh);
+                    ldsm_x4(bf, yb + 8 * jj * ROWB + 32 * ks);
                     mma_s8(acc[jj], af, bf[0], bf[1]);
                     if (jj + 1 < ntile) mma_s8(acc[jj + 1], af, bf[2], bf[3]);
                 }
@@ -774,15 +776,10 @@ __device__ __forceinline__ void tile_hybrid(const TileArgs& a, uint8_t* smem) {
         int acc[NTW][4];
 #pragma unroll
         for (int j = 0; j < NTW; j++) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0;
-        // loop-invariant per lane: the ldmatrix row of each column-tile pair
-        // (a padding column reads row 0, its result is dropped) and the A words
-        uint32_t bbase[(NTW + 1) / 2];
-#pragma unroll
-        for (int jj = 0; jj < NTW; jj += 2) {
-            int c = 8 * (tile0 + jj + (lane >> 4)) + (lane & 7);
-            if (c >= cols) c = 0;
-            bbase[jj / 2] = sig_s + c * ROWB + 16 * kh;
-        }
+        // this lane's ldmatrix row of column tile tile0, + 8 rows per further
+        // tile (a padding column reads a row past the window's used rows,
+        // still inside the window and filter copies; its result is dropped)
+        const uint32_t bbase = sig_s + (8 * (tile0 + (lane >> 4)) + (lane & 7)) * ROWB + 16 * kh;
         // shift u: A words at ya - T u, B rows of window block uch - 1 - u
         const uint32_t ya0 = smem_u32(gcp) + rho * GW + PADB - rho + T * uch - 16 * mt - gq + 4 * tq;
         const uint32_t boff0 = (uch - 1) * MS * ROWB;
@@ -801,7 +798,7 @@ __device__ __forceinline__ void tile_hybrid(const TileArgs& a, uint8_t* smem) {
                 for (int jj = 0; jj < NTW; jj += 2) {
                     if (jj >= ntile) break;
                     uint32_t bf[4];
-                    ldsm_x4(bf, bbase[jj / 2] + boff + 32 * ks);
+                    ldsm_x4(bf, bbase + boff + 8 * jj * ROWB + 32 * ks);
                     mma_s8(acc[jj], af, bf[0], bf[1]);
                     if (jj + 1 < ntile) mma_s8(acc[jj + 1], af, bf[2], bf[3]);
                 }
