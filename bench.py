@@ -506,29 +506,36 @@ def run_ours(args, rank, world, local_rank):
         peak_dp4a = ops / (e0.elapsed_time(e1) * 1e-3) / 1e12
         achieved = mma_ops_per_launch / (inner_avg * 1e-3) / 1e12
         hybrid = wl.name == "cconv"
-        peak_mixed = {}
+        peak_mixed, peak_layouts = {}, {}
         if hybrid:
-            # both int8 pipes in the convolution kernel's warp layout (8 tensor + 4 dp4a warps,
-            # 3 blocks per SM), swept over the share of the work given to dp4a; the ceiling
-            # is the best split (the kernel gives dp4a 8 of 16 output blocks, 1/2)
+            # both int8 pipes in the convolution kernel's warp layouts (8 tensor + 4 dp4a warps
+            # at 3 blocks per SM, 4 + 4 at 4), swept over the share of the work given to dp4a;
+            # the ceiling is the best split and layout (the kernel gives dp4a 8 of 16 output
+            # blocks, 1/2, with 4 tensor warps)
             I, DW = 2048, 4
-            for num, den in ((0, 1), (1, 8), (1, 4), (3, 8), (1, 2)):
-                idp = (256 * I * num) // (DW * (den - num))
-                probe.mixed_peak(16, (256 * 16 * num) // (DW * (den - num)), 8, DW, 3)
-                e0.record(stream)
-                ops = probe.mixed_peak(I, idp, 8, DW, 3)
-                e1.record(stream)
-                torch.cuda.synchronize()
-                peak_mixed[f"{num}/{den}"] = ops / (e0.elapsed_time(e1) * 1e-3) / 1e12
+            for MW, BPS in ((8, 3), (4, 4)):
+                lay = peak_layouts.setdefault(f"{MW} tensor + {DW} dp4a warps x {BPS}", {})
+                for num, den in ((0, 1), (1, 8), (1, 4), (3, 8), (1, 2)):
+                    idp = (32 * MW * I * num) // (DW * (den - num))
+                    probe.mixed_peak(16, (32 * MW * 16 * num) // (DW * (den - num)), MW, DW, BPS)
+                    e0.record(stream)
+                    ops = probe.mixed_peak(I, idp, MW, DW, BPS)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    key = f"{num}/{den}"
+                    lay[key] = ops / (e0.elapsed_time(e1) * 1e-3) / 1e12
+                    peak_mixed[key] = max(peak_mixed.get(key, 0.0), lay[key])
         peak = max(peak_mixed.values()) if hybrid else peak_mma
         src = ("measured in this run: mma.sync.m16n8k32 s8 register-resident probe (probe/ne_probe.h, ne_probe_mma_peak)"
-               + ("; the kernel splits each group between the two int8 pipes (8 of 16 blocks on 8 tensor "
-                  "warps, 8 on 4 dp4a warps), so the peak is the best of ne_probe_mixed_peak (both pipes in "
-                  "the kernel's warp layout) over the dp4a work shares in peak_mixed" if hybrid else "")
+               + ("; the kernel splits each group between the two int8 pipes (8 of 16 blocks on 4 tensor "
+                  "warps, 8 on 4 dp4a warps, 4 blocks per SM), so the peak is the best of ne_probe_mixed_peak "
+                  "(both pipes in the kernel's warp layouts, peak_mixed_layouts) over the dp4a work shares in "
+                  "peak_mixed" if hybrid else "")
                + "; MEASURED_PEAKS.json has no int8 figure and sm_103a has no tcgen05 integer MMA")
         roof = {"bound": "tensor", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "TOP/s",
                 "frac": achieved / peak, "traffic": traffic_for(dominant, dom_src), "peak_source": src,
                 "peak_mma": peak_mma, "peak_dp4a": peak_dp4a, "peak_mixed": peak_mixed or None,
+                "peak_mixed_layouts": peak_layouts or None,
                 "algorithmic": f"{mma_ops_per_launch} int8 ops per launch (2 x M x S x units)",
                 "ms_per_launch": inner_avg}
     elif wl.name == "cconv_ntt":

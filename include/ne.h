@@ -285,8 +285,10 @@ ne_status ne_lconv(ne_params p, ne_digits dg, const int32_t* c, const int8_t* g,
  * after it): how ne_cconv_digits and ne_cconv_entangled split a group of at
  * most 16 Toeplitz blocks between the int8 tensor pipe and the dp4a pipe of
  * the CUDA cores.  -1: the default (the split measured fastest per digit-plane
- * count); 0: tensor pipe only; HR in {23, 24, 34, 42, 43, 44}: H dp4a warps
- * of R outputs per thread take H * R / 2 of the blocks.  NE_EINVAL for any
+ * count); 0: tensor pipe only; HR in {23, 24, 34, 42, 43, 44}: 8 tensor
+ * warps and H dp4a warps of R outputs per thread, which take H * R / 2 of
+ * the blocks; 4HR in {443, 444}: the same with 4 tensor warps (groups of 16
+ * blocks from raw streams or planes; others take HR).  NE_EINVAL for any
  * other value. */
 ne_status ne_set_cconv_split(int32_t variant);
 

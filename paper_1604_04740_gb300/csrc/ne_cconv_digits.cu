@@ -30,7 +30,7 @@ extern "C" ne_status ne_cconv_digits(ne_params p, ne_digits dg, const int8_t* pl
 }
 
 extern "C" ne_status ne_set_cconv_split(int32_t variant) {
-    static const int ok[] = {-1, 0, 23, 24, 34, 42, 43, 44};
+    static const int ok[] = {-1, 0, 23, 24, 34, 42, 43, 44, 443, 444};
     for (int v : ok)
         if (v == variant) {
             g_split = variant;

@@ -98,8 +98,9 @@ __global__ void __launch_bounds__(cconv::THREADS, (NTW <= 6 ? 4 : (NTW <= 10 ? 3
 
 // The hybrid tile (tensor pipe + dp4a pipe) for groups of 9..16 blocks
 // (NBC: 16 for groups of exactly 16 blocks, compiled for that size; 0: any).
-template <int MT, int MSC, int HW, int R, int LD, int NBC>
-__global__ void __launch_bounds__(cconv::hybrid_threads(HW), cconv::hybrid_threads(HW) <= 384 ? 3 : 2)
+template <int MT, int MSC, int HW, int R, int LD, int NBC, int TW>
+__global__ void __launch_bounds__(cconv::hybrid_threads(HW, TW),
+                                  cconv::hybrid_threads(HW, TW) <= 256 ? 4 : (cconv::hybrid_threads(HW, TW) <= 384 ? 3 : 2))
     k_cconv_digits_hybrid(CconvArgs a, int64_t b_off) {
     extern __shared__ __align__(128) uint8_t smem[];
     const int64_t b = b_off + blockIdx.y;
@@ -122,10 +123,10 @@ __global__ void __launch_bounds__(cconv::hybrid_threads(HW), cconv::hybrid_threa
 #pragma unroll
     for (int i = 0; i < NE_MAX_DIGITS; i++) t.shift[i] = a.shift[i];
     raw_fields(a, b, t);
-    cconv::tile_hybrid<MT, MSC, HW, R, LD, NBC>(t, smem);
+    cconv::tile_hybrid<MT, MSC, HW, R, LD, NBC, TW>(t, smem);
 }
 
-template <int MT, int MSC, int HW, int R, int LD, int NBC>
+template <int MT, int MSC, int HW, int R, int LD, int NBC, int TW = 8>
 ne_status launch_hybrid(const CconvArgs& a, int64_t batch, cudaStream_t s) {
     if (a.N / cconv::T <= 32 * HW * R / cconv::T) return NE_EINVAL;   // needs a block left for the tensor pipe
     const int smem = cconv::hybrid_smem_bytes(MSC);
@@ -133,14 +134,15 @@ ne_status launch_hybrid(const CconvArgs& a, int64_t batch, cudaStream_t s) {
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-        if (cudaFuncSetAttribute(k_cconv_digits_hybrid<MT, MSC, HW, R, LD, NBC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if (cudaFuncSetAttribute(k_cconv_digits_hybrid<MT, MSC, HW, R, LD, NBC, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  smem) != cudaSuccess)
             return check_launch("ne_cconv_digits: shared-memory attribute");
         attr_set[dev] = true;
     }
     for (int64_t b0 = 0; b0 < batch; b0 += 65535) {
         const int64_t nb = batch - b0 < 65535 ? batch - b0 : 65535;
-        k_cconv_digits_hybrid<MT, MSC, HW, R, LD, NBC><<<dim3(1, (unsigned)nb), cconv::hybrid_threads(HW), smem, s>>>(a, b0);
+        k_cconv_digits_hybrid<MT, MSC, HW, R, LD, NBC, TW>
+            <<<dim3(1, (unsigned)nb), cconv::hybrid_threads(HW, TW), smem, s>>>(a, b0);
         ne_status st = check_launch("ne_cconv_digits (hybrid)");
         if (st) return st;
     }
@@ -149,17 +151,17 @@ ne_status launch_hybrid(const CconvArgs& a, int64_t batch, cudaStream_t s) {
 
 // Split of a group between the tensor pipe and the dp4a pipe (variant -1:
 // the default).  Default for groups of 16 blocks (measured on GB300 at 4096
-// groups of N = 1024): 6 planes (M = 3, two digits) put 8 blocks on 4 dp4a
-// warps of 4 outputs per thread (variant 44, half of the work; 0.260 ms
-// against 0.272 ms for 43 and 0.271 ms for 34), 8 planes 6 blocks on 4 warps
-// of 3 outputs (variant 43; 0.336 ms against 0.366 ms for 44, whose 32 dp4a
-// accumulators per thread spill, and 0.381 ms for 24).
+// groups of N = 1024): 8 blocks on 4 tensor warps and 8 on 4 dp4a warps of 4
+// outputs per thread (variant 444: 4 CTAs per SM for 6 planes; M = 3 0.250 ms
+// against 0.259 ms with 8 tensor warps (44) and 0.270 ms for 43; M = 4 0.330
+// ms against 0.333 ms for 43).
 // ne_set_cconv_split overrides it: 0 tensor pipe only; HR (23, 24, 34, 42,
-// 43, 44) H dp4a warps of R outputs per thread (H * R / 2 blocks on dp4a),
-// for any group of at most 16 blocks.
+// 43, 44) 8 tensor warps and H dp4a warps of R outputs per thread (H * R / 2
+// blocks on dp4a), for any group of at most 16 blocks; 443, 444 the same
+// dp4a share with 4 tensor warps (groups of 16 blocks; others take 43, 44).
 
 int hybrid_variant(int64_t NB, int MS) {
-    if (g_split == -1) return NB == 16 ? (MS == 6 ? 44 : 43) : 0;
+    if (g_split == -1) return NB == 16 ? 444 : 0;
     return g_split;
 }
 
@@ -181,6 +183,18 @@ ne_status launch_hybrid_variant(int var, const CconvArgs& a, int64_t batch, cuda
         case 42: return launch_hybrid_n<MT, MSC, 4, 2, LD>(a, batch, s);
         case 43: return launch_hybrid_n<MT, MSC, 4, 3, LD>(a, batch, s);
         case 44: return launch_hybrid_n<MT, MSC, 4, 4, LD>(a, batch, s);
+        // 4 tensor warps + 4 dp4a warps (4 CTAs per SM when shared memory
+        // allows), groups of 16 blocks from raw streams or planes; otherwise
+        // the same dp4a share with 8 tensor warps
+        case 444:
+        case 443:
+            if constexpr (LD != cconv::LD_WORDS) {
+                if (a.N == 16 * cconv::T)
+                    return var == 444 ? launch_hybrid<MT, MSC, 4, 4, LD, 16, 4>(a, batch, s)
+                                      : launch_hybrid<MT, MSC, 4, 3, LD, 16, 4>(a, batch, s);
+            }
+            return var == 444 ? launch_hybrid_n<MT, MSC, 4, 4, LD>(a, batch, s)
+                              : launch_hybrid_n<MT, MSC, 4, 3, LD>(a, batch, s);
         default: return NE_EINVAL;
     }
 }

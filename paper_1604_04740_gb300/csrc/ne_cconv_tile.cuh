@@ -658,7 +658,8 @@ __device__ __forceinline__ void tile(const TileArgs& a, uint8_t* smem, int p0, i
 // thread loads one new filter word (from four byte-shifted copies of the
 // reversed filter, so that every read is aligned) and each plane's digit
 // word (a broadcast, 8 inputs per load), for R x planes dp4a.
-__host__ __device__ constexpr int hybrid_threads(int HW) { return THREADS + 32 * HW; }
+// TW tensor warps (8: two column halves of 4 row tiles; 4: one) and HW dp4a warps
+__host__ __device__ constexpr int hybrid_threads(int HW, int TW = 8) { return 32 * (TW + HW); }
 constexpr int GDP = 2192;                     // bytes per filter copy slot: >= 2 * 1024 + 16 + 4 * 31
 constexpr int GDPW = 514;                     // words of a copy the dp4a reads reach: (2 * 1024 + 8) / 4
 // Byte offset of dp4a filter copy rr for R outputs per thread (R = 2, 3, 4).
@@ -685,10 +686,13 @@ __host__ __device__ constexpr int hybrid_smem_bytes(int MS) {
 
 // NBC: the group's block count when the caller fixes it at compile time (every
 // size below and the shape of the tensor warps' loop are then constants), else 0
-template <int MT, int MSC, int HW, int R, int LD = LD_PLANES, int NBC = 0>
+template <int MT, int MSC, int HW, int R, int LD = LD_PLANES, int NBC = 0, int TW = 8>
 __device__ __forceinline__ void tile_hybrid(const TileArgs& a, uint8_t* smem) {
     constexpr int MS = MSC;
-    constexpr int NTHR = hybrid_threads(HW);
+    constexpr int NTHR = hybrid_threads(HW, TW);
+    constexpr int HALVES = TW / 4;        // column parts of the tensor warps
+    static_assert(TW == 4 || TW == 8, "4 or 8 tensor warps");
+    static_assert(TW == 8 || NBC != 0, "4 tensor warps hold every column tile: compile-time groups only");
     constexpr int DT = 32 * HW;           // dp4a threads
     static_assert((DT * R) % T == 0, "dp4a outputs must be whole blocks");
     static_assert(R >= 2 && R <= 4, "the dp4a filter copies are laid out for 2 to 4 outputs per thread");
@@ -700,7 +704,7 @@ __device__ __forceinline__ void tile_hybrid(const TileArgs& a, uint8_t* smem) {
     const int WB = npb + uch - 1;
     const int cols = npb * MS;
     const int NT = (cols + 7) / 8;
-    const int NTH = (NT + 1) / 2;
+    const int NTH = (NT + HALVES - 1) / HALVES;
 
     uint8_t* sig = smem;                                  // [WB][MS][ROWB]
     uint8_t* gcp = smem + WBMAX * MS * ROWB;              // 4 x GW (tensor-pipe filter window)
@@ -763,16 +767,19 @@ __device__ __forceinline__ void tile_hybrid(const TileArgs& a, uint8_t* smem) {
     cp_async_wait<0>();
     __syncthreads();
 
-    if (warp < THREADS / 32) {
+    if (warp < TW) {
         // -- tensor pipe: output blocks [0, npb), as in tile() --
         const int mt = warp & 3, half = warp >> 2;
         const int gq = lane >> 2, tq = lane & 3;
         const int tile0 = half * NTH;
         // both halves hold NTH column tiles when NT is even
-        const int ntile = NT == 2 * NTH ? NTH : max(0, min(NT, tile0 + NTH) - tile0);
+        const int ntile = NT == HALVES * NTH ? NTH : max(0, min(NT, tile0 + NTH) - tile0);
         const int kh = (lane >> 3) & 1;
         const int rho = (4 - (gq & 3)) & 3;
-        constexpr int NTW = (16 * MS / 8 + 1) / 2;
+        // column tiles a warp holds: at most 16 blocks' worth, or exactly the
+        // compile-time group's
+        constexpr int NTW = NBC ? (((NBC - DT * R / T) * MS + 7) / 8 + HALVES - 1) / HALVES
+                                : (16 * MS / 8 + HALVES - 1) / HALVES;
         int acc[NTW][4];
 #pragma unroll
         for (int j = 0; j < NTW; j++) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0;
@@ -819,7 +826,7 @@ __device__ __forceinline__ void tile_hybrid(const TileArgs& a, uint8_t* smem) {
         }
     } else {
         // -- dp4a pipe: thread t = 4 k + rho owns outputs i0 + 4 r, i0 = npb T + rho + 4 R k --
-        const int t = tid - THREADS;               // 0 .. DT - 1
+        const int t = tid - 32 * TW;               // 0 .. DT - 1
         const int rho = t & 3, k = t >> 2;
         const int rr = (4 - rho) & 3;              // the copy whose words start at i0's byte shift
         const int i0 = npb * T + rho + 4 * R * k;

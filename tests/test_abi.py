@@ -160,23 +160,26 @@ def test_lsb_operator_argument_checks(lib):
 
 
 def test_cconv_split_accepts_exactly_the_documented_variants(lib):
-    # ne.h lists the tensor / dp4a splits: -1 (default), 0 (tensor pipe only)
-    # and HR = H dp4a warps of R outputs per thread; anything else is refused
+    # ne.h lists the tensor / dp4a splits: -1 (default), 0 (tensor pipe only),
+    # HR = 8 tensor warps and H dp4a warps of R outputs per thread, and 4HR the
+    # same with 4 tensor warps; anything else is refused
     lib.ne_set_cconv_split.argtypes = [ctypes.c_int32]
-    header = open(os.path.join(ROOT, "include", "ne.h")).read()
-    listed = re.search(r"HR in \{([0-9, ]+)\}", header.replace("\n *", " "))
-    assert listed, "ne.h documents the accepted splits"
-    documented = {int(v) for v in listed.group(1).split(",")}
+    header = re.sub(r"\s*\n\s*\*\s*", " ", open(os.path.join(ROOT, "include", "ne.h")).read())
+    hr = re.search(r"HR in \{([0-9, ]+)\}", header)
+    twhr = re.search(r"4HR in \{([0-9, ]+)\}", header)
+    assert hr and twhr, "ne.h documents the accepted splits"
+    documented = {int(v) for v in hr.group(1).split(",")} | {int(v) for v in twhr.group(1).split(",")}
     try:
         for v in sorted(documented | {-1, 0}):
             assert lib.ne_set_cconv_split(v) == 0, v
-        for v in range(-3, 100):
+        for v in range(-3, 500):
             if v not in documented | {-1, 0}:
                 assert lib.ne_set_cconv_split(v) == 1, v
-        # every accepted HR puts whole 64-output blocks on the dp4a warps and
-        # keeps three CTAs of 256 + 32 H threads within 384 threads
+        # every accepted code puts whole 64-output blocks on the dp4a warps and
+        # keeps a CTA of 32 (TW + H) threads within 384
         for v in documented:
-            H, R = divmod(v, 10)
-            assert (32 * H * R) % 64 == 0 and 2 <= R <= 4 and 256 + 32 * H <= 384, v
+            TW = 4 if v >= 100 else 8
+            H, R = divmod(v % 100, 10)
+            assert (32 * H * R) % 64 == 0 and 2 <= R <= 4 and 32 * (TW + H) <= 384, v
     finally:
         assert lib.ne_set_cconv_split(-1) == 0

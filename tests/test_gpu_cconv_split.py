@@ -19,7 +19,7 @@ torch = pytest.importorskip("torch")
 
 DEV = "cuda"
 
-SPLITS = [0, 23, 24, 34, 42, 43, 44]
+SPLITS = [0, 23, 24, 34, 42, 43, 44, 443, 444]
 
 
 @pytest.fixture(scope="module")
