@@ -650,8 +650,9 @@ __device__ __forceinline__ void tile(const TileArgs& a, uint8_t* smem, int p0, i
 // into an int32, on the integer ALUs) have about the same throughput and run
 // on separate pipes.  For groups of 9..16 blocks (N in (512, 1024]) the
 // hybrid tile gives the last HW * R / 2 output blocks to HW extra warps that
-// compute them with dp4a, while the 8 MMA warps compute the other blocks as
-// tile() does; both finish into the same stash and the same epilogue.  A
+// compute them with dp4a, while TW MMA warps (8 as in tile(), or 4 that each
+// hold every column tile of their 16 rows) compute the other blocks; both
+// finish into the same stash and the same epilogue.  A
 // dp4a thread owns R outputs 4 apart, i0 + 4 r, for every digit plane.  The
 // filter word that output i0 + 4 r needs at input chunk J (positions 4 J ..
 // 4 J + 3) is the one output i0 needs at chunk J - r, so per 4 inputs a
